@@ -1,0 +1,40 @@
+"""Workload table: the five synthetic workloads the tests and benchmark use.
+
+Each entry names the volume recipe, wavelet levels J, global coefficient
+budget K_tot, number of views and image size.  Sizes follow the scale of the
+paper's datasets (Sec. 5.1: 256^3 to 512^3 volumes, ~1.8e5 Gaussians for
+Supernova) while staying synthetic.
+"""
+
+import numpy as np
+
+_C3_EDGE_CHOICES = (32, 48, 64, 96, 128)
+
+
+def _c3_edges(seed=3, n=32):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(e) for e in rng.choice(_C3_EDGE_CHOICES, size=n)]
+
+
+CONFIGS = {
+    "c0": dict(key="c0", workload="tiny: 32^3 blobs, J=2, ~4k Gaussians, 1 view 128x128",
+               volume="blobs", G=32, blobs=4, seed=0, levels=2, K_tot=4096,
+               views=1, width=128, height=128),
+    "c1": dict(key="c1", workload="128^3 blobs+k^-2 noise, J=3, ~100k Gaussians, 8 views 512x512",
+               volume="blobs+bandnoise", G=128, blobs=32, seed=1, levels=3, K_tot=100000,
+               views=8, width=512, height=512),
+    "c2": dict(key="c2", workload="256^3 k^-5/3 turbulence, J=4, ~500k Gaussians, 16 views 800x800",
+               volume="turbulence", G=256, seed=2, levels=4, K_tot=500000,
+               views=16, width=800, height=800),
+    "c3": dict(key="c3", workload="32 uneven blob volumes (edges 32..128), J=2, 4 views 256x256 each",
+               volume="blobs", edges=_c3_edges(), seed=3, levels=2, K_tot_frac=0.07,
+               views_per_volume=4, width=256, height=256),
+    "c4": dict(key="c4", workload="512^3 supernova-like shells, J=5, ~3M Gaussians, 8 views 1024x1024",
+               volume="supernova", G=512, seed=4, levels=5, K_tot=3000000,
+               views=8, width=1024, height=1024, fwd_only=(1920, 1080)),
+}
+
+
+def config(key):
+    """A copy of one workload entry."""
+    return dict(CONFIGS[key])
