@@ -1,0 +1,370 @@
+"""Benchmark of the VBM image-space fine-tuning step on GB300.
+
+Workload (default "c1"): a 128^3 synthetic volume (32 random blobs plus
+k^-2 band-limited noise), 3-level bior4.4 DWT, ~1e5 Gaussians built on the
+GPU by vbm_build, 8 orbit views at 512x512 rendered by vbm_render_dvr as
+targets.  One step = forward splatting of all views, L1 + D-SSIM loss,
+backward to every Gaussian parameter, Adam (Sec. 4.4).
+
+value      steps/s of the batched step (all views per launch, CUDA graph),
+           device time from CUDA events, L2 flushed between steps
+plain      steps/s of the same step run one view per launch sequence
+e2e        steps/s through FineTuner.step_host: targets copied from pinned
+           host memory every step, loss read back every step
+roofline   the dominant kernel (forward or backward compositing) timed live
+           with CUDA events recorded by the library on its launch stream
+cpu_baseline  the FP64 oracle on the host, one view of the step (scaled)
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun with N > 1 every rank runs an independent replica (the step
+has no cross-GPU exchange in this build); rank 0 prints the line.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fine-tune steps/sec (fwd+bwd, batched vs plain) on 1 GB300; raster Gpixel/s; %roofline"
+FWD_FLOP_PER_PAIR = 20     # dx, dy, quadratic form, o*G, min, 1-a, T(1-a), a*T, 3 colour FMAs
+BWD_FLOP_PER_PAIR = 60     # T recovery, colour and alpha partials, exponent chain, 9 partial sums
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c1")
+    ap.add_argument("--plain-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+
+def make_workload(cfg_key, device):
+    """Volume -> Gaussians (vbm_build) and DVR targets (vbm_render_dvr), all on the GPU."""
+    import torch
+    from paper_2601_09417_gb300 import vbm
+    from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, config, orbit_cameras, volume_for_config
+    from vbm_inputs.cameras import camera_array
+    cfg = config(cfg_key)
+    F = volume_for_config(cfg)
+    G = cfg["G"]
+    dims = (G, G, G)
+    tf = vbm.make_tf(TF_KNOTS_X, TF_KNOTS_RGBA)
+    bank = vbm.bank_build(cfg["levels"], 0)
+    Fd = torch.from_numpy(F).to(device)
+    params, n = vbm.build(Fd, dims, tf, bank, vbm.make_select(cfg["K_tot"]), capacity=2 * cfg["K_tot"])
+    params = params[:, :n].contiguous()
+    cams = orbit_cameras(dims, cfg["views"], cfg["width"], cfg["height"])
+    recs = camera_array(cams)
+    cams_dev = vbm.cameras_to_device(recs, device)
+    rgba = torch.zeros((cfg["views"], 4, cfg["height"], cfg["width"]), device=device)
+    vbm.render_dvr(Fd, dims, tf, cams_dev, cfg["views"], cfg["width"], cfg["height"], 0.5, rgba)
+    targets = rgba[:, :3].contiguous()
+    torch.cuda.synchronize()
+    return cfg, F, params, n, recs, cams, targets
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- timing
+
+def time_steps(fn, steps, flush):
+    """Per-step CUDA-event times (ms) with an L2 flush before each step."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s, e in evs:
+        flush()
+        s.record()
+        fn()
+        e.record()
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in evs]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("raster.cu", "vbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_2601_09417_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu capture of the current kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------- cpu baseline
+
+def cpu_baseline(cfg, P_host, cams, targets_host):
+    """FP64 oracle, one view of the step plus Adam over all Gaussians, scaled to a step."""
+    from oracle import adam as oadam
+    from oracle import loss as oloss
+    from oracle import raster as oraster
+    from vbm_inputs.cameras import cameras_as_float32
+    c32 = cameras_as_float32(cams)
+    P64 = P_host.astype(np.float64)
+    t0 = time.perf_counter()
+    fwd = oraster.splat_forward(P64, [c32[0]])
+    _, dimg = oloss.loss_and_grad(fwd["img"], targets_host[:1].astype(np.float64))
+    dimg *= 1.0 / len(cams)
+    grad, _, _ = oraster.splat_backward(fwd, P64, [c32[0]], dimg)
+    t_view = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oadam.adam_step(P64, grad, np.zeros_like(P64), np.zeros_like(P64), 1, oadam.default_lrs(cfg["G"]))
+    t_adam = time.perf_counter() - t1
+    t_step = len(cams) * t_view + t_adam
+    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": "1 of %d views (projection, binning, compositing, loss, backward) timed, x%d, plus Adam "
+                      "over all %d Gaussians; %.2f s per view" % (len(cams), len(cams), P_host.shape[1], t_view)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the same workload, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    device = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    if device is None:
+        print(json.dumps({"impl": "reference", "unavailable": "workload inputs are built on the GPU"}))
+        return
+    torch.cuda.set_device(device)
+    cfg, F, params, n, recs, cams, targets = make_workload(args.config, device)
+    P = params.cpu().numpy()
+    T = targets.cpu().numpy()
+    vals = []
+    for _ in range(max(1, min(args.steps, 3))):
+        vals.append(cpu_baseline(cfg, P, cams, T))
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "gaussians": int(n)},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2601_09417_gb300 import vbm
+    from paper_2601_09417_gb300.finetune import FineTuner
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    vbm.load()
+
+    cfg, F, params, n, recs, cams, targets = make_workload(args.config, device)
+    V, H, W = cfg["views"], cfg["height"], cfg["width"]
+    ft = FineTuner(params, recs, targets, extent=cfg["G"])
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    # profiling hooks: events around the compositing kernels, recorded inside the graph
+    kev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in kev:          # torch creates the underlying cudaEvent on the first record
+        e.record()
+    torch.cuda.synchronize()
+    ft.plan.set_profile(kev)
+    ft.capture()
+    for _ in range(args.warmup):
+        ft.step_graph()
+    torch.cuda.synchronize()
+    ok, need, bad = ft.check()
+    if not ok:
+        raise RuntimeError("pair capacity too small: %d needed" % need)
+
+    launches0 = vbm.kernel_launches()
+    ft.step_batched()
+    torch.cuda.synchronize()
+    launches_per_step = vbm.kernel_launches() - launches0
+
+    # ------------------------------------------------------------ timed region
+    props = torch.cuda.get_device_properties(device)
+    uuid = str(getattr(props, "uuid", "")) or str(local)
+    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else uuid))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ms, fwd_ms, bwd_ms = [], [], []
+    s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush()
+        s_ev.record()
+        ft.step_graph()
+        e_ev.record()
+        e_ev.synchronize()
+        step_ms.append(s_ev.elapsed_time(e_ev))
+        fwd_ms.append(kev[0].elapsed_time(kev[1]))
+        bwd_ms.append(kev[2].elapsed_time(kev[3]))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ----------------------------------------------------- plain (per view) form
+    plain_steps = args.plain_steps if args.plain_steps is not None else max(3, min(args.steps, 20))
+    ft.plan.set_profile(None)
+    for _ in range(2):
+        ft.step_plain()
+    plain = time_steps(ft.step_plain, plain_steps, flush)
+    plain_ms = sum(plain) / len(plain)
+
+    # ------------------------------------------------------------ end to end
+    host_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
+    host_t.copy_(targets)
+    host_l = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    ft.plan.set_profile(kev)
+    ft.capture()
+    for _ in range(2):
+        ft.step_host(host_t, host_l)
+    e2e = time_steps(lambda: ft.step_host(host_t, host_l), args.steps, flush)
+    e2e_ms = sum(e2e) / len(e2e)
+
+    # ------------------------------------------------------- algorithmic work
+    n_eval = torch.zeros((V, H, W), dtype=torch.int32, device=device)
+    ft.plan.set_profile(None, n_eval)
+    ft.plan.forward(ft.params, ft.cams, ft.img)
+    torch.cuda.synchronize()
+    st = ft.plan.buffers()
+    p_fwd = int(n_eval.sum().item())
+    p_bwd = int(vbm.device_tensor(st.n_contrib, (V, H, W), np.int32).sum().item())
+    n_pairs = int(vbm.device_tensor(st.n_pairs, (1,), np.int64).item())
+    f_fwd = sum(fwd_ms) / len(fwd_ms)
+    f_bwd = sum(bwd_ms) / len(bwd_ms)
+    peak_tflops = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if f_bwd >= f_fwd:
+        kname, flops, kms = "raster_bwd", p_bwd * BWD_FLOP_PER_PAIR, f_bwd
+    else:
+        kname, flops, kms = "raster_fwd", p_fwd * FWD_FLOP_PER_PAIR, f_fwd
+    achieved = flops / (kms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": profiled_traffic(kname), "kernel": kname,
+                "kernel_ms": kms, "fwd_kernel_ms": f_fwd, "bwd_kernel_ms": f_bwd,
+                "pairs_fwd": p_fwd, "pairs_bwd": p_bwd,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock",
+                "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR}}
+
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
+                       "tile": "16x16", "pairs": n_pairs, "form": "batched, CUDA graph",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "plain": {"value": 1e3 / plain_ms, "unit": "steps/s", "ms_per_step": plain_ms,
+                      "form": "one view per launch sequence, no graph"},
+            "batched_over_plain": plain_ms / ms_per_step,
+            "raster_gpixel_per_s": V * H * W / (f_fwd * 1e-3) / 1e9,
+            "e2e": {"value": 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(targets.numel() * 4),
+                    "d2h_bytes_per_step": 8},
+            "roofline": roofline, "gpu_launches": int(launches_per_step * args.steps),
+            "wall_s_timed": wall}
+    if clk is not None:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, ft.params.cpu().numpy(), cams, targets.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -48,7 +48,7 @@ def _load():
         lib.orc_project.argtypes = [I64, P, P, I64, P, I32, I32, P]
         lib.orc_bin_sort.argtypes = [I64, P, P, P, I32, I32, I32, I64, P, P, P]
         lib.orc_bin_sort.restype = I64
-        lib.orc_render.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_render.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_render_bwd.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, I64]
         lib.orc_render_brute.argtypes = [I32, I32, I32, I32, I32, I64, P, P, P, P, P, P, P, P]
         lib.orc_project_bwd_items.argtypes = [I64, P, P, I64, P, P, P]
@@ -112,9 +112,10 @@ def render(n_views, W, H, tile_w, tile_h, ranges, items, splat, color, bg):
     nc = np.zeros((n_views, H, W), dtype=np.int32)
     ne = np.zeros((n_views, H, W), dtype=np.int32)
     margin = np.zeros((n_views, H, W))
+    nb = np.zeros((n_views, H, W), dtype=np.int32)
     lib.orc_render(n_views, W, H, tile_w, tile_h, _p(ranges), _p(items), _p(splat), _p(color), _p(bg),
-                   _p(img), _p(T), _p(nc), _p(ne), _p(margin))
-    return dict(img=img, T_final=T, n_contrib=nc, n_eval=ne, margin=margin)
+                   _p(img), _p(T), _p(nc), _p(ne), _p(margin), _p(nb))
+    return dict(img=img, T_final=T, n_contrib=nc, n_eval=ne, margin=margin, n_blend=nb)
 
 
 def render_bwd(n_views, W, H, tile_w, tile_h, ranges, items, splat, color, bg, dL_dimg, dL_dalpha=None):

@@ -289,7 +289,8 @@ static int composite_pixel(const scene_desc *sd, int view, int px, int py, doubl
 
 void orc_render(int n_views, int W, int H, int tile_w, int tile_h, const int32_t *ranges, const int32_t *items,
                 const double *splat, const double *color, const double *bg,
-                double *img, double *T_final, int32_t *n_contrib, int32_t *n_eval, double *margin)
+                double *img, double *T_final, int32_t *n_contrib, int32_t *n_eval, double *margin,
+                int32_t *n_blend)
 {
     scene_desc sd = {ranges, items, splat, color, bg, W, H, tile_w, tile_h,
                      (W + tile_w - 1) / tile_w, (H + tile_h - 1) / tile_h};
@@ -299,13 +300,14 @@ void orc_render(int n_views, int W, int H, int tile_w, int tile_h, const int32_t
             for (int px = 0; px < W; px++) {
                 double C[3], T, m;
                 int32_t last, ev;
-                composite_pixel(&sd, v, px, py, C, &T, &last, &ev, &m, NULL);
+                int nb = composite_pixel(&sd, v, px, py, C, &T, &last, &ev, &m, NULL);
                 int64_t pix = (int64_t)py * W + px;
                 for (int ch = 0; ch < 3; ch++) img[((int64_t)v * 3 + ch) * HW + pix] = C[ch];
                 T_final[v * HW + pix] = T;
                 n_contrib[v * HW + pix] = last;
                 if (n_eval) n_eval[v * HW + pix] = ev;
                 if (margin) margin[v * HW + pix] = m;
+                if (n_blend) n_blend[v * HW + pix] = nb;
             }
 }
 

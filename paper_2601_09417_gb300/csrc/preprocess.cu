@@ -1,0 +1,310 @@
+// EWA projection of 3D Gaussians to 2D splats (forward and backward).
+//
+// One thread per (view, Gaussian) item.  Parameters are read from the SoA
+// layout P[14][stride], so the 14 loads of a warp are each one coalesced
+// 128-byte transaction.  The forward writes the per-item splat records the
+// rasteriser stages (geo = u, v, A, B; col = r, g, b, opacity; conic C), the
+// tile rectangle, the depth key of the depth sort and the tile count.  The
+// backward recomputes the forward state from the parameters (cheaper than
+// storing it) and sums the per-view contributions of a Gaussian in
+// registers, so the parameter gradient is written once, without atomics.
+//
+// Sec. 4.4 fine-tunes "as in" 3D Gaussian Splatting; the constants are that
+// method's (vbm_internal.h).
+#include "vbm_internal.h"
+
+namespace vbm {
+namespace {
+
+struct ProjState {
+    float mu[3], s[3], qn[4], qnorm, R[3][3], Sig[3][3];
+    float t[3], xzc, yzc;
+    bool clampx, clampy, culled;
+    float T0[3], T1[3];
+    float a, b, c, det, opac;
+};
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+__device__ __forceinline__ int floordiv_i(int a, int b)
+{
+    int q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+__device__ void project_state(const float *__restrict__ P, int64_t stride, int64_t g, const vbm_camera &cam,
+                              ProjState &st)
+{
+#pragma unroll
+    for (int k = 0; k < 3; k++) st.mu[k] = P[k * stride + g];
+#pragma unroll
+    for (int k = 0; k < 3; k++) st.s[k] = expf(P[(3 + k) * stride + g]);
+    float q[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) q[k] = P[(6 + k) * stride + g];
+    st.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    float inv = 1.0f / st.qnorm;
+#pragma unroll
+    for (int k = 0; k < 4; k++) st.qn[k] = q[k] * inv;
+    float w = st.qn[0], x = st.qn[1], y = st.qn[2], z = st.qn[3];
+    st.R[0][0] = 1.f - 2.f * (y * y + z * z); st.R[0][1] = 2.f * (x * y - w * z); st.R[0][2] = 2.f * (x * z + w * y);
+    st.R[1][0] = 2.f * (x * y + w * z); st.R[1][1] = 1.f - 2.f * (x * x + z * z); st.R[1][2] = 2.f * (y * z - w * x);
+    st.R[2][0] = 2.f * (x * z - w * y); st.R[2][1] = 2.f * (y * z + w * x); st.R[2][2] = 1.f - 2.f * (x * x + y * y);
+    float s2[3] = {st.s[0] * st.s[0], st.s[1] * st.s[1], st.s[2] * st.s[2]};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            st.Sig[a][b] = st.R[a][0] * s2[0] * st.R[b][0] + st.R[a][1] * s2[1] * st.R[b][1] +
+                           st.R[a][2] * s2[2] * st.R[b][2];
+    const float *Wm = cam.R;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+        st.t[r] = Wm[3 * r] * st.mu[0] + Wm[3 * r + 1] * st.mu[1] + Wm[3 * r + 2] * st.mu[2] + cam.t[r];
+    st.opac = 1.0f / (1.0f + expf(-P[10 * stride + g]));
+    st.culled = !(st.t[2] > cam.znear);
+    st.clampx = st.clampy = false;
+    if (st.culled) return;
+    float tz = st.t[2];
+    float xz = st.t[0] / tz, yz = st.t[1] / tz;
+    float Wi = (float)cam.width, Hi = (float)cam.height;
+    float xlo = (-kFrustumGuard * Wi - cam.cx) / cam.fx, xhi = ((1.f + kFrustumGuard) * Wi - cam.cx) / cam.fx;
+    float ylo = (-kFrustumGuard * Hi - cam.cy) / cam.fy, yhi = ((1.f + kFrustumGuard) * Hi - cam.cy) / cam.fy;
+    st.xzc = clampf(xz, xlo, xhi);
+    st.yzc = clampf(yz, ylo, yhi);
+    st.clampx = st.xzc != xz;
+    st.clampy = st.yzc != yz;
+    float J00 = cam.fx / tz, J02 = -cam.fx * st.xzc / tz;
+    float J11 = cam.fy / tz, J12 = -cam.fy * st.yzc / tz;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        st.T0[k] = J00 * Wm[k] + J02 * Wm[6 + k];
+        st.T1[k] = J11 * Wm[3 + k] + J12 * Wm[6 + k];
+    }
+    float ST0[3], ST1[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        ST0[i] = st.Sig[i][0] * st.T0[0] + st.Sig[i][1] * st.T0[1] + st.Sig[i][2] * st.T0[2];
+        ST1[i] = st.Sig[i][0] * st.T1[0] + st.Sig[i][1] * st.T1[1] + st.Sig[i][2] * st.T1[2];
+    }
+    st.a = st.T0[0] * ST0[0] + st.T0[1] * ST0[1] + st.T0[2] * ST0[2] + kDilation;
+    st.b = st.T0[0] * ST1[0] + st.T0[1] * ST1[1] + st.T0[2] * ST1[2];
+    st.c = st.T1[0] * ST1[0] + st.T1[1] * ST1[1] + st.T1[2] * ST1[2] + kDilation;
+    st.det = st.a * st.c - st.b * st.b;
+    if (!(st.det > 0.f)) st.culled = true;
+}
+
+__global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
+                                 const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
+                                 const int64_t *__restrict__ view_item_offset, int vb, int TX, int TY, int tw, int th,
+                                 float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
+                                 float *__restrict__ depth, int4 *__restrict__ rect, int32_t *__restrict__ radius,
+                                 uint32_t *__restrict__ touched, uint32_t *__restrict__ keyA,
+                                 uint32_t *__restrict__ valA)
+{
+    const int v = vb + blockIdx.y;
+    const int scene = view_scene ? view_scene[v] : 0;
+    const int64_t g0 = scene_offset[scene];
+    const int64_t ns = scene_offset[scene + 1] - g0;
+    const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gl >= ns) return;
+    const int64_t g = g0 + gl;
+    const int64_t item = view_item_offset[v] - view_item_offset[vb] + gl;
+    const vbm_camera cam = cams[v];
+    ProjState st;
+    project_state(P, stride, g, cam, st);
+    float4 cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
+    col[item] = cg;
+    depth[item] = st.t[2];
+    uint32_t ntouch = 0;
+    int4 rc = make_int4(0, 0, 0, 0);
+    int r_int = 0;
+    if (!st.culled) {
+        float inv_det = 1.0f / st.det;
+        float A = st.c * inv_det, B = -st.b * inv_det, C = st.a * inv_det;
+        float mid = 0.5f * (st.a + st.c);
+        float disc = mid * mid - st.det;
+        float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
+        // Bounded so the integer rectangle arithmetic cannot overflow; any
+        // radius above 2^24 already spans every image narrower than 6.7M px.
+        float r = fminf(ceilf(kRadiusSigmas * sqrtf(lam1)), 16777216.0f);
+        float u = cam.fx * (st.t[0] / st.t[2]) + cam.cx;
+        float vv = cam.fy * (st.t[1] / st.t[2]) + cam.cy;
+        geo[item] = make_float4(u, vv, A, B);
+        conic_c[item] = C;
+        r_int = (int)r;
+        int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
+        int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
+        rc.x = min(max(floordiv_i(fu - r_int, tw), 0), TX);
+        rc.z = min(max(floordiv_i(fu + r_int, tw) + 1, 0), TX);
+        rc.y = min(max(floordiv_i(fv - r_int, th), 0), TY);
+        rc.w = min(max(floordiv_i(fv + r_int, th) + 1, 0), TY);
+        ntouch = (uint32_t)((rc.z - rc.x) * (rc.w - rc.y));
+    } else {
+        geo[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        conic_c[item] = 0.f;
+    }
+    rect[item] = rc;
+    radius[item] = r_int;
+    touched[item] = ntouch;
+    keyA[item] = ntouch ? __float_as_uint(st.t[2]) : 0xFFFFFFFFu;
+    valA[item] = (uint32_t)item;
+}
+
+// Chain rule from the per-item splat gradient (du, dv, dA, dB, dC, dopacity,
+// dr, dg, db) to the 14 parameters, summed over the views of the call that
+// see Gaussian g.  Mirrors the forward step by step (see the header comment).
+__global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
+                                 const int64_t *__restrict__ scene_offset, int n_scenes,
+                                 const int32_t *__restrict__ scene_view_ptr, const int32_t *__restrict__ scene_views,
+                                 const int64_t *__restrict__ view_item_offset, int vb, int vc, int64_t n_items,
+                                 const float *__restrict__ gs, float *__restrict__ grad, int accumulate,
+                                 int64_t g_begin, int64_t g_end)
+{
+    const int64_t g = g_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= g_end) return;
+    int lo = 0, hi = n_scenes - 1;  // scene of g: last s with scene_offset[s] <= g
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (scene_offset[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const int scene = lo;
+    const int64_t gl = g - scene_offset[scene];
+    float acc[14];
+#pragma unroll
+    for (int k = 0; k < 14; k++) acc[k] = 0.f;
+    bool seen = false;
+    for (int e = scene_view_ptr[scene]; e < scene_view_ptr[scene + 1]; e++) {
+        const int v = scene_views[e];
+        if (v < vb || v >= vb + vc) continue;
+        seen = true;
+        const int64_t item = view_item_offset[v] - view_item_offset[vb] + gl;
+        float g9[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) g9[k] = gs[k * n_items + item];
+        const vbm_camera cam = cams[v];
+        ProjState st;
+        project_state(P, stride, g, cam, st);
+        acc[10] += g9[5] * st.opac * (1.f - st.opac);
+        acc[11] += g9[6];
+        acc[12] += g9[7];
+        acc[13] += g9[8];
+        if (st.culled) continue;
+        const float *Wm = cam.R;
+        float a = st.a, b = st.b, c = st.c, D = st.det;
+        float iD2 = 1.0f / (D * D);
+        float dA = g9[2], dB = g9[3], dC = g9[4];
+        float dLa = (dA * (-c * c) + dB * (b * c) + dC * (-b * b)) * iD2;
+        float dLb = (dA * (2.f * b * c) + dB * (-(a * c + b * b)) + dC * (2.f * a * b)) * iD2;
+        float dLc = (dA * (-b * b) + dB * (a * b) + dC * (-a * a)) * iD2;
+        float ST0[3], ST1[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            ST0[i] = st.Sig[i][0] * st.T0[0] + st.Sig[i][1] * st.T0[1] + st.Sig[i][2] * st.T0[2];
+            ST1[i] = st.Sig[i][0] * st.T1[0] + st.Sig[i][1] * st.T1[1] + st.Sig[i][2] * st.T1[2];
+        }
+        float dT0[3], dT1[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            dT0[i] = 2.f * dLa * ST0[i] + dLb * ST1[i];
+            dT1[i] = dLb * ST0[i] + 2.f * dLc * ST1[i];
+        }
+        float dJ00 = dT0[0] * Wm[0] + dT0[1] * Wm[1] + dT0[2] * Wm[2];
+        float dJ02 = dT0[0] * Wm[6] + dT0[1] * Wm[7] + dT0[2] * Wm[8];
+        float dJ11 = dT1[0] * Wm[3] + dT1[1] * Wm[4] + dT1[2] * Wm[5];
+        float dJ12 = dT1[0] * Wm[6] + dT1[1] * Wm[7] + dT1[2] * Wm[8];
+        float tx = st.t[0], ty = st.t[1], tz = st.t[2];
+        float itz = 1.0f / tz, itz2 = itz * itz;
+        float dxc_dtx = st.clampx ? 0.f : itz, dxc_dtz = st.clampx ? 0.f : -tx * itz2;
+        float dyc_dty = st.clampy ? 0.f : itz, dyc_dtz = st.clampy ? 0.f : -ty * itz2;
+        float fx = cam.fx, fy = cam.fy;
+        float dt0 = g9[0] * fx * itz + dJ02 * (-fx * itz) * dxc_dtx;
+        float dt1 = g9[1] * fy * itz + dJ12 * (-fy * itz) * dyc_dty;
+        float dt2 = g9[0] * (-fx * tx * itz2) + g9[1] * (-fy * ty * itz2) + dJ00 * (-fx * itz2) +
+                    dJ11 * (-fy * itz2) + dJ02 * (fx * st.xzc * itz2 - fx * itz * dxc_dtz) +
+                    dJ12 * (fy * st.yzc * itz2 - fy * itz * dyc_dtz);
+#pragma unroll
+        for (int k = 0; k < 3; k++) acc[k] += Wm[k] * dt0 + Wm[3 + k] * dt1 + Wm[6 + k] * dt2;
+        // dL/dSigma over all nine entries, then Sigma = M M^T with M = R diag(s)
+        float GS[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                GS[i][j] = dLa * st.T0[i] * st.T0[j] + dLb * st.T0[i] * st.T1[j] + dLc * st.T1[i] * st.T1[j];
+        float dR[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            float ds = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                float dM = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; j++) dM += (GS[i][j] + GS[j][i]) * st.R[j][k] * st.s[k];
+                ds += dM * st.R[i][k];
+                dR[i][k] = dM * st.s[k];
+            }
+            acc[3 + k] += ds * st.s[k];
+        }
+        float w = st.qn[0], x = st.qn[1], y = st.qn[2], z = st.qn[3];
+        float dq[4];
+        dq[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+        dq[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                       z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+        dq[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                       w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+        dq[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                       y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+        float dot = dq[0] * st.qn[0] + dq[1] * st.qn[1] + dq[2] * st.qn[2] + dq[3] * st.qn[3];
+        float iq = 1.0f / st.qnorm;
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc[6 + k] += (dq[k] - st.qn[k] * dot) * iq;
+    }
+    if (!seen) return;
+#pragma unroll
+    for (int k = 0; k < 14; k++) {
+        float *dst = grad + k * stride + g;
+        *dst = accumulate ? *dst + acc[k] : acc[k];
+    }
+}
+
+}  // namespace
+
+vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, const vbm_camera *cams, int vb, int vc,
+                          cudaStream_t st)
+{
+    dim3 block(256);
+    dim3 grid((unsigned)((p->max_scene + 255) / 256), (unsigned)vc);
+    if (p->max_scene == 0) return VBM_OK;
+    k_preprocess_fwd<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
+                                              p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
+                                              p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
+                                              p->desc.tile_h, p->geo, p->col, p->conic_c, p->depth, p->rect,
+                                              p->radius, p->touched, p->keyA[0], p->valA[0]);
+    VBM_LAUNCH("preprocess_fwd");
+    note_launches(1);
+    return VBM_OK;
+}
+
+vbm_status preprocess_bwd(vbm_plan *p, const float *params, int64_t stride, const vbm_camera *cams, int vb, int vc,
+                          float *grad, int accumulate, cudaStream_t st)
+{
+    // Gaussians of the scenes the call's views render form one column range
+    // when the views are consecutive; bound it by the scenes' extent.
+    int64_t g_begin = INT64_MAX, g_end = 0;
+    for (int v = vb; v < vb + vc; v++) {
+        int s = p->desc.n_scenes > 1 ? p->view_scene[v] : 0;
+        g_begin = std::min(g_begin, p->scene_offset[s]);
+        g_end = std::max(g_end, p->scene_offset[s + 1]);
+    }
+    if (g_end <= g_begin) return VBM_OK;
+    int64_t n = g_end - g_begin;
+    k_preprocess_bwd<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+        params, stride, cams, p->d_scene_offset, p->desc.n_scenes, p->d_scene_view_ptr, p->d_scene_views,
+        p->d_view_item_offset, vb, vc, p->last_items, p->g_splat, grad, accumulate, g_begin, g_end);
+    VBM_LAUNCH("preprocess_bwd");
+    note_launches(1);
+    return VBM_OK;
+}
+
+}  // namespace vbm

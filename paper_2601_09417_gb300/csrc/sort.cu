@@ -1,0 +1,373 @@
+// Tile binning with a depth order: scans, a stable LSD radix sort, pair
+// emission and tile ranges.
+//
+// The order the rasteriser needs is "by tile, then by depth, ties by item
+// index".  Instead of sorting every (tile, Gaussian) pair on a 64-bit
+// (tile | depth) key, the items are first sorted by their 32-bit depth key
+// (N x V elements), the pairs are then emitted in that depth order, and a
+// stable sort on the tile id alone (ceil(log2 #tiles) bits, usually two 8-bit
+// passes) groups them by tile.  Stability carries the depth order (and the
+// item-index tie break of the first stable sort) into every tile's list, so
+// the result equals the 64-bit sort while the large pair array is sorted on
+// ~16 key bits instead of ~45 and each pair is 8 bytes instead of 12.
+//
+// Every kernel here runs on a fixed grid (a multiple of the SM count) and
+// reads element counts from device memory, so a whole step can be captured
+// in a CUDA graph without knowing the pair count on the host.  No kernel
+// waits on another block: the radix sort is reduce-then-scan (upsweep
+// histograms, one scan block, downsweep scatter).
+#include "vbm_internal.h"
+
+namespace vbm {
+namespace {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 8;                      // elements per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__device__ __forceinline__ int64_t chunk_of(int64_t n, int blocks)
+{
+    int64_t c = (n + blocks - 1) / blocks;
+    return (c + kSortTile - 1) / kSortTile * kSortTile;
+}
+
+// Per-block digit histogram of keys in the block's chunk: hist[d * blocks + b].
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                                const int64_t *__restrict__ d_n, int shift,
+                                                                uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t h[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t n = *d_n;
+    const int64_t chunk = chunk_of(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+}
+
+// Exclusive scan (in place) of the digit-major histogram: one block.
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int total)
+{
+    __shared__ uint32_t sums[1024];
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int beg = threadIdx.x * per;
+    const int end = min(total, beg + per);
+    uint32_t s = 0;
+    for (int i = beg; i < end; i++) s += hist[i];
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : 0u;
+        __syncthreads();
+        sums[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? sums[threadIdx.x - 1] : 0u;
+    for (int i = beg; i < end; i++) {
+        uint32_t v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter of the block's chunk, tile by tile.  Within a tile, warp w
+// owns elements [w * 32 * kSortItems, (w + 1) * 32 * kSortItems) and walks
+// them 32 at a time; the rank of an element among equal digits is
+// (elements of that digit in earlier tiles of this block) + (in earlier
+// warps of this tile) + (earlier in this warp), found with __match_any_sync.
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
+                                                                  const uint32_t *__restrict__ vals_in,
+                                                                  uint32_t *__restrict__ keys_out,
+                                                                  uint32_t *__restrict__ vals_out,
+                                                                  const int64_t *__restrict__ d_n, int shift,
+                                                                  const uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t run[kRadix];
+    __shared__ uint32_t tile_total[kRadix];
+    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    const int64_t n = *d_n;
+    const int64_t chunk = chunk_of(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] = hist[(int64_t)d * gridDim.x + blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int64_t tbase = beg; tbase < end; tbase += kSortTile) {
+        for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) wcnt[w][d] = 0;
+        __syncthreads();
+        uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+        const int64_t wbase = tbase + (int64_t)warp * 32 * kSortItems;
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int64_t i = wbase + it * 32 + lane;
+            const bool valid = i < end;
+            k[it] = valid ? keys_in[i] : 0u;
+            v[it] = valid ? vals_in[i] : 0u;
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            rank[it] = 0;
+            if (valid) {
+                const uint32_t d = (k[it] >> shift) & (kRadix - 1);
+                const uint32_t peers = __match_any_sync(vmask, d);
+                const int leader = __ffs(peers) - 1;
+                const uint32_t prior = wcnt[warp][d];
+                rank[it] = prior + __popc(peers & lt_mask);
+                __syncwarp(vmask);
+                if (lane == leader) wcnt[warp][d] = prior + __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = s;
+                s += c;
+            }
+            tile_total[d] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int64_t i = wbase + it * 32 + lane;
+            if (i < end) {
+                const uint32_t d = (k[it] >> shift) & (kRadix - 1);
+                const uint32_t pos = run[d] + wcnt[warp][d] + rank[it];
+                keys_out[pos] = k[it];
+                vals_out[pos] = v[it];
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] += tile_total[d];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ gather scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+
+__device__ __forceinline__ int64_t scan_chunk(int64_t n, int blocks)
+{
+    const int64_t t = kScanThreads * kScanItems;
+    int64_t c = (n + blocks - 1) / blocks;
+    return (c + t - 1) / t * t;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ counts,
+                                                              const uint32_t *__restrict__ idx, int64_t n,
+                                                              int64_t *__restrict__ block_sums)
+{
+    __shared__ int64_t red[kScanThreads];
+    const int64_t chunk = scan_chunk(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    int64_t s = 0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) s += counts[idx[i]];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < (unsigned)off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+}
+
+__global__ void k_scan_top(int64_t *__restrict__ block_sums, int blocks)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int b = 0; b < blocks; b++) {
+            int64_t v = block_sums[b];
+            block_sums[b] = run;
+            run += v;
+        }
+        block_sums[blocks] = run;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ counts,
+                                                            const uint32_t *__restrict__ idx, int64_t n,
+                                                            const int64_t *__restrict__ block_sums,
+                                                            int64_t *__restrict__ out)
+{
+    __shared__ int64_t warp_sums[kScanThreads / 32];
+    __shared__ int64_t carry;
+    const int64_t chunk = scan_chunk(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    if (threadIdx.x == 0) carry = block_sums[blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t tb = beg; tb < end; tb += kScanThreads * kScanItems) {
+        int64_t v[kScanItems];
+        int64_t local = 0;
+#pragma unroll
+        for (int it = 0; it < kScanItems; it++) {
+            const int64_t i = tb + (int64_t)threadIdx.x * kScanItems + it;
+            v[it] = i < end ? (int64_t)counts[idx[i]] : 0;
+            local += v[it];
+        }
+        int64_t incl = local;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        int64_t wpre = 0, tot = 0;
+        for (int w = 0; w < kScanThreads / 32; w++) {
+            if (w < warp) wpre += warp_sums[w];
+            tot += warp_sums[w];
+        }
+        int64_t run = carry + wpre + incl - local;
+#pragma unroll
+        for (int it = 0; it < kScanItems; it++) {
+            const int64_t i = tb + (int64_t)threadIdx.x * kScanItems + it;
+            if (i < end) out[i] = run;
+            run += v[it];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = block_sums[gridDim.x];
+}
+
+// ------------------------------------------------------------- emission
+
+__global__ void k_set_i64(int64_t *dst, int64_t value)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = value;
+}
+
+// Pairs for the items in depth order: item sorted[s] owns [offsets[s],
+// offsets[s+1]) and writes one (tile, item) pair per tile of its rectangle,
+// row-major.  If the total exceeds the capacity nothing is emitted, the pair
+// count is set to 0 and the plan's status records the required size.
+__global__ void k_emit_pairs(const uint32_t *__restrict__ sorted, const int64_t *__restrict__ offsets, int64_t n,
+                             const int4 *__restrict__ rect, const int64_t *__restrict__ view_item_offset, int vb,
+                             int vc, int TX, int TY, int64_t capacity, uint32_t *__restrict__ pair_tile,
+                             uint32_t *__restrict__ pair_item, int64_t *__restrict__ n_pairs,
+                             int64_t *__restrict__ status)
+{
+    const int64_t total = offsets[n];
+    const bool overflow = total > capacity;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *n_pairs = overflow ? 0 : total;
+        if (overflow) {
+            atomicOr((unsigned long long *)&status[0], (unsigned long long)kStatusCapacity);
+            atomicMax((unsigned long long *)&status[1], (unsigned long long)total);
+        }
+    }
+    if (overflow) return;
+    const int64_t base_item = view_item_offset[vb];
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t beg = offsets[s];
+        if (offsets[s + 1] == beg) continue;
+        const uint32_t item = sorted[s];
+        int lo = 0, hi = vc - 1;   // view of the item: last v with offset <= item
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (view_item_offset[vb + mid] - base_item <= (int64_t)item) lo = mid; else hi = mid - 1;
+        }
+        const int4 rc = rect[item];
+        const uint32_t tile0 = (uint32_t)lo * (uint32_t)(TX * TY);
+        int64_t o = beg;
+        for (int ty = rc.y; ty < rc.w; ty++)
+            for (int tx = rc.x; tx < rc.z; tx++) {
+                pair_tile[o] = tile0 + (uint32_t)(ty * TX + tx);
+                pair_item[o] = item;
+                o++;
+            }
+    }
+}
+
+__global__ void k_tile_ranges(const uint32_t *__restrict__ tile, const int64_t *__restrict__ n_pairs,
+                              int2 *__restrict__ ranges)
+{
+    const int64_t n = *n_pairs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = tile[i];
+        if (i == 0 || tile[i - 1] != t) ranges[t].x = (int)i;
+        if (i == n - 1 || tile[i + 1] != t) ranges[t].y = (int)(i + 1);
+    }
+}
+
+int ceil_log2(int64_t x)
+{
+    int b = 0;
+    while ((int64_t(1) << b) < x) b++;
+    return b;
+}
+
+}  // namespace
+
+size_t radix_sort_hist_words(int blocks) { return (size_t)kRadix * blocks; }
+
+int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,
+                     const SortScratch &s, cudaStream_t st)
+{
+    int cur = 0;
+    if (n_max <= 0) return cur;
+    for (int shift = 0; shift < bits; shift += kRadixBits) {
+        k_radix_upsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], d_n, shift, s.hist);
+        k_radix_scan<<<1, 1024, 0, st>>>(s.hist, kRadix * s.blocks);
+        k_radix_downsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], d_n,
+                                                             shift, s.hist);
+        cur = 1 - cur;
+        note_launches(3);
+    }
+    return cur;
+}
+
+void gather_scan(const uint32_t *counts, const uint32_t *idx, int64_t n, int64_t *out, const ScanScratch &s,
+                 cudaStream_t st)
+{
+    k_scan_reduce<<<s.blocks, kScanThreads, 0, st>>>(counts, idx, n, s.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(s.block_sums, s.blocks);
+    k_scan_down<<<s.blocks, kScanThreads, 0, st>>>(counts, idx, n, s.block_sums, out);
+    note_launches(3);
+}
+
+vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
+{
+    const int64_t n_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
+    const int64_t n_tiles = (int64_t)vc * p->TX * p->TY;
+    k_set_i64<<<1, 32, 0, st>>>(p->d_n_items, n_items);
+    note_launches(1);
+    // 1. depth order of the items (stable: ties keep the item order)
+    const int a = radix_sort_pairs(p->keyA, p->valA, p->d_n_items, n_items, 32, p->sort_scratch, st);
+    // 2. pair offsets in depth order
+    gather_scan(p->touched, p->valA[a], n_items, p->offsets, p->scan_scratch, st);
+    // 3. emit pairs
+    const int grid = num_sms() * 4;
+    k_emit_pairs<<<grid, 256, 0, st>>>(p->valA[a], p->offsets, n_items, p->rect, p->d_view_item_offset, vb, vc,
+                                       p->TX, p->TY, p->desc.pair_capacity, p->pair_tile[0], p->pair_item[0],
+                                       p->d_n_pairs, p->d_status);
+    VBM_LAUNCH("emit_pairs");
+    note_launches(1);
+    // 4. stable sort of the pairs by tile
+    p->pair_buf = radix_sort_pairs(p->pair_tile, p->pair_item, p->d_n_pairs, p->desc.pair_capacity,
+                                   ceil_log2(n_tiles), p->sort_scratch, st);
+    // 5. tile ranges
+    VBM_CUDA(cudaMemsetAsync(p->ranges, 0, sizeof(int2) * n_tiles, st));
+    k_tile_ranges<<<grid, 256, 0, st>>>(p->pair_tile[p->pair_buf], p->d_n_pairs, p->ranges);
+    VBM_LAUNCH("tile_ranges");
+    note_launches(1);
+    return VBM_OK;
+}
+
+}  // namespace vbm

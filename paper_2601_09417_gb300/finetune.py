@@ -1,0 +1,109 @@
+"""Image-space fine-tuning of the Gaussians (Sec. 4.4), one step = render all views,
+L1 + D-SSIM loss against the targets, backward to every parameter, Adam.
+
+Two forms of the same step:
+  * plain   -- one view per launch sequence: for each view, its forward,
+               its loss term and its backward (accumulating the gradient),
+               then one Adam update;
+  * batched -- every view (and every scene of an uneven batch) in one
+               launch per kernel, the whole step captured once as a CUDA
+               graph and replayed.
+Both run only the library's kernels; this module allocates the buffers,
+sequences the C-ABI calls and owns the graph.
+"""
+
+import numpy as np
+import torch
+
+from . import vbm
+
+
+def default_lrs(extent):
+    """Per-row-group learning rates: mean, log-scale, quaternion, opacity, colour."""
+    return [1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3]
+
+
+class FineTuner:
+    def __init__(self, params, cam_records, targets, scene_offset=None, view_scene=None, tile=(16, 16),
+                 pair_capacity=None, lrs=None, lam=0.2, bg=(0.0, 0.0, 0.0), extent=None, device="cuda"):
+        self.device = torch.device(device)
+        self.params = params
+        self.n = params.shape[1] if scene_offset is None else int(scene_offset[-1])
+        self.V, _, self.H, self.W = targets.shape
+        self.targets = targets
+        self.cams = vbm.cameras_to_device(cam_records, self.device)
+        self.bg = tuple(float(b) for b in bg)
+        self.lam = float(lam)
+        self.scene_offset = np.asarray([0, self.n] if scene_offset is None else scene_offset, dtype=np.int64)
+        self.view_scene = view_scene
+        if pair_capacity is None:
+            pair_capacity = max(1 << 20, 64 * self.n * self.V)
+        self.plan = vbm.Plan(self.scene_offset, self.V, self.W, self.H, view_scene=view_scene, tile_w=tile[0],
+                             tile_h=tile[1], pair_capacity=min(pair_capacity, (1 << 31) - 1))
+        self.img = torch.zeros((self.V, 3, self.H, self.W), device=self.device)
+        self.dimg = torch.zeros_like(self.img)
+        self.grad = torch.zeros_like(params)
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.nonfinite = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.ws = vbm.loss_workspace(self.V, self.H, self.W, self.device)
+        self.scale = 1.0 / (self.V * 3 * self.H * self.W)
+        ext = extent if extent is not None else 1.0
+        self.lrs = list(lrs) if lrs is not None else default_lrs(ext)
+        self.graph = None
+
+    # -------------------------------------------------------------- steps
+    def step_plain(self):
+        """One view per launch sequence, then Adam (no graph)."""
+        for v in range(self.V):
+            self.plan.forward(self.params, self.cams, self.img, view_begin=v, view_count=1, bg=self.bg)
+            vbm.loss(self.img[v], self.targets[v], 1, self.H, self.W, self.lam, self.scale, self.loss, self.dimg[v],
+                     self.ws, accumulate=v > 0)
+            self.plan.backward(self.params, self.cams, self.dimg, self.grad, view_begin=v, view_count=1,
+                               bg=self.bg, accumulate=v > 0)
+        vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
+                 nonfinite=self.nonfinite)
+
+    def step_batched(self):
+        """All views in one launch per kernel, then Adam."""
+        self.plan.forward(self.params, self.cams, self.img, bg=self.bg)
+        vbm.loss(self.img, self.targets, self.V, self.H, self.W, self.lam, self.scale, self.loss, self.dimg,
+                 self.ws)
+        self.plan.backward(self.params, self.cams, self.dimg, self.grad, bg=self.bg)
+        vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
+                 nonfinite=self.nonfinite)
+
+    def capture(self):
+        """Capture step_batched as a CUDA graph (run it once first on a side stream)."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            snapshot = [t.clone() for t in (self.params, self.m, self.v, self.step_count)]
+            self.step_batched()
+            for dst, src in zip((self.params, self.m, self.v, self.step_count), snapshot):
+                dst.copy_(src)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step_batched()
+        return self.graph
+
+    def step_graph(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def step_host(self, host_targets, host_loss):
+        """End-to-end step through host memory: copy this step's targets from pinned host
+        memory, run the captured step, read the loss back to pinned host memory."""
+        self.targets.copy_(host_targets, non_blocking=True)
+        self.step_graph()
+        host_loss.copy_(self.loss, non_blocking=True)
+
+    def check(self):
+        """(ok, pairs_needed, nonfinite): synchronises."""
+        ok, need = self.plan.check()
+        return ok, need, int(self.nonfinite.item())

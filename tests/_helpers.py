@@ -1,0 +1,70 @@
+"""Shared helpers of the GPU parity tests: seeded scenes and device-buffer readers."""
+
+import numpy as np
+
+from vbm_inputs import gaussians_in_view, orbit_cameras
+from vbm_inputs.cameras import camera_array, cameras_as_float32
+
+def read_device(ptr, shape, dtype):
+    """Copy device memory at a raw pointer into a numpy array."""
+    from paper_2601_09417_gb300 import vbm
+    if int(np.prod(shape)) == 0:
+        return np.zeros(shape, dtype=dtype)
+    return vbm.device_tensor(ptr, shape, dtype).cpu().numpy().copy()
+
+
+def scene(seed=0, n=2000, G=32, V=2, W=100, H=76, **kw):
+    """Random Gaussians (float32) inside a G^3 box and an orbit of V cameras."""
+    P = gaussians_in_view(n, G, seed=seed, **kw).astype(np.float32)
+    cams = orbit_cameras((G, G, G), V, W, H)
+    return P, cams, cameras_as_float32(cams)
+
+
+def to_device(P, cams, device="cuda"):
+    import torch
+    from paper_2601_09417_gb300 import vbm
+    return torch.from_numpy(np.ascontiguousarray(P)).to(device), vbm.cameras_to_device(camera_array(cams), device)
+
+
+def plan_state(plan, n_views):
+    """Numpy copies of a plan's buffers after a forward (and backward) call."""
+    b = plan.buffers()
+    n = b.n_items
+    st = dict(n_items=n)
+    st["geo"] = read_device(b.geo, (n, 4), np.float32)
+    st["col"] = read_device(b.col, (n, 4), np.float32)
+    st["conic_c"] = read_device(b.conic_c, (n,), np.float32)
+    st["depth"] = read_device(b.depth, (n,), np.float32)
+    st["rect"] = read_device(b.rect, (n, 4), np.int32)
+    st["radius"] = read_device(b.radius, (n,), np.int32)
+    n_pairs = int(read_device(b.n_pairs, (1,), np.int64)[0])
+    st["n_pairs"] = n_pairs
+    st["pair_tile"] = read_device(b.pair_tile, (n_pairs,), np.uint32)
+    st["pair_item"] = read_device(b.pair_item, (n_pairs,), np.uint32)
+    TX = (plan.width + plan.tile_w - 1) // plan.tile_w
+    TY = (plan.height + plan.tile_h - 1) // plan.tile_h
+    st["ranges"] = read_device(b.ranges, (n_views * TX * TY, 2), np.int32)
+    if b.T_final:
+        st["T_final"] = read_device(b.T_final, (plan.n_views, plan.height, plan.width), np.float32)
+        st["n_contrib"] = read_device(b.n_contrib, (plan.n_views, plan.height, plan.width), np.int32)
+    st["g_splat"] = read_device(b.g_splat, (9, n), np.float32)
+    return st
+
+
+def gpu_splats_as_oracle(st):
+    """GPU per-item splat records as the oracle's (n, 6) u v A B C opacity and (n, 3) colour."""
+    g = st["geo"].astype(np.float64)
+    splat = np.stack([g[:, 0], g[:, 1], g[:, 2], g[:, 3], st["conic_c"].astype(np.float64),
+                      st["col"][:, 3].astype(np.float64)], axis=1)
+    return splat, st["col"][:, :3].astype(np.float64)
+
+
+def rel_group_error(g, ref):
+    """(norm-wise relative error, worst element error / (|ref| + rms(ref)))."""
+    g = np.asarray(g, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    nrm = np.linalg.norm(ref)
+    if nrm == 0:
+        return float(np.linalg.norm(g)), float(np.abs(g).max(initial=0.0))
+    rms = np.sqrt(np.mean(ref * ref))
+    return float(np.linalg.norm(g - ref) / nrm), float((np.abs(g - ref) / (np.abs(ref) + rms)).max())

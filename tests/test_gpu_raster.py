@@ -1,0 +1,262 @@
+"""GPU parity of the splatting forward/backward (Sec. 4.4) against the FP64 oracle.
+
+Bars (from the method's accuracy targets):
+  * tile keys, pair order and ranges bit-exact given the GPU's projected depths;
+  * images within 1e-4 max-abs per channel, excluding pixels where an FP32 vs
+    FP64 difference can flip a compositing cut-off (relative margin to
+    alpha = 1/255 or T = 1e-4 below 1e-5); flagged pixels must stay rare;
+  * gradients within 1e-3 relative (group norm) and
+    |g - g_ref| <= 1e-3 (|g_ref| + rms(g_ref)) element-wise.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from _helpers import gpu_splats_as_oracle, plan_state, rel_group_error, scene, to_device
+from oracle import raster as oraster
+from oracle.raster import PJ
+
+pytestmark = pytest.mark.gpu
+
+
+def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0)):
+    params, cams_dev = to_device(P, cams)
+    V = len(cams)
+    so = [0, P.shape[1]] if scene_offset is None else scene_offset
+    plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap)
+    img = torch.zeros((V, 3, H, W), device="cuda")
+    alpha = torch.zeros((V, H, W), device="cuda")
+    plan.forward(params, cams_dev, img, alpha, bg=bg)
+    torch.cuda.synchronize()
+    return plan, params, cams_dev, img.cpu().numpy(), alpha.cpu().numpy()
+
+
+def _tiles(W, H, tile):
+    return (W + tile[0] - 1) // tile[0], (H + tile[1] - 1) // tile[1]
+
+
+def test_preprocess_matches_oracle(cuda_lib):
+    P, cams, cams32 = scene(seed=1, n=3000, V=3, W=100, H=76)
+    plan, *_ = _forward(cuda_lib, P, cams, 100, 76)
+    st = plan_state(plan, 3)
+    n = P.shape[1]
+    P64 = P.astype(np.float64)
+    flagged = 0
+    for v in range(3):
+        ref = oraster.project(P64, cams32[v], np.arange(n), 16, 16)
+        sl = slice(v * n, (v + 1) * n)
+        assert np.allclose(st["depth"][sl], ref[:, PJ["DEPTH"]], rtol=1e-6, atol=1e-5)
+        assert np.allclose(st["col"][sl, 3], ref[:, PJ["OPAC"]], atol=2e-7)
+        assert np.array_equal(st["col"][sl, :3], P[11:14].T)
+        vis = ref[:, PJ["TOUCHED"]] > 0
+        culled = ref[:, PJ["RADIUS"]] == 0
+        safe = ((ref[:, PJ["M_RADIUS"]] > 1e-3) | culled) & (ref[:, PJ["M_RECT"]] > 1e-3) \
+            & (ref[:, PJ["M_CULL"]] > 1e-3)
+        flagged += int((~safe).sum())
+        g = st["geo"][sl]
+        scale_uv = np.abs(ref[:, [PJ["U"], PJ["V"]]]) + 100.0
+        assert (np.abs(g[vis, 0:2] - ref[vis][:, [PJ["U"], PJ["V"]]]) < 1e-6 * scale_uv[vis]).all()
+        conic = np.stack([g[:, 2], g[:, 3], st["conic_c"][sl]], axis=1)
+        cref = ref[:, [PJ["A"], PJ["B"], PJ["C"]]]
+        cs = np.abs(cref[vis]).max(axis=1, keepdims=True)
+        assert (np.abs(conic[vis] - cref[vis]) <= 2e-5 * cs).all()
+        assert np.array_equal(st["radius"][sl][safe], ref[safe, PJ["RADIUS"]].astype(np.int32))
+        rref = ref[:, [PJ["X0"], PJ["Y0"], PJ["X1"], PJ["Y1"]]].astype(np.int32)
+        assert np.array_equal(st["rect"][sl][safe], rref[safe])
+    assert flagged < 0.01 * 3 * n
+
+
+def test_binning_bit_exact_given_gpu_depths(cuda_lib):
+    P, cams, cams32 = scene(seed=2, n=2500, V=3, W=100, H=76)
+    plan, *_ = _forward(cuda_lib, P, cams, 100, 76)
+    st = plan_state(plan, 3)
+    n = P.shape[1]
+    TX, TY = _tiles(100, 76, (16, 16))
+    view_of = np.repeat(np.arange(3, dtype=np.int32), n)
+    tiles, items, ranges = oraster.bin_sort(view_of, st["rect"], st["depth"].astype(np.float64), TX, TY, 3)
+    assert st["n_pairs"] == tiles.size > 0
+    assert np.array_equal(st["pair_tile"].astype(np.int64), tiles)
+    assert np.array_equal(st["pair_item"].astype(np.int64), items.astype(np.int64))
+    assert np.array_equal(st["ranges"], ranges)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8)])
+def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile):
+    W, H = 100, 76
+    P, cams, cams32 = scene(seed=3, n=2500, V=2, W=W, H=H)
+    bg = (0.1, 0.2, 0.05)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg)
+    st = plan_state(plan, 2)
+    splat, color = gpu_splats_as_oracle(st)
+    ref = oraster.render(2, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32), splat, color,
+                         np.array(bg))
+    good = ref["margin"] > 1e-5
+    assert good.mean() > 0.99, good.mean()
+    err = np.abs(img - ref["img"]).transpose(1, 0, 2, 3)[:, good]
+    assert err.max() <= 1e-4, err.max()
+    assert np.abs(alpha - (1 - ref["T_final"]))[good].max() <= 1e-4
+    assert np.array_equal(st["n_contrib"][good], ref["n_contrib"][good])
+    assert np.abs(st["T_final"] - ref["T_final"])[good].max() <= 1e-4
+    assert img.max() > 0.05      # the scene is not empty
+
+
+def _flag_pixels_of_unsafe_items(ref_fwd, gpu_rect, n_views, W, H, tile, n):
+    """Pixels of tiles whose lists differ between the FP32 and FP64 projections: the tiles in
+    the symmetric difference of an item's two rectangles (a radius, rectangle or culling
+    decision that FP32 rounding flipped)."""
+    pj = ref_fwd["proj"]
+    rref = pj[:, [PJ["X0"], PJ["Y0"], PJ["X1"], PJ["Y1"]]].astype(np.int32)
+    TX, TY = (W + tile[0] - 1) // tile[0], (H + tile[1] - 1) // tile[1]
+    tiles = np.zeros((n_views, TY, TX), dtype=bool)
+    for it in np.nonzero(np.any(rref != gpu_rect, axis=1))[0]:
+        a = np.zeros((TY, TX), dtype=bool)
+        b = np.zeros((TY, TX), dtype=bool)
+        a[rref[it, 1]:rref[it, 3], rref[it, 0]:rref[it, 2]] = True
+        b[gpu_rect[it, 1]:gpu_rect[it, 3], gpu_rect[it, 0]:gpu_rect[it, 2]] = True
+        tiles[it // n] |= a ^ b
+    mask = np.repeat(np.repeat(tiles, tile[1], axis=1), tile[0], axis=2)[:, :H, :W]
+    return mask
+
+
+def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
+    W, H = 128, 128
+    P, cams, cams32 = scene(seed=4, n=4000, V=1, W=W, H=H)
+    plan, _, _, img, _ = _forward(cuda_lib, P, cams, W, H)
+    st = plan_state(plan, 1)
+    ref = oraster.splat_forward(P.astype(np.float64), cams32, 16, 16)
+    bad = _flag_pixels_of_unsafe_items(ref, st["rect"], 1, W, H, (16, 16), P.shape[1]) | (ref["margin"] < 1e-3)
+    assert bad.mean() < 0.3, bad.mean()
+    err = np.abs(img - ref["img"]).transpose(1, 0, 2, 3)[:, ~bad]
+    assert err.max() <= 1e-4, err.max()
+
+
+def test_backward_matches_oracle(cuda_lib):
+    W, H, V = 100, 76, 2
+    P, cams, cams32 = scene(seed=5, n=2000, V=V, W=W, H=H)
+    n = P.shape[1]
+    bg = (0.05, 0.1, 0.2)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg)
+    st = plan_state(plan, V)
+    splat, color = gpu_splats_as_oracle(st)
+    ref = oraster.render(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
+                         np.array(bg))
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal((V, 3, H, W)).astype(np.float32)
+    wa = rng.standard_normal((V, H, W)).astype(np.float32)
+    keep = ref["margin"] > 1e-5            # no gradient through pixels near a cut-off
+    w *= keep[:, None]
+    wa *= keep
+    grad = torch.zeros_like(params)
+    plan.backward(params, cams_dev, torch.from_numpy(w).cuda(), grad, dalpha=torch.from_numpy(wa).cuda(), bg=bg)
+    torch.cuda.synchronize()
+    st = plan_state(plan, V)
+    g_ref, c_ref = oraster.render_bwd(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
+                                      np.array(bg), w.astype(np.float64), wa.astype(np.float64))
+    gs = st["g_splat"]
+    for k in range(6):
+        nrm, elt = rel_group_error(gs[k], g_ref[:, k])
+        assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
+    for k in range(3):
+        nrm, elt = rel_group_error(gs[6 + k], c_ref[:, k])
+        assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
+    # chain rule to the parameters, checked on the GPU's own per-item gradients
+    P64 = P.astype(np.float64)
+    gfull = np.zeros((14, n))
+    for v in range(V):
+        sl = slice(v * n, (v + 1) * n)
+        gp = oraster.project_bwd(P64, cams32[v], np.arange(n), gs[:6, sl].T.astype(np.float64))
+        gfull += gp.T
+        gfull[11:14] += gs[6:9, sl].astype(np.float64)
+    g_gpu = grad.cpu().numpy()
+    for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+        nrm, elt = rel_group_error(g_gpu[lo:hi], gfull[lo:hi])
+        assert nrm < 1e-3 and elt < 1e-3, (lo, nrm, elt)
+
+
+def test_backward_end_to_end_fp64(cuda_lib):
+    """Whole backward (splats from FP32 parameters) against the FP64 oracle's gradient."""
+    W, H, V = 96, 96, 2
+    P, cams, cams32 = scene(seed=6, n=1500, V=V, W=W, H=H)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H)
+    st = plan_state(plan, V)
+    ref = oraster.splat_forward(P.astype(np.float64), cams32, 16, 16)
+    bad = _flag_pixels_of_unsafe_items(ref, st["rect"], V, W, H, (16, 16), P.shape[1]) | (ref["margin"] < 1e-3)
+    w = np.random.default_rng(1).standard_normal((V, 3, H, W))
+    w *= ~bad[:, None]
+    grad = torch.zeros_like(params)
+    plan.backward(params, cams_dev, torch.from_numpy(w.astype(np.float32)).cuda(), grad)
+    torch.cuda.synchronize()
+    gref, _, _ = oraster.splat_backward(ref, P.astype(np.float64), cams32, w)
+    g = grad.cpu().numpy()
+    for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+        nrm, elt = rel_group_error(g[lo:hi], gref[lo:hi])
+        assert nrm < 1e-3, (lo, nrm, elt)
+
+
+def test_per_view_calls_equal_batched_call(cuda_lib):
+    W, H, V = 64, 48, 4
+    P, cams, cams32 = scene(seed=7, n=1500, V=V, W=W, H=H)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H)
+    w = torch.from_numpy(np.random.default_rng(2).standard_normal((V, 3, H, W)).astype(np.float32)).cuda()
+    g_batch = torch.zeros_like(params)
+    plan.backward(params, cams_dev, w, g_batch)
+    img_views = torch.zeros((V, 3, H, W), device="cuda")
+    g_views = torch.zeros_like(params)
+    for v in range(V):
+        plan.forward(params, cams_dev, img_views, view_begin=v, view_count=1)
+        plan.backward(params, cams_dev, w, g_views, view_begin=v, view_count=1, accumulate=v > 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(img_views.cpu().numpy(), img)
+    nrm, elt = rel_group_error(g_views.cpu().numpy(), g_batch.cpu().numpy())
+    assert nrm < 1e-5 and elt < 1e-4
+
+
+def test_uneven_multi_scene_batch(cuda_lib):
+    W, H = 80, 64
+    sizes = [500, 1500, 37]
+    Ps = [scene(seed=10 + i, n=s, V=1, W=W, H=H)[0] for i, s in enumerate(sizes)]
+    P = np.concatenate(Ps, axis=1)
+    so = np.concatenate([[0], np.cumsum(sizes)])
+    view_scene = [0, 1, 1, 2, 0]
+    _, cams, cams32 = scene(seed=0, n=1, V=5, W=W, H=H)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, scene_offset=so, view_scene=view_scene)
+    ref = oraster.splat_forward(P.astype(np.float64), cams32, 16, 16, scene_offset=so, view_scene=view_scene)
+    st = plan_state(plan, 5)
+    assert st["n_items"] == sum(sizes[s] for s in view_scene)
+    splat, color = gpu_splats_as_oracle(st)
+    ref_g = oraster.render(5, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
+                           np.zeros(3))
+    good = ref_g["margin"] > 1e-5
+    assert np.abs(img - ref_g["img"]).transpose(1, 0, 2, 3)[:, good].max() <= 1e-4
+    # each view shows only its own scene
+    for v, s in enumerate(view_scene):
+        single = oraster.splat_forward(Ps[s].astype(np.float64), [cams32[v]], 16, 16)
+        gd = good[v] & (single["margin"][0] > 1e-3) & (ref["margin"][v] > 1e-3)
+        assert np.abs(img[v] - single["img"][0])[:, gd].max() <= 1e-3
+
+
+def test_capacity_overflow_is_reported(cuda_lib):
+    W, H = 64, 48
+    P, cams, _ = scene(seed=8, n=800, V=1, W=W, H=H)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, cap=16, bg=(0.3, 0.2, 0.1))
+    ok, need = plan.check()
+    assert not ok and need > 16
+    assert np.allclose(img[0, 0], 0.3) and np.allclose(img[0, 2], 0.1)
+    ok, _ = plan.check()         # the status word is cleared by the check
+    assert ok
+
+
+def test_empty_and_culled_scenes(cuda_lib):
+    W, H = 40, 24
+    bg = (0.25, 0.5, 0.75)
+    P = np.zeros((14, 0), dtype=np.float32)
+    _, cams, _ = scene(seed=0, n=1, V=2, W=W, H=H)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg)
+    assert np.array_equal(img[:, 0], np.full((2, H, W), 0.25, dtype=np.float32)) and alpha.max() == 0
+    # every Gaussian behind the camera (camera-space z = -5)
+    P, cams, _ = scene(seed=9, n=50, V=1, W=W, H=H)
+    R, t = np.asarray(cams[0]["R"]), np.asarray(cams[0]["t"])
+    P[0:3] = (R.T @ (np.array([0.0, 0.0, -5.0]) - t))[:, None]
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg)
+    assert alpha.max() == 0 and np.allclose(img[0, 2], 0.75)

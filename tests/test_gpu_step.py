@@ -1,0 +1,148 @@
+"""GPU parity of the image loss, Adam and a whole fine-tuning step (Sec. 4.4, Sec. 5.2),
+plus a central finite-difference check of the GPU gradient."""
+
+import numpy as np
+import pytest
+import torch
+
+from _helpers import rel_group_error, scene, to_device
+from oracle import adam as oadam
+from oracle import loss as oloss
+from oracle import raster as oraster
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape", [(2, 40, 50), (1, 128, 128), (3, 17, 33)])
+def test_loss_and_gradient(cuda_lib, shape):
+    vbm = cuda_lib
+    V, H, W = shape
+    rng = np.random.default_rng(V * 100 + H)
+    x = rng.uniform(0, 1, (V, 3, H, W)).astype(np.float32)
+    y = np.clip(x + rng.normal(0, 0.15, x.shape), 0, 1).astype(np.float32)
+    x[0, 0, :3, :3] = y[0, 0, :3, :3]         # exact ties: sign(0) = 0
+    L_ref, g_ref = oloss.loss_and_grad(x.astype(np.float64), y.astype(np.float64))
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ws = vbm.loss_workspace(V, H, W)
+    L = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(xt)
+    vbm.loss(xt, yt, V, H, W, 0.2, 1.0 / x.size, L, g, ws)
+    torch.cuda.synchronize()
+    assert abs(L.item() - L_ref) <= 1e-6 * L_ref
+    nrm, elt = rel_group_error(g.cpu().numpy(), g_ref)
+    assert nrm < 1e-3 and elt < 1e-3, (nrm, elt)
+    # accumulate: per-image calls add up to the batched value
+    L2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for v in range(V):
+        vbm.loss(xt[v], yt[v], 1, H, W, 0.2, 1.0 / x.size, L2, g[v], ws, accumulate=v > 0)
+    torch.cuda.synchronize()
+    assert abs(L2.item() - L.item()) <= 1e-12 * max(1.0, L.item())
+
+
+def test_adam_matches_oracle(cuda_lib):
+    vbm = cuda_lib
+    rng = np.random.default_rng(3)
+    n, stride = 1000, 1003
+    P = rng.standard_normal((14, stride)).astype(np.float32)
+    lrs = oadam.default_lrs(64.0)
+    Pt = torch.from_numpy(P.copy()).cuda()
+    m, v = torch.zeros_like(Pt), torch.zeros_like(Pt)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P64, m64, v64 = P[:, :n].astype(np.float64), np.zeros((14, n)), np.zeros((14, n))
+    for t in range(1, 4):
+        G = (rng.standard_normal((14, stride)) * 10.0 ** rng.uniform(-4, 0, (14, 1))).astype(np.float32)
+        vbm.adam(Pt, torch.from_numpy(G).cuda(), m, v, n, step, lrs, nonfinite=bad)
+        oadam.adam_step(P64, G[:, :n].astype(np.float64), m64, v64, t, lrs)
+    torch.cuda.synchronize()
+    out = Pt.cpu().numpy()
+    assert step.item() == 3 and bad.item() == 0
+    assert np.abs(out[:, :n] - P64).max() < 2e-5 * max(1.0, np.abs(P64).max())
+    assert np.array_equal(out[:, n:], P[:, n:])      # columns beyond n untouched
+    # a non-finite gradient element is counted and leaves its parameter alone
+    G = np.zeros((14, stride), dtype=np.float32)
+    G[2, 5] = np.nan
+    before = Pt.cpu().numpy()
+    vbm.adam(Pt, torch.from_numpy(G).cuda(), m, v, n, step, lrs, nonfinite=bad)
+    torch.cuda.synchronize()
+    assert bad.item() == 1 and Pt.cpu().numpy()[2, 5] == before[2, 5]
+
+
+def test_gradient_central_differences(cuda_lib):
+    """Autograd backward (torch.autograd.Function over vbm_raster_fwd/bwd) of L = sum w * img
+    on 64 sampled parameters against central differences of the GPU forward (FP32, h = 1e-4,
+    tolerance 5e-2 relative: difference noise).  A sample is skipped when the FP64 oracle
+    shows that a compositing decision differs between theta + h and theta - h (per pixel: the
+    number of blended Gaussians or the position of the last one) or a tile rectangle moves:
+    the loss is discontinuous across such a flip."""
+    from paper_2601_09417_gb300.autograd import render
+    vbm = cuda_lib
+    W, H, V = 64, 64, 2
+    P, cams, cams32 = scene(seed=21, n=300, V=V, W=W, H=H, scale_range=(0.8, 2.5))
+    params, cams_dev = to_device(P, cams)
+    plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 20)
+    w = torch.from_numpy(np.random.default_rng(5).uniform(0.5, 1.5, (V, 3, H, W)).astype(np.float32)).cuda()
+    p = params.clone().requires_grad_(True)
+    (render(p, plan, cams_dev) * w).sum().backward()
+    g = p.grad.cpu().numpy()
+    img = torch.zeros((V, 3, H, W), device="cuda")
+
+    def L(Pn):
+        plan.forward(torch.from_numpy(Pn).cuda(), cams_dev, img)
+        return float((img.double() * w.double()).sum().item())
+    rng = np.random.default_rng(6)
+    checked = 0
+    h = 1e-4
+    for _ in range(2000):
+        if checked == 64:
+            break
+        r, c = int(rng.integers(0, 14)), int(rng.integers(0, P.shape[1]))
+        if abs(g[r, c]) < 1e-2 * np.abs(g[r]).max():
+            continue
+        Pp, Pm = P.copy(), P.copy()
+        Pp[r, c] += h
+        Pm[r, c] -= h
+        fp = oraster.splat_forward(Pp.astype(np.float64), cams32)
+        fm = oraster.splat_forward(Pm.astype(np.float64), cams32)
+        if not (np.array_equal(fp["n_blend"], fm["n_blend"]) and np.array_equal(fp["n_contrib"], fm["n_contrib"])
+                and np.array_equal(fp["rect"], fm["rect"])):
+            continue
+        fd = (L(Pp) - L(Pm)) / (2 * h)
+        assert abs(fd - g[r, c]) <= 5e-2 * abs(g[r, c]) + 1e-3, (r, c, fd, g[r, c])
+        checked += 1
+    assert checked == 64, checked
+
+
+def test_full_step_matches_oracle_step(cuda_lib):
+    vbm = cuda_lib
+    from oracle.step import finetune_step
+    W, H, V, G = 64, 48, 2, 32
+    P, cams, cams32 = scene(seed=31, n=800, V=V, W=W, H=H)
+    target = np.random.default_rng(2).uniform(0, 0.4, (V, 3, H, W)).astype(np.float32)
+    params, cams_dev = to_device(P, cams)
+    plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 20)
+    img = torch.zeros((V, 3, H, W), device="cuda")
+    dimg = torch.empty_like(img)
+    ws = vbm.loss_workspace(V, H, W)
+    L = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.zeros_like(params)
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lrs = oadam.default_lrs(G)
+    tgt = torch.from_numpy(target).cuda()
+    plan.forward(params, cams_dev, img)
+    vbm.loss(img, tgt, V, H, W, 0.2, 1.0 / img.numel(), L, dimg, ws)
+    plan.backward(params, cams_dev, dimg, grad)
+    vbm.adam(params, grad, m, v, P.shape[1], step, lrs)
+    torch.cuda.synchronize()
+    P64 = P.astype(np.float64)
+    m64, v64 = np.zeros_like(P64), np.zeros_like(P64)
+    L_ref, g_ref, fwd = finetune_step(P64, m64, v64, 1, cams32, target.astype(np.float64), lrs)
+    assert abs(L.item() - L_ref) <= 1e-4 * L_ref
+    nrm, _ = rel_group_error(grad.cpu().numpy(), g_ref)
+    assert nrm < 2e-2, nrm   # pixels at cut-offs are not excluded here
+    # Adam's first step moves each parameter by about lr: compare the steps
+    d_gpu = params.cpu().numpy() - P
+    d_ref = P64 - P.astype(np.float64)
+    agree = np.sign(d_gpu) == np.sign(d_ref)
+    assert agree.mean() > 0.97
