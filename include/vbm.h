@@ -159,7 +159,7 @@ VBM_API vbm_status vbm_build_workspace_size(const int dims[3], int levels, size_
 /* Volume -> Gaussians (Sec. 4.1: F -> RF -> Phi -> G): TF, J-level DWT,
  * adaptive filtering (Supp. Sec. 1) and the per-coefficient map
  * (Eq. 22-24): amplitude s |A| w, centre u + 2^j k + 1/2, covariance of the
- * bank entry; opacity logit = logit(clamp(amp_alpha, 1e-4, 0.99)), colour =
+ * bank entry; opacity logit = logit(clamp(amp_alpha, 2/255, 0.99)), colour =
  * amp_rgb.  Gaussians are written subband by subband, each in raster order
  * of k, to d_params[14][capacity] (stride = capacity).  *n_out = number kept;
  * if it exceeds capacity nothing is written and VBM_ERR_CAPACITY is
@@ -228,7 +228,8 @@ VBM_API vbm_status vbm_plan_check(vbm_plan *plan, void *stream, int64_t *pairs_n
 /* Forward splatting of views [view_begin, view_begin + view_count) (Sec. 4.4,
  * 3DGS conventions): per (view, Gaussian) EWA projection (cull z <= znear,
  * x/z and y/z clamped to the image +15% for the Jacobian, 2D covariance
- * J W Sigma W^T J^T + 0.3 I, radius ceil(3 sqrt(lambda_max))), tile binning
+ * J W Sigma W^T J^T + 0.3 I, radius ceil(k sqrt(lambda_max)) with
+ * k = min(3, sqrt(2 ln(255 o))), no tiles when o < 1/255), tile binning
  * ordered by depth (ties by Gaussian index), front-to-back compositing per
  * pixel (alpha = min(0.99, o e^power), skip alpha < 1/255, stop before T
  * falls below 1e-4).  Writes d_img[V][3][H][W] = C + T bg and, if not NULL,

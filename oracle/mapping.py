@@ -9,9 +9,13 @@ Test infrastructure only.  Sec. 4.3:
 Readings (the paper leaves the 3DGS parameterisation implicit, Eq. 32):
   * delta = (1/2, 1/2, 1/2) is the voxel-centre offset: centre (world) =
     u_{j,o} + 2^j k + 1/2.
-  * amplitude -> opacity: logit(clamp(s p_alpha, 1e-4, 0.99)) so that the
+  * amplitude -> opacity: logit(clamp(s p_alpha, 2/255, 0.99)) so that the
     sigmoid-activated 3DGS opacity reproduces it; colour = s p_rgb (raw, no
-    activation, view independent).
+    activation, view independent).  The floor 2/255 keeps every retained
+    coefficient visible: the fine-tuning renderer never composites a splat
+    whose opacity is below 1/255 (such a Gaussian would get no gradient and
+    stay invisible), while the adaptive filter kept the coefficient as
+    significant (Sec. 4.3).
   * log_scale and rotation come from the bank entry of the subband.
   * s is applied by default (energy_comp); it can be switched off.
 Gaussians are emitted subband by subband (oracle.dwt.subbands order) and,
@@ -76,7 +80,7 @@ def map_coefficients(A, masks, levels, bank_entries, energy_comp=True):
         P[2] = entry["u"][2] + step * kz + 0.5
         P[3:6] = np.asarray(entry["log_scale"])[:, None]
         P[6:10] = np.asarray(entry["quat"])[:, None]
-        op = np.clip(amp[3], 1e-4, 0.99)
+        op = np.clip(amp[3], 2.0 / 255.0, 0.99)
         P[10] = np.log(op / (1.0 - op))
         P[11:14] = amp[0:3]
         cols.append(P)

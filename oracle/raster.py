@@ -21,9 +21,9 @@ _SRC = os.path.join(_HERE, "raster_ref.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc_raster.so")
 
-NPROJ = 17
+NPROJ = 18
 PJ = dict(U=0, V=1, A=2, B=3, C=4, OPAC=5, DEPTH=6, RADIUS=7, X0=8, Y0=9, X1=10, Y1=11,
-          TOUCHED=12, M_RADIUS=13, M_RECT=14, M_CULL=15, M_CLAMP=16)
+          TOUCHED=12, M_RADIUS=13, M_RECT=14, M_CULL=15, M_CLAMP=16, M_OPAC=17)
 
 _lib = None
 

@@ -15,7 +15,12 @@
  *                         centred principal point)
  *   DILATION 0.3          added to the diagonal of the 2D covariance
  *   EIG_FLOOR 0.1         lambda_max = mid + sqrt(max(0.1, mid^2 - det))
- *   RADIUS_SIGMAS 3       r = ceil(3 sqrt(lambda_max)) pixels
+ *   RADIUS_SIGMAS 3       r = ceil(k sqrt(lambda_max)) pixels with
+ *                         k = min(3, sqrt(2 ln(255 o))): the 3-sigma extent of
+ *                         3DGS, shrunk to the ellipse outside which
+ *                         o e^power < 1/255 (such pairs are skipped anyway, so
+ *                         the image is unchanged); Gaussians with o < 1/255 can
+ *                         never be composited and get no tiles
  *   ALPHA_MAX 0.99, ALPHA_MIN 1/255, T_MIN 1e-4 compositing cut-offs
  * Pixel (i, j) has its centre at (i + 1/2, j + 1/2); the image-plane mean is
  * (fx x/z + cx, fy y/z + cy).  A Gaussian's tile rectangle covers the tiles
@@ -54,6 +59,7 @@ enum {
     PJ_M_RECT,     /* distance (px) of u -/+ r, v -/+ r to the nearest tile edge */
     PJ_M_CULL,     /* |z - znear|                                               */
     PJ_M_CLAMP,    /* distance of x/z, y/z to the frustum clamp limits           */
+    PJ_M_OPAC,     /* |255 o - 1|: distance of the opacity to the 1/255 cut-off  */
     NPROJ
 };
 
@@ -146,14 +152,17 @@ void orc_project(int64_t n_items, const int64_t *gidx, const double *P, int64_t 
         o[PJ_DEPTH] = st.t[2];
         o[PJ_OPAC] = st.opac;
         o[PJ_M_CULL] = fabs(st.t[2] - cam[CAM_ZNEAR]);
-        if (st.culled) continue;
+        o[PJ_M_OPAC] = fabs(255.0 * st.opac - 1.0);
+        if (st.culled || st.opac < ALPHA_MIN) continue;
         o[PJ_A] = st.c / st.det;
         o[PJ_B] = -st.b / st.det;
         o[PJ_C] = st.a / st.det;
         double mid = 0.5 * (st.a + st.c);
         double disc = mid * mid - st.det;
         double lam1 = mid + sqrt(disc > EIG_FLOOR ? disc : EIG_FLOOR);
-        double rr = RADIUS_SIGMAS * sqrt(lam1);
+        double k = sqrt(2.0 * log(255.0 * st.opac));
+        if (k > RADIUS_SIGMAS) k = RADIUS_SIGMAS;
+        double rr = k * sqrt(lam1);
         double r = ceil(rr);
         o[PJ_RADIUS] = r;
         o[PJ_M_RADIUS] = fmin(rr - floor(rr), ceil(rr) - rr);

@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(1024) k_map_subband(const float *__restrict__ 
             P[2 * stride + pos] = me.u[2] + step * z + 0.5f;
             for (int d = 0; d < 3; d++) P[(3 + d) * stride + pos] = me.log_scale[d];
             for (int d = 0; d < 4; d++) P[(6 + d) * stride + pos] = me.quat[d];
-            const float op = fminf(fmaxf(amp[3], 1e-4f), 0.99f);
+            // floor 2/255: a retained coefficient stays above the 1/255 cut-off
+            const float op = fminf(fmaxf(amp[3], 2.f / 255.f), 0.99f);
             P[10 * stride + pos] = logf(op / (1.f - op));
             P[11 * stride + pos] = amp[0];
             P[12 * stride + pos] = amp[1];

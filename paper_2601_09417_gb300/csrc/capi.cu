@@ -174,6 +174,7 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     }
     p->sort_scratch.blocks = num_sms() * 2;
     ALLOC(p->sort_scratch.hist, radix_sort_hist_words(p->sort_scratch.blocks));
+    if (s == VBM_OK) p->sort_scratch.digit_total = p->sort_scratch.hist + 256 * (size_t)p->sort_scratch.blocks;
     p->scan_scratch.blocks = num_sms() * 2;
     ALLOC(p->scan_scratch.block_sums, p->scan_scratch.blocks + 1);
     ALLOC(p->d_n_items, 1);

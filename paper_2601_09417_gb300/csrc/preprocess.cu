@@ -10,7 +10,10 @@
 // registers, so the parameter gradient is written once, without atomics.
 //
 // Sec. 4.4 fine-tunes "as in" 3D Gaussian Splatting; the constants are that
-// method's (vbm_internal.h).
+// method's (vbm_internal.h), except that the splat radius is the extent of the
+// region where o e^power >= 1/255 (at most 3 sigma): every pixel outside it
+// would skip the splat, so the image is the same with fewer (tile, splat)
+// pairs.
 #include "vbm_internal.h"
 
 namespace vbm {
@@ -119,15 +122,20 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     uint32_t ntouch = 0;
     int4 rc = make_int4(0, 0, 0, 0);
     int r_int = 0;
-    if (!st.culled) {
+    // A splat whose opacity is below the 1/255 compositing cut-off can never be
+    // blended (alpha = o G <= o), so it gets no tiles.
+    if (!st.culled && st.opac >= kAlphaMin) {
         float inv_det = 1.0f / st.det;
         float A = st.c * inv_det, B = -st.b * inv_det, C = st.a * inv_det;
         float mid = 0.5f * (st.a + st.c);
         float disc = mid * mid - st.det;
         float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
+        // Extent of the ellipse where o e^power >= 1/255 (capped at 3 sigma):
+        // pixels beyond it skip this splat anyway, so fewer tiles list it.
+        const float k = fminf(kRadiusSigmas, sqrtf(2.f * logf(255.f * st.opac)));
         // Bounded so the integer rectangle arithmetic cannot overflow; any
         // radius above 2^24 already spans every image narrower than 6.7M px.
-        float r = fminf(ceilf(kRadiusSigmas * sqrtf(lam1)), 16777216.0f);
+        float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
         float u = cam.fx * (st.t[0] / st.t[2]) + cam.cx;
         float vv = cam.fy * (st.t[1] / st.t[2]) + cam.cy;
         geo[item] = make_float4(u, vv, A, B);

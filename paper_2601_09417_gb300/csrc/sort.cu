@@ -34,10 +34,12 @@ __device__ __forceinline__ int64_t chunk_of(int64_t n, int blocks)
     return (c + kSortTile - 1) / kSortTile * kSortTile;
 }
 
-// Per-block digit histogram of keys in the block's chunk: hist[d * blocks + b].
+// Per-block digit histogram of keys in the block's chunk: hist[d * blocks + b],
+// and the per-digit totals over all blocks (digit_total, zeroed before).
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                                 const int64_t *__restrict__ d_n, int shift,
-                                                                uint32_t *__restrict__ hist)
+                                                                uint32_t *__restrict__ hist,
+                                                                uint32_t *__restrict__ digit_total)
 {
     __shared__ uint32_t h[kRadix];
     for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
@@ -49,31 +51,65 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
     for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x)
         atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+        hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+        if (h[d]) atomicAdd(&digit_total[d], h[d]);
+    }
 }
 
-// Exclusive scan (in place) of the digit-major histogram: one block.
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int total)
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sums, uint32_t *total)
 {
-    __shared__ uint32_t sums[1024];
-    const int per = (total + blockDim.x - 1) / blockDim.x;
-    const int beg = threadIdx.x * per;
-    const int end = min(total, beg + per);
-    uint32_t s = 0;
-    for (int i = beg; i < end; i++) s += hist[i];
-    sums[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        uint32_t v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : 0u;
-        __syncthreads();
-        sums[threadIdx.x] += v;
-        __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
     }
-    uint32_t run = threadIdx.x ? sums[threadIdx.x - 1] : 0u;
-    for (int i = beg; i < end; i++) {
-        uint32_t v = hist[i];
-        hist[i] = run;
-        run += v;
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        if (lane < nw) warp_sums[lane] = wi - w;
+        if (lane == 31 && total) *total = wi;
+    }
+    __syncthreads();
+    const uint32_t r = warp_sums[warp] + incl - x;
+    __syncthreads();
+    return r;
+}
+
+// Digit-major exclusive offsets, one block per digit d: base(d) = sum of the
+// totals of the smaller digits, then a scan of digit d's per-block counts.
+__global__ void __launch_bounds__(kSortThreads) k_radix_offsets(uint32_t *__restrict__ hist,
+                                                                const uint32_t *__restrict__ digit_total, int blocks)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t s_base;
+    const int d = blockIdx.x;
+    uint32_t lower = 0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) lower += digit_total[i];
+    const uint32_t dummy = block_exclusive_scan(lower, warp_sums, &s_base);
+    (void)dummy;
+    __syncthreads();
+    uint32_t carry = s_base;
+    __syncthreads();
+    uint32_t *h = hist + (int64_t)d * blocks;
+    for (int b0 = 0; b0 < blocks; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t x = b < blocks ? h[b] : 0u;
+        __shared__ uint32_t chunk_total;
+        const uint32_t ex = block_exclusive_scan(x, warp_sums, &chunk_total);
+        if (b < blocks) h[b] = carry + ex;
+        __syncthreads();
+        carry += chunk_total;
+        __syncthreads();
     }
 }
 
@@ -184,17 +220,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__
     if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
 }
 
-__global__ void k_scan_top(int64_t *__restrict__ block_sums, int blocks)
+// Exclusive scan of the per-block sums (blocks <= 1024) in one block; total at [blocks].
+__global__ void __launch_bounds__(1024) k_scan_top(int64_t *__restrict__ block_sums, int blocks)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int64_t run = 0;
-        for (int b = 0; b < blocks; b++) {
-            int64_t v = block_sums[b];
-            block_sums[b] = run;
-            run += v;
-        }
-        block_sums[blocks] = run;
+    __shared__ int64_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t x = (int)threadIdx.x < blocks ? block_sums[threadIdx.x] : 0;
+    int64_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
     }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t w = warp_sums[lane];
+        int64_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        warp_sums[lane] = wi - w;
+        if (lane == 31) block_sums[blocks] = wi;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < blocks) block_sums[threadIdx.x] = warp_sums[warp] + incl - x;
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ counts,
@@ -315,7 +367,7 @@ int ceil_log2(int64_t x)
 
 }  // namespace
 
-size_t radix_sort_hist_words(int blocks) { return (size_t)kRadix * blocks; }
+size_t radix_sort_hist_words(int blocks) { return (size_t)kRadix * blocks + kRadix; }
 
 int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,
                      const SortScratch &s, cudaStream_t st)
@@ -323,8 +375,9 @@ int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, i
     int cur = 0;
     if (n_max <= 0) return cur;
     for (int shift = 0; shift < bits; shift += kRadixBits) {
-        k_radix_upsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], d_n, shift, s.hist);
-        k_radix_scan<<<1, 1024, 0, st>>>(s.hist, kRadix * s.blocks);
+        cudaMemsetAsync(s.digit_total, 0, kRadix * sizeof(uint32_t), st);
+        k_radix_upsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], d_n, shift, s.hist, s.digit_total);
+        k_radix_offsets<<<kRadix, kSortThreads, 0, st>>>(s.hist, s.digit_total, s.blocks);
         k_radix_downsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], d_n,
                                                              shift, s.hist);
         cur = 1 - cur;
@@ -337,7 +390,7 @@ void gather_scan(const uint32_t *counts, const uint32_t *idx, int64_t n, int64_t
                  cudaStream_t st)
 {
     k_scan_reduce<<<s.blocks, kScanThreads, 0, st>>>(counts, idx, n, s.block_sums);
-    k_scan_top<<<1, 32, 0, st>>>(s.block_sums, s.blocks);
+    k_scan_top<<<1, 1024, 0, st>>>(s.block_sums, s.blocks);
     k_scan_down<<<s.blocks, kScanThreads, 0, st>>>(counts, idx, n, s.block_sums, out);
     note_launches(3);
 }

@@ -70,8 +70,9 @@ FilterBank make_filters(int wavelet);
 // `bits` bits of the key; the element count is read from d_n on the device.
 // Results end in (keys[0], vals[0]) or (keys[1], vals[1]): the returned index.
 struct SortScratch {
-    uint32_t *hist = nullptr;   // radix * blocks counters
-    int blocks = 0;
+    uint32_t *hist = nullptr;          // radix * blocks counters
+    uint32_t *digit_total = nullptr;   // radix counters (inside the same allocation)
+    int blocks = 0;                    // <= 1024
 };
 size_t radix_sort_hist_words(int blocks);
 int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,

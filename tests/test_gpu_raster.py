@@ -52,7 +52,7 @@ def test_preprocess_matches_oracle(cuda_lib):
         vis = ref[:, PJ["TOUCHED"]] > 0
         culled = ref[:, PJ["RADIUS"]] == 0
         safe = ((ref[:, PJ["M_RADIUS"]] > 1e-3) | culled) & (ref[:, PJ["M_RECT"]] > 1e-3) \
-            & (ref[:, PJ["M_CULL"]] > 1e-3)
+            & (ref[:, PJ["M_CULL"]] > 1e-3) & (ref[:, PJ["M_OPAC"]] > 1e-3)
         flagged += int((~safe).sum())
         g = st["geo"][sl]
         scale_uv = np.abs(ref[:, [PJ["U"], PJ["V"]]]) + 100.0

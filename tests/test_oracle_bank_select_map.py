@@ -203,7 +203,7 @@ def test_single_atom_maps_to_its_lobe():
         e = [x for x in entries if x["j"] == j and tuple(x["o"]) == o][0]
         assert np.allclose(P[11:14, best], np.abs(amp[:3]) * e["w"], rtol=1e-12)
         op = 1 / (1 + np.exp(-P[10, best]))
-        assert op == pytest.approx(min(0.99, abs(amp[3]) * e["w"]), rel=1e-12)
+        assert op == pytest.approx(min(0.99, max(2 / 255, abs(amp[3]) * e["w"])), rel=1e-12)
 
 
 def test_mapping_structure_and_energy_compensation():
@@ -227,7 +227,7 @@ def test_mapping_structure_and_energy_compensation():
 
 
 def test_opacity_clamp_values():
-    """logit(clamp(.)): a huge alpha amplitude gives logit(0.99) = ln 99, a tiny one logit(1e-4)."""
+    """logit(clamp(.)): a huge alpha amplitude gives logit(0.99) = ln 99, a tiny one logit(2/255)."""
     entries = obank.build_bank(1, "haar")
     bands = subbands(1)
     masks = [np.zeros((4, 4, 4), dtype=bool) for _ in bands]
@@ -238,4 +238,4 @@ def test_opacity_clamp_values():
     assert P.shape[1] == 1 and P[10, 0] == pytest.approx(np.log(99.0), rel=1e-12)
     A[3, 0, 0, 4] = 1e-9
     P = map_coefficients(A, masks, 1, entries)
-    assert P[10, 0] == pytest.approx(np.log(1e-4 / (1 - 1e-4)), rel=1e-12)
+    assert P[10, 0] == pytest.approx(np.log(2.0 / 253.0), rel=1e-12)

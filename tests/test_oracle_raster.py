@@ -38,9 +38,38 @@ def test_on_axis_isotropic_projection(sigma, z):
     assert abs(pj[PJ["B"]]) < 1e-14
     assert pj[PJ["U"]] == pytest.approx(cam["cx"], abs=1e-12)
     assert pj[PJ["V"]] == pytest.approx(cam["cy"], abs=1e-12)
-    assert pj[PJ["RADIUS"]] == np.ceil(3 * np.sqrt(a + np.sqrt(0.1)))
+    assert pj[PJ["RADIUS"]] == np.ceil(3 * np.sqrt(a + np.sqrt(0.1)))   # o = 0.62: k = 3
     assert pj[PJ["DEPTH"]] == pytest.approx(z)
     assert pj[PJ["OPAC"]] == pytest.approx(1 / (1 + np.exp(-0.5)))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_every_visible_pixel_is_inside_the_tile_rectangle(seed):
+    """The radius rule keeps every pixel where o e^power >= 1/255 inside the Gaussian's tile
+    rectangle (checked by evaluating the splat at every pixel), and a Gaussian whose opacity
+    is below 1/255 gets no tiles."""
+    W, H = 96, 80
+    cams = orbit_cameras((32, 32, 32), 1, W, H)
+    P = gaussians_in_view(300, 32, seed=seed, opacity_logit_range=(-7.0, 3.0))
+    pj = raster.project(P, cams[0], np.arange(300), 16, 16)
+    jj, ii = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    n_visible = 0
+    for g in range(300):
+        r = pj[g]
+        o = r[PJ["OPAC"]]
+        if o < 1 / 255:
+            assert r[PJ["TOUCHED"]] == 0
+            continue
+        if r[PJ["RADIUS"]] == 0:
+            continue
+        dx, dy = r[PJ["U"]] - ii, r[PJ["V"]] - jj
+        power = -0.5 * (r[PJ["A"]] * dx * dx + r[PJ["C"]] * dy * dy) - r[PJ["B"]] * dx * dy
+        vis = o * np.exp(power) >= 1 / 255
+        n_visible += int(vis.any())
+        tx, ty = (ii // 16).astype(int), (jj // 16).astype(int)
+        inside = (tx >= r[PJ["X0"]]) & (tx < r[PJ["X1"]]) & (ty >= r[PJ["Y0"]]) & (ty < r[PJ["Y1"]])
+        assert not (vis & ~inside).any(), g
+    assert n_visible > 50
 
 
 def test_projection_covariance_is_symmetric_pd_and_culls():
