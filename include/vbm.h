@@ -199,8 +199,10 @@ typedef struct vbm_plan vbm_plan;
  * ranges [scene_offset[s], scene_offset[s+1]) of one parameter array; view v
  * renders scene view_scene[v] (NULL means all views render scene 0).  Every
  * view has the same width x height.  Tiles are tile_w x tile_h pixels
- * (tile_w * tile_h in {64, 128, 256}).  pair_capacity bounds the number of
- * (tile, Gaussian) pairs of one call. */
+ * (tile_w * tile_h in {64, 128, 256}); each compositing thread handles
+ * pixels_per_thread pixels of one tile column (at least 32 threads per
+ * tile).  pair_capacity bounds the number of (tile, Gaussian) pairs of one
+ * call. */
 typedef struct {
     int32_t n_scenes;
     int32_t n_views;
@@ -210,7 +212,7 @@ typedef struct {
     int32_t tile_w, tile_h;
     int64_t pair_capacity;
     int32_t flags;
-    int32_t pad;
+    int32_t pixels_per_thread;     /* 0 = default (2); 1, 2 or 4 */
 } vbm_plan_desc;
 
 /* Create a plan (allocates device memory, synchronous). */

@@ -102,6 +102,9 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     VBM_ARG(d->tile_w > 0 && d->tile_h > 0 && (tp == 64 || tp == 128 || tp == 256),
             "tile_w * tile_h must be 64, 128 or 256");
     VBM_ARG(d->pair_capacity > 0 && d->pair_capacity < ((int64_t)1 << 31), "pair_capacity out of range");
+    VBM_ARG(d->pixels_per_thread == 0 || d->pixels_per_thread == 1 || d->pixels_per_thread == 2 ||
+                d->pixels_per_thread == 4,
+            "pixels_per_thread must be 0, 1, 2 or 4");
     VBM_ARG(d->scene_offset[0] == 0, "scene_offset[0] must be 0");
     for (int s = 0; s < d->n_scenes; s++)
         VBM_ARG(d->scene_offset[s + 1] >= d->scene_offset[s], "scene_offset must be non-decreasing");

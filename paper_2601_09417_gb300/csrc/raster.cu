@@ -1,21 +1,35 @@
 // Front-to-back alpha compositing of the binned splats and its reverse-order
 // backward (Sec. 4.4, "as in" 3D Gaussian Splatting).
 //
-// One block per image tile, one thread per pixel.  A tile's depth-ordered
-// list is staged through shared memory NT entries at a time: each thread
-// gathers one entry's splat record (two float4 and a float) so every pixel of
-// the tile reads it from shared memory.  The conic is pre-scaled by
-// -log2(e)/2 at staging, so the exponent is evaluated in base 2 with one
-// ex2.approx instruction (relative error ~2^-22) per (pixel, Gaussian) pair.
-// Early termination: a pixel stops once its transmittance would fall below
-// 1e-4, and the whole block leaves the list as soon as __syncthreads_count
-// reports every pixel done.
+// One block per image tile.  Each thread owns PPT pixels of one tile column
+// (rows ly, ly + TH/PPT, ...), so the per-splat work that only depends on the
+// column (shared-memory loads, dx, A' dx^2, B' dx) is done once per thread,
+// and the per-pixel arithmetic of two pixels is issued as packed FP32x2
+// operations (__ffma2_rn / __fmul2_rn / __fadd2_rn, sm_100+).
+//
+// A tile's depth-ordered list is staged through shared memory NT entries at a
+// time.  While staging, each entry is tested against the tile: the minimum of
+// its quadratic form over the rectangle of the tile's pixel centres gives the
+// largest alpha any pixel of the tile can see; entries below the 1/255
+// cut-off (with a 1e-3 margin in the exponent, far above rounding) are
+// dropped and the rest compacted in list order.  A dropped entry would have
+// been skipped by every pixel, so the image, the saved state and the
+// gradients are unchanged; the original list position travels with each
+// entry for the contributor count.
+//
+// The conic is pre-scaled by -log2(e)/2 when staged, so the exponent is one
+// ex2.approx.ftz per (pixel, splat) pair; its rounding sequence is fixed
+// (explicit _rn operations) so the backward recomputes exactly the forward's
+// alphas and skip decisions.  A pixel stops once its transmittance would
+// fall below 1e-4; the block leaves the list when __syncthreads_count reports
+// every pixel done.
 //
 // The backward walks each tile's list from the back, starting at the largest
 // contributor count of the block, recovers the transmittance by division and
-// accumulates per-(view, Gaussian) gradients.  Per pair, the nine partials of
-// a warp are summed with shuffles before one atomicAdd per value, and warps
-// with no contributing pixel skip the reduction (warp ballot).
+// accumulates per-(view, splat) gradients: per splat, the nine partials are
+// summed over a warp with shuffles (skipped by ballot when no lane
+// contributes), over the block through shared memory in groups of 32 splats,
+// and then added to global memory with nine atomics per (splat, tile).
 #include "vbm_internal.h"
 
 namespace vbm {
@@ -25,6 +39,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kHalfLog2e = -0.5f * kLog2e;   // scales A and C
 constexpr float kNegLog2e = -kLog2e;           // scales B
+constexpr float kCullMargin = 1e-3f;           // natural-log margin of the tile test
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -33,28 +48,99 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Base-2 exponent of a staged splat at a pixel, p2 = A' dx^2 + C' dy^2 +
-// B' dx dy, with an explicit rounding sequence so the backward recomputes
-// exactly the forward's alpha (and therefore the same skip decisions).
-struct SplatEval {
-    float dx, dy, p2, G, raw;
-};
-
-__device__ __forceinline__ SplatEval splat_eval(const float4 g, const float cc, const float opac, const float pxc,
-                                                const float pyc)
+// Smallest q = A dx^2 + 2 B dx dy + C dy^2 (dx = x - u, dy = y - v) over the
+// rectangle [x0, x1] x [y0, y1]: 0 inside, else the minimum over the four
+// edges, each the clamped 1D minimiser.
+__device__ __forceinline__ float rect_min_quadratic(float u, float v, float A, float B, float C, float x0, float x1,
+                                                    float y0, float y1)
 {
-    SplatEval e;
-    e.dx = __fsub_rn(g.x, pxc);
-    e.dy = __fsub_rn(g.y, pyc);
-    float t = __fmul_rn(__fmul_rn(g.z, e.dx), e.dx);
-    t = __fmaf_rn(__fmul_rn(cc, e.dy), e.dy, t);
-    e.p2 = __fmaf_rn(__fmul_rn(g.w, e.dx), e.dy, t);
-    e.G = ex2_approx(e.p2);
-    e.raw = __fmul_rn(opac, e.G);
-    return e;
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.f;
+    float best = 3.4e38f;
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const float dx = (e ? x1 : x0) - u;
+        const float dy = fminf(fmaxf(v - B * dx / C, y0), y1) - v;
+        best = fminf(best, A * dx * dx + 2.f * B * dx * dy + C * dy * dy);
+        const float ey = (e ? y1 : y0) - v;
+        const float ex = fminf(fmaxf(u - B * ey / A, x0), x1) - u;
+        best = fminf(best, A * ex * ex + 2.f * B * ex * ey + C * ey * ey);
+    }
+    return best;
 }
 
+struct TileGeom {
+    int vrel, px, py0, rows_step;
+    float pxc;
+    float x0, x1, y0, y1;   // pixel-centre rectangle of the tile (clipped to the image)
+};
+
+template <int NT, int PPT>
+__device__ __forceinline__ TileGeom tile_geom(int tw, int TX, int TY, int W, int H)
+{
+    constexpr int NPIX = NT * PPT;
+    const int th = NPIX / tw;
+    TileGeom t;
+    const int tiles_per_view = TX * TY;
+    t.vrel = blockIdx.x / tiles_per_view;
+    const int tt = blockIdx.x - t.vrel * tiles_per_view;
+    const int ty = tt / TX, tx = tt - ty * TX;
+    t.px = tx * tw + (int)(threadIdx.x % tw);
+    t.rows_step = th / PPT;
+    t.py0 = ty * th + (int)(threadIdx.x / tw);
+    t.pxc = t.px + 0.5f;
+    t.x0 = tx * tw + 0.5f;
+    t.x1 = min(tx * tw + tw, W) - 0.5f;
+    t.y0 = ty * th + 0.5f;
+    t.y1 = min(ty * th + th, H) - 0.5f;
+    return t;
+}
+
+// Stage entries [base, min(base + NT, end)) of a tile list: test each against
+// the tile and compact the survivors, in list order, into shared memory.
+// Returns the number staged.  All threads of the block must call it.
 template <int NT>
+__device__ __forceinline__ int stage_entries(int base, int end, int list_begin, const uint32_t *__restrict__ pair_item,
+                                             const float4 *__restrict__ geo, const float4 *__restrict__ col,
+                                             const float *__restrict__ conic_c, const TileGeom &tg, float4 *s_geo,
+                                             float4 *s_col, float2 *s_cp, uint32_t *s_item, int *s_warp)
+{
+    const int idx = base + (int)threadIdx.x;
+    bool keep = false;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), c = g;
+    float cc = 0.f;
+    uint32_t it = 0;
+    if (idx < end) {
+        it = pair_item[idx];
+        g = geo[it];
+        cc = conic_c[it];
+        c = col[it];
+        const float q = rect_min_quadratic(g.x, g.y, g.z, g.w, cc, tg.x0, tg.x1, tg.y0, tg.y1);
+        keep = 0.5f * q <= logf(255.f * c.w) + kCullMargin;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+    __syncthreads();            // the previous batch is no longer read
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) {
+        const int cnt = s_warp[w];
+        before += w < warp ? cnt : 0;
+        total += cnt;
+    }
+    if (keep) {
+        const int slot = before + __popc(bal & ((1u << lane) - 1u));
+        s_geo[slot] = make_float4(g.x, g.y, g.z * kHalfLog2e, g.w * kNegLog2e);
+        s_cp[slot] = make_float2(cc * kHalfLog2e, __int_as_float(idx - list_begin));
+        s_col[slot] = c;
+        if (s_item) s_item[slot] = it;
+    }
+    __syncthreads();
+    return total;
+}
+
+template <int NT, int PPT>
 __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ ranges,
                                                    const uint32_t *__restrict__ pair_item,
                                                    const float4 *__restrict__ geo, const float4 *__restrict__ col,
@@ -64,68 +150,98 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
                                                    float *__restrict__ T_final, int32_t *__restrict__ n_contrib,
                                                    int32_t *__restrict__ n_eval)
 {
-    __shared__ float4 s_geo[NT];   // u, v, A', B'
-    __shared__ float4 s_col[NT];   // r, g, b, opacity
-    __shared__ float s_c[NT];      // C'
-    const int tiles_per_view = TX * TY;
-    const int vrel = blockIdx.x / tiles_per_view;
-    const int t = blockIdx.x - vrel * tiles_per_view;
-    const int ty = t / TX, tx = t - ty * TX;
-    const int th = NT / tw;
-    const int px = tx * tw + (int)(threadIdx.x % tw);
-    const int py = ty * th + (int)(threadIdx.x / tw);
-    const bool inside = px < W && py < H;
-    const float pxc = px + 0.5f, pyc = py + 0.5f;
+    static_assert(PPT == 1 || PPT % 2 == 0, "pixels per thread: 1 or even");
+    constexpr int STEP = PPT == 1 ? 1 : 2;
+    __shared__ float4 s_geo[NT];
+    __shared__ float4 s_col[NT];
+    __shared__ float2 s_cp[NT];
+    __shared__ int s_warp[NT / 32];
+    const TileGeom tg = tile_geom<NT, PPT>(tw, TX, TY, W, H);
     const int2 rg = ranges[blockIdx.x];
-    bool done = !inside;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = 0;
-    int evaluated = rg.y - rg.x;
+    float pyc[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    int last[PPT], evaluated[PPT];
+    bool inside[PPT], done[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int py = tg.py0 + k * tg.rows_step;
+        pyc[k] = py + 0.5f;
+        inside[k] = tg.px < W && py < H;
+        done[k] = !inside[k];
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+        evaluated[k] = rg.y - rg.x;
+    }
     for (int base = rg.x; base < rg.y; base += NT) {
-        if (__syncthreads_count(done) == NT) break;
-        const int idx = base + threadIdx.x;
-        if (idx < rg.y) {
-            const uint32_t it = pair_item[idx];
-            const float4 g = geo[it];
-            s_geo[threadIdx.x] = make_float4(g.x, g.y, g.z * kHalfLog2e, g.w * kNegLog2e);
-            s_c[threadIdx.x] = conic_c[it] * kHalfLog2e;
-            s_col[threadIdx.x] = col[it];
-        }
-        __syncthreads();
-        const int n = min(NT, rg.y - base);
-        if (!done) {
-            for (int j = 0; j < n; j++) {
-                const float4 c = s_col[j];
-                const SplatEval e = splat_eval(s_geo[j], s_c[j], c.w, pxc, pyc);
-                if (e.p2 > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, e.raw);
-                if (alpha < kAlphaMin) continue;
-                const float testT = T * (1.f - alpha);
-                if (testT < kTMin) {
-                    done = true;
-                    evaluated = base - rg.x + j + 1;
-                    break;
+        bool all_done = true;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) all_done &= done[k];
+        if (__syncthreads_count(all_done) == NT) break;
+        const int n = stage_entries<NT>(base, rg.y, rg.x, pair_item, geo, col, conic_c, tg, s_geo, s_col, s_cp,
+                                        nullptr, s_warp);
+        if (all_done) continue;
+        for (int j = 0; j < n; j++) {
+            const float4 g = s_geo[j];
+            const float2 cp = s_cp[j];
+            const float4 c = s_col[j];
+            const int pos = __float_as_int(cp.y);
+            const float dx = __fsub_rn(g.x, tg.pxc);
+            const float t0 = __fmul_rn(__fmul_rn(g.z, dx), dx);
+            const float bdx = __fmul_rn(g.w, dx);
+#pragma unroll
+            for (int k = 0; k < PPT; k += STEP) {
+                float p2[2], raw[2];
+                if (PPT == 1) {
+                    const float dy = __fsub_rn(g.y, pyc[k]);
+                    const float t = __fmaf_rn(__fmul_rn(cp.x, dy), dy, t0);
+                    p2[0] = __fmaf_rn(bdx, dy, t);
+                    raw[0] = __fmul_rn(c.w, ex2_approx(p2[0]));
+                } else {
+                    // a - b == a + (-b) exactly, so this matches __fsub_rn in the backward
+                    const float2 dy = __fadd2_rn(make_float2(g.y, g.y), make_float2(-pyc[k], -pyc[k + STEP - 1]));
+                    const float2 t = __ffma2_rn(__fmul2_rn(make_float2(cp.x, cp.x), dy), dy, make_float2(t0, t0));
+                    const float2 q = __ffma2_rn(make_float2(bdx, bdx), dy, t);
+                    p2[0] = q.x;
+                    p2[1] = q.y;
+                    const float2 r = __fmul2_rn(make_float2(c.w, c.w), make_float2(ex2_approx(q.x), ex2_approx(q.y)));
+                    raw[0] = r.x;
+                    raw[1] = r.y;
                 }
-                const float wgt = alpha * T;
-                C0 += c.x * wgt;
-                C1 += c.y * wgt;
-                C2 += c.z * wgt;
-                T = testT;
-                last = base - rg.x + j + 1;
+#pragma unroll
+                for (int h = 0; h < STEP; h++) {
+                    const int kk = k + h;
+                    const float alpha = fminf(kAlphaMax, raw[h]);
+                    const bool cand = !done[kk] && p2[h] <= 0.f && alpha >= kAlphaMin;
+                    const float testT = T[kk] * (1.f - alpha);
+                    const bool term = cand && testT < kTMin;
+                    const bool blend = cand && !term;
+                    if (term) {
+                        done[kk] = true;
+                        evaluated[kk] = pos + 1;
+                    }
+                    const float wgt = blend ? alpha * T[kk] : 0.f;
+                    C0[kk] = __fmaf_rn(c.x, wgt, C0[kk]);
+                    C1[kk] = __fmaf_rn(c.y, wgt, C1[kk]);
+                    C2[kk] = __fmaf_rn(c.z, wgt, C2[kk]);
+                    T[kk] = blend ? testT : T[kk];
+                    last[kk] = blend ? pos + 1 : last[kk];
+                }
             }
         }
     }
-    if (inside) {
-        const int64_t HW = (int64_t)H * W;
-        const int64_t v = vb + vrel;
-        const int64_t pix = (int64_t)py * W + px;
-        img[(v * 3 + 0) * HW + pix] = C0 + T * bg0;
-        img[(v * 3 + 1) * HW + pix] = C1 + T * bg1;
-        img[(v * 3 + 2) * HW + pix] = C2 + T * bg2;
-        if (alpha_out) alpha_out[v * HW + pix] = 1.f - T;
-        T_final[v * HW + pix] = T;
-        n_contrib[v * HW + pix] = last;
-        if (n_eval) n_eval[v * HW + pix] = evaluated;
+    const int64_t HW = (int64_t)H * W;
+    const int64_t v = vb + tg.vrel;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        if (!inside[k]) continue;
+        const int64_t pix = (int64_t)(tg.py0 + k * tg.rows_step) * W + tg.px;
+        img[(v * 3 + 0) * HW + pix] = C0[k] + T[k] * bg0;
+        img[(v * 3 + 1) * HW + pix] = C1[k] + T[k] * bg1;
+        img[(v * 3 + 2) * HW + pix] = C2[k] + T[k] * bg2;
+        if (alpha_out) alpha_out[v * HW + pix] = 1.f - T[k];
+        T_final[v * HW + pix] = T[k];
+        n_contrib[v * HW + pix] = last[k];
+        if (n_eval) n_eval[v * HW + pix] = evaluated[k];
     }
 }
 
@@ -136,7 +252,9 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-template <int NT>
+constexpr int kGroup = 32;   // splats per block-level gradient reduction
+
+template <int NT, int PPT>
 __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ ranges,
                                                    const uint32_t *__restrict__ pair_item,
                                                    const float4 *__restrict__ geo, const float4 *__restrict__ col,
@@ -147,173 +265,192 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
                                                    const int32_t *__restrict__ n_contrib, float *__restrict__ gs,
                                                    int64_t n_items)
 {
+    constexpr int NW = NT / 32;
     __shared__ float4 s_geo[NT];
     __shared__ float4 s_col[NT];
-    __shared__ float s_c[NT];
+    __shared__ float2 s_cp[NT];
     __shared__ uint32_t s_item[NT];
+    __shared__ int s_warp[NW];
+    __shared__ float s_red[NW][kGroup][9];
     __shared__ int s_max;
-    const int tiles_per_view = TX * TY;
-    const int vrel = blockIdx.x / tiles_per_view;
-    const int t = blockIdx.x - vrel * tiles_per_view;
-    const int ty = t / TX, tx = t - ty * TX;
-    const int th = NT / tw;
-    const int px = tx * tw + (int)(threadIdx.x % tw);
-    const int py = ty * th + (int)(threadIdx.x / tw);
-    const bool inside = px < W && py < H;
-    const float pxc = px + 0.5f, pyc = py + 0.5f;
+    const TileGeom tg = tile_geom<NT, PPT>(tw, TX, TY, W, H);
     const int2 rg = ranges[blockIdx.x];
     const int64_t HW = (int64_t)H * W;
-    const int64_t v = vb + vrel;
-    const int64_t pix = (int64_t)py * W + px;
-    float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dA = 0.f;
-    int nc = 0;
-    if (inside) {
-        T = T_final[v * HW + pix];
-        nc = n_contrib[v * HW + pix];
-        dC0 = dimg[(v * 3 + 0) * HW + pix];
-        dC1 = dimg[(v * 3 + 1) * HW + pix];
-        dC2 = dimg[(v * 3 + 2) * HW + pix];
-        if (dalpha) dA = dalpha[v * HW + pix];
+    const int64_t v = vb + tg.vrel;
+    float pyc[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], tail[PPT], S0[PPT], S1[PPT], S2[PPT];
+    int nc[PPT];
+    int my_max = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int py = tg.py0 + k * tg.rows_step;
+        pyc[k] = py + 0.5f;
+        T[k] = 1.f;
+        dC0[k] = dC1[k] = dC2[k] = 0.f;
+        nc[k] = 0;
+        float dA = 0.f;
+        if (tg.px < W && py < H) {
+            const int64_t pix = (int64_t)py * W + tg.px;
+            T[k] = T_final[v * HW + pix];
+            nc[k] = n_contrib[v * HW + pix];
+            dC0[k] = dimg[(v * 3 + 0) * HW + pix];
+            dC1[k] = dimg[(v * 3 + 1) * HW + pix];
+            dC2[k] = dimg[(v * 3 + 2) * HW + pix];
+            if (dalpha) dA = dalpha[v * HW + pix];
+        }
+        // constant part of dL/dalpha_k (1 - alpha_k): background and alpha-output terms
+        tail[k] = T[k] * (bg0 * dC0[k] + bg1 * dC1[k] + bg2 * dC2[k]) - dA * T[k];
+        S0[k] = S1[k] = S2[k] = 0.f;
+        my_max = max(my_max, nc[k]);
     }
-    const float Tf = T;
-    // constant part of dL/dalpha_k * (1 - alpha_k): background and alpha-output terms
-    const float tail = Tf * (bg0 * dC0 + bg1 * dC1 + bg2 * dC2) - dA * Tf;
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;   // sum over later contributors of c alpha T
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, nc);
+    atomicMax(&s_max, my_max);
     __syncthreads();
     const int max_nc = s_max;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int hi = max_nc; hi > 0; hi -= NT) {
         const int lo = max(0, hi - NT);
-        __syncthreads();
-        const int pos_load = lo + (int)threadIdx.x;
-        if (pos_load < hi) {
-            const uint32_t it = pair_item[rg.x + pos_load];
-            const float4 g = geo[it];
-            s_geo[threadIdx.x] = make_float4(g.x, g.y, g.z * kHalfLog2e, g.w * kNegLog2e);
-            s_c[threadIdx.x] = conic_c[it] * kHalfLog2e;
-            s_col[threadIdx.x] = col[it];
-            s_item[threadIdx.x] = it;
-        }
-        __syncthreads();
-        for (int j = hi - 1 - lo; j >= 0; j--) {
-            const int pos = lo + j;
-            float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f,
-                  g_bl = 0.f;
-            bool contrib = false;
-            if (pos < nc) {
+        const int n = stage_entries<NT>(rg.x + lo, rg.x + hi, rg.x, pair_item, geo, col, conic_c, tg, s_geo, s_col,
+                                        s_cp, s_item, s_warp);
+        // walk the compacted batch backwards in groups of kGroup splats
+        for (int g_hi = n; g_hi > 0; g_hi -= kGroup) {
+            const int g_lo = max(0, g_hi - kGroup);
+            for (int j = g_hi - 1; j >= g_lo; j--) {
                 const float4 g = s_geo[j];
-                const float cc = s_c[j];
+                const float2 cp = s_cp[j];
                 const float4 c = s_col[j];
-                const SplatEval e = splat_eval(g, cc, c.w, pxc, pyc);
-                const float dx = e.dx, dy = e.dy, G = e.G, raw = e.raw;
-                const float alpha = fminf(kAlphaMax, raw);
-                if (e.p2 <= 0.f && alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float om = 1.f - alpha;
-                    T = T / om;
-                    const float wgt = alpha * T;
-                    g_r = wgt * dC0;
-                    g_g = wgt * dC1;
-                    g_bl = wgt * dC2;
-                    const float dLda = (c.x * T * dC0 + c.y * T * dC1 + c.z * T * dC2) -
-                                       (S0 * dC0 + S1 * dC1 + S2 * dC2 + tail) / om;
-                    S0 += c.x * wgt;
-                    S1 += c.y * wgt;
-                    S2 += c.z * wgt;
-                    if (raw < kAlphaMax) {
-                        const float dpow = dLda * raw;   // dL/dpower = dL/dalpha * o * G
-                        g_o = dLda * G;
-                        // natural-log exponent derivatives; A' = -log2e A / 2, B' = -log2e B
-                        g_u = dpow * kLn2 * (2.f * g.z * dx + g.w * dy);
-                        g_v = dpow * kLn2 * (2.f * cc * dy + g.w * dx);
-                        g_a = dpow * (-0.5f * dx * dx);
-                        g_b = dpow * (-dx * dy);
-                        g_c = dpow * (-0.5f * dy * dy);
+                const int pos = __float_as_int(cp.y);
+                const float dx = __fsub_rn(g.x, tg.pxc);
+                const float t0 = __fmul_rn(__fmul_rn(g.z, dx), dx);
+                const float bdx = __fmul_rn(g.w, dx);
+                float acc[9];
+#pragma unroll
+                for (int q = 0; q < 9; q++) acc[q] = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    const float dy = __fsub_rn(g.y, pyc[k]);
+                    const float t = __fmaf_rn(__fmul_rn(cp.x, dy), dy, t0);
+                    const float p2 = __fmaf_rn(bdx, dy, t);
+                    const float G = ex2_approx(p2);
+                    const float raw = __fmul_rn(c.w, G);
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (pos < nc[k] && p2 <= 0.f && alpha >= kAlphaMin) {
+                        any = true;
+                        const float om = 1.f - alpha;
+                        T[k] = T[k] / om;
+                        const float wgt = alpha * T[k];
+                        acc[6] += wgt * dC0[k];
+                        acc[7] += wgt * dC1[k];
+                        acc[8] += wgt * dC2[k];
+                        const float dLda = (c.x * T[k] * dC0[k] + c.y * T[k] * dC1[k] + c.z * T[k] * dC2[k]) -
+                                           (S0[k] * dC0[k] + S1[k] * dC1[k] + S2[k] * dC2[k] + tail[k]) / om;
+                        S0[k] += c.x * wgt;
+                        S1[k] += c.y * wgt;
+                        S2[k] += c.z * wgt;
+                        if (raw < kAlphaMax) {
+                            const float dpow = dLda * raw;   // dL/dpower = dL/dalpha o G
+                            acc[5] += dLda * G;
+                            // natural-log exponent: A' = -log2e A / 2, B' = -log2e B
+                            acc[0] += dpow * kLn2 * (2.f * g.z * dx + g.w * dy);
+                            acc[1] += dpow * kLn2 * (2.f * cp.x * dy + g.w * dx);
+                            acc[2] += dpow * (-0.5f * dx * dx);
+                            acc[3] += dpow * (-dx * dy);
+                            acc[4] += dpow * (-0.5f * dy * dy);
+                        }
                     }
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                g_u = warp_sum(g_u);
-                g_v = warp_sum(g_v);
-                g_a = warp_sum(g_a);
-                g_b = warp_sum(g_b);
-                g_c = warp_sum(g_c);
-                g_o = warp_sum(g_o);
-                g_r = warp_sum(g_r);
-                g_g = warp_sum(g_g);
-                g_bl = warp_sum(g_bl);
-                if (lane == 0) {
-                    const uint32_t it = s_item[j];
-                    atomicAdd(&gs[0 * n_items + it], g_u);
-                    atomicAdd(&gs[1 * n_items + it], g_v);
-                    atomicAdd(&gs[2 * n_items + it], g_a);
-                    atomicAdd(&gs[3 * n_items + it], g_b);
-                    atomicAdd(&gs[4 * n_items + it], g_c);
-                    atomicAdd(&gs[5 * n_items + it], g_o);
-                    atomicAdd(&gs[6 * n_items + it], g_r);
-                    atomicAdd(&gs[7 * n_items + it], g_g);
-                    atomicAdd(&gs[8 * n_items + it], g_bl);
+                const int slot = j - g_lo;
+                if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                    for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
+                    if (lane == 0)
+#pragma unroll
+                        for (int q = 0; q < 9; q++) s_red[warp][slot][q] = acc[q];
+                } else if (lane == 0) {
+#pragma unroll
+                    for (int q = 0; q < 9; q++) s_red[warp][slot][q] = 0.f;
                 }
             }
+            __syncthreads();
+            const int cnt = g_hi - g_lo;
+            for (int e = threadIdx.x; e < cnt * 9; e += NT) {
+                const int slot = e / 9, q = e - slot * 9;
+                float sum = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; w++) sum += s_red[w][slot][q];
+                if (sum != 0.f) atomicAdd(&gs[(int64_t)q * n_items + s_item[g_lo + slot]], sum);
+            }
+            __syncthreads();
         }
     }
 }
 
-template <int NT>
+int pixels_per_thread(const vbm_plan *p)
+{
+    const int npix = p->desc.tile_w * p->desc.tile_h;
+    int ppt = p->desc.pixels_per_thread > 0 ? p->desc.pixels_per_thread : 2;
+    while (ppt > 1 && npix / ppt < 32) ppt >>= 1;
+    return ppt;
+}
+
+template <int NT, int PPT>
 vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img, float *alpha, cudaStream_t st)
 {
     const int blocks = vc * p->TX * p->TY;
     record_event(p->prof_ev[0], st);
-    k_raster_fwd<NT><<<blocks, NT, 0, st>>>(p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
-                                             p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb, bg[0],
-                                             bg[1], bg[2], img, alpha, p->T_final, p->n_contrib, p->prof_n_eval);
+    k_raster_fwd<NT, PPT><<<blocks, NT, 0, st>>>(p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+                                                  p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb,
+                                                  bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib,
+                                                  p->prof_n_eval);
     VBM_LAUNCH("raster_fwd");
     record_event(p->prof_ev[1], st);
     note_launches(1);
     return VBM_OK;
 }
 
-template <int NT>
+template <int NT, int PPT>
 vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const float *dimg, const float *dalpha,
                       cudaStream_t st)
 {
     const int blocks = vc * p->TX * p->TY;
     record_event(p->prof_ev[2], st);
-    k_raster_bwd<NT><<<blocks, NT, 0, st>>>(p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
-                                             p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb, bg[0],
-                                             bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat,
-                                             p->last_items);
+    k_raster_bwd<NT, PPT><<<blocks, NT, 0, st>>>(p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+                                                  p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb,
+                                                  bg[0], bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib,
+                                                  p->g_splat, p->last_items);
     VBM_LAUNCH("raster_bwd");
     record_event(p->prof_ev[3], st);
     note_launches(1);
     return VBM_OK;
 }
 
+// Dispatch on (pixels per tile, pixels per thread).
+#define VBM_RASTER_DISPATCH(FN, ...)                                                          \
+    switch (p->desc.tile_w * p->desc.tile_h * 8 + pixels_per_thread(p)) {                     \
+        case 256 * 8 + 1: return FN<256, 1>(__VA_ARGS__);                                     \
+        case 256 * 8 + 2: return FN<128, 2>(__VA_ARGS__);                                     \
+        case 256 * 8 + 4: return FN<64, 4>(__VA_ARGS__);                                      \
+        case 128 * 8 + 1: return FN<128, 1>(__VA_ARGS__);                                     \
+        case 128 * 8 + 2: return FN<64, 2>(__VA_ARGS__);                                      \
+        case 128 * 8 + 4: return FN<32, 4>(__VA_ARGS__);                                      \
+        case 64 * 8 + 1: return FN<64, 1>(__VA_ARGS__);                                       \
+        case 64 * 8 + 2: return FN<32, 2>(__VA_ARGS__);                                       \
+        default: set_error("unsupported tile / pixels-per-thread combination"); return VBM_ERR_ARG; \
+    }
+
 }  // namespace
 
 vbm_status raster_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img, float *alpha, cudaStream_t st)
 {
-    switch (p->desc.tile_w * p->desc.tile_h) {
-        case 64: return launch_fwd<64>(p, vb, vc, bg, img, alpha, st);
-        case 128: return launch_fwd<128>(p, vb, vc, bg, img, alpha, st);
-        case 256: return launch_fwd<256>(p, vb, vc, bg, img, alpha, st);
-        default: set_error("tile_w * tile_h must be 64, 128 or 256"); return VBM_ERR_ARG;
-    }
+    VBM_RASTER_DISPATCH(launch_fwd, p, vb, vc, bg, img, alpha, st)
 }
 
 vbm_status raster_bwd(vbm_plan *p, const float *, int64_t, int vb, int vc, const float bg[3], const float *dimg,
                       const float *dalpha, float *, cudaStream_t st)
 {
     VBM_CUDA(cudaMemsetAsync(p->g_splat, 0, sizeof(float) * 9 * p->last_items, st));
-    switch (p->desc.tile_w * p->desc.tile_h) {
-        case 64: return launch_bwd<64>(p, vb, vc, bg, dimg, dalpha, st);
-        case 128: return launch_bwd<128>(p, vb, vc, bg, dimg, dalpha, st);
-        case 256: return launch_bwd<256>(p, vb, vc, bg, dimg, dalpha, st);
-        default: set_error("tile_w * tile_h must be 64, 128 or 256"); return VBM_ERR_ARG;
-    }
+    VBM_RASTER_DISPATCH(launch_bwd, p, vb, vc, bg, dimg, dalpha, st)
 }
 
 }  // namespace vbm

@@ -20,11 +20,13 @@ from oracle.raster import PJ
 pytestmark = pytest.mark.gpu
 
 
-def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0)):
+def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0),
+             ppt=0):
     params, cams_dev = to_device(P, cams)
     V = len(cams)
     so = [0, P.shape[1]] if scene_offset is None else scene_offset
-    plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap)
+    plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap,
+                    pixels_per_thread=ppt)
     img = torch.zeros((V, 3, H, W), device="cuda")
     alpha = torch.zeros((V, H, W), device="cuda")
     plan.forward(params, cams_dev, img, alpha, bg=bg)
@@ -81,12 +83,13 @@ def test_binning_bit_exact_given_gpu_depths(cuda_lib):
     assert np.array_equal(st["ranges"], ranges)
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8)])
-def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile):
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((16, 16), 2), ((16, 16), 4), ((8, 8), 2), ((16, 8), 1),
+                                      ((16, 8), 4)])
+def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt):
     W, H = 100, 76
     P, cams, cams32 = scene(seed=3, n=2500, V=2, W=W, H=H)
     bg = (0.1, 0.2, 0.05)
-    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt)
     st = plan_state(plan, 2)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(2, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -131,12 +134,13 @@ def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
     assert err.max() <= 1e-4, err.max()
 
 
-def test_backward_matches_oracle(cuda_lib):
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_backward_matches_oracle(cuda_lib, ppt):
     W, H, V = 100, 76, 2
     P, cams, cams32 = scene(seed=5, n=2000, V=V, W=W, H=H)
     n = P.shape[1]
     bg = (0.05, 0.1, 0.2)
-    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg, ppt=ppt)
     st = plan_state(plan, V)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
