@@ -288,6 +288,23 @@ VBM_API vbm_status vbm_loss(const float *d_img, const float *d_target, int n_ima
                     float lambda, double scale, double *d_loss, int32_t accumulate, float *d_dL_dimg,
                     void *d_ws, size_t ws_bytes, void *stream);
 
+/* vbm_loss without a workspace argument and without any allocation, for
+ * callers that cannot allocate device memory when they compute the loss:
+ * code running while a CUDA graph is being captured, loops whose memory
+ * budget is fixed at start-up, hosts that own only the image buffers they
+ * pass.  The paper has no counterpart; this is a deployment variant of
+ * vbm_loss with identical arguments and results minus (d_ws, ws_bytes).
+ * Scratch is a static 32 MiB device array of the library (held by every GPU
+ * that loads it, until exit): calls whose vbm_loss workspace would exceed
+ * 32 MiB return VBM_ERR_CAPACITY without launching (split the batch and use
+ * accumulate).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race;
+ * nothing in it needs clearing between calls. */
+VBM_API vbm_status vbm_loss_static(const float *d_img, const float *d_target, int n_images, int height, int width,
+                                   float lambda, double scale, double *d_loss, int32_t accumulate,
+                                   float *d_dL_dimg, void *stream);
+
 /* Adam step (Sec. 5.2) on P[14][stride], first n columns: *d_step is
  * incremented on the device and t = the new value drives the bias
  * correction; row groups {0-2, 3-5, 6-9, 10, 11-13} use lrs[0..4].

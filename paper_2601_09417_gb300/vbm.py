@@ -20,7 +20,7 @@ EXPORTED = ["vbm_last_error", "vbm_version", "vbm_bank_build", "vbm_tf_apply", "
             "vbm_build_workspace_size", "vbm_build", "vbm_render_dvr", "vbm_plan_create",
             "vbm_plan_destroy", "vbm_plan_check", "vbm_raster_fwd", "vbm_raster_bwd",
             "vbm_plan_get_buffers", "vbm_loss_workspace_size", "vbm_loss", "vbm_adam",
-            "vbm_kernel_launches", "vbm_plan_set_profile"]
+            "vbm_kernel_launches", "vbm_plan_set_profile", "vbm_loss_static"]
 
 
 class VbmError(RuntimeError):
@@ -106,6 +106,7 @@ def load():
         "vbm_loss": (I32, [V, V, I32, I32, I32, F32, F64, V, I32, V, V, S, V]),
         "vbm_adam": (I32, [V, V, V, V, I64, I64, V, ctypes.POINTER(F32 * 5), F32, F32, F32, V, V]),
         "vbm_kernel_launches": (I64, []),
+        "vbm_loss_static": (I32, [V, V, I32, I32, I32, F32, F64, V, I32, V, V]),
         "vbm_plan_set_profile": (I32, [V, ctypes.POINTER(V * 4), V]),
     }
     for name, (res, args) in sig.items():
@@ -325,6 +326,12 @@ def loss_workspace(n_images, height, width, device="cuda"):
 def loss(img, target, n_images, height, width, lam, scale, loss_out, dimg, ws, accumulate=False):
     _check(load().vbm_loss(_ptr(img), _ptr(target), n_images, height, width, float(lam), float(scale),
                            _ptr(loss_out), int(bool(accumulate)), _ptr(dimg), _ptr(ws), ws.numel(), _stream()))
+
+
+def loss_static(img, target, n_images, height, width, lam, scale, loss_out, dimg, accumulate=False):
+    """vbm_loss without a workspace: scratch lives in the library's static device array."""
+    _check(load().vbm_loss_static(_ptr(img), _ptr(target), n_images, height, width, float(lam), float(scale),
+                                  _ptr(loss_out), int(bool(accumulate)), _ptr(dimg), _stream()))
 
 
 def adam(params, grad, m, v, n, step, lrs, beta1=0.9, beta2=0.999, eps=1e-15, nonfinite=None):
