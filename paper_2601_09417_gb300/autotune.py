@@ -1,0 +1,101 @@
+"""Autotuner of the splatting launch configuration.
+
+Candidates are (tile shape, pixels per thread).  The tile shape sets how
+finely splats are binned (smaller tiles: more pairs to sort, fewer wasted
+evaluations per pixel); pixels per thread sets how many pixels of a tile
+column one thread composites and therefore the number of threads per block,
+which is also the number of list entries staged in shared memory per round.
+Each candidate runs the batch's forward and backward calls on the caller's
+own Gaussians and cameras; the fastest (median of a few timed repetitions,
+CUDA events on the current stream) wins.  Results are cached in a JSON file
+keyed by device name and workload signature.
+"""
+
+import hashlib
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import vbm
+
+CANDIDATES = [((16, 16), 1), ((16, 16), 2), ((16, 8), 1), ((16, 8), 2), ((8, 8), 1), ((8, 8), 2)]
+DEFAULT = ((16, 16), 2)
+
+
+def _cache_path():
+    return os.environ.get("VBM_AUTOTUNE_CACHE",
+                          os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json"))
+
+
+def _signature(params, n, cam_bytes, W, H, scene_offset, view_scene):
+    h = hashlib.sha256()
+    h.update(np.asarray([n, W, H], dtype=np.int64).tobytes())
+    h.update(cam_bytes)
+    h.update(np.asarray(scene_offset, dtype=np.int64).tobytes())
+    if view_scene is not None:
+        h.update(np.asarray(view_scene, dtype=np.int32).tobytes())
+    return h.hexdigest()[:16]
+
+
+def time_config(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, pair_capacity, iters=5):
+    """Median ms of one forward + backward call of the whole batch with this configuration."""
+    plan = vbm.Plan(scene_offset, n_views, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1],
+                    pair_capacity=pair_capacity, pixels_per_thread=ppt)
+    img = torch.zeros((n_views, 3, H, W), device=params.device)
+    dimg = torch.full_like(img, 1e-6)
+    grad = torch.zeros_like(params)
+    times = []
+    for it in range(iters + 2):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        plan.forward(params, cams_dev, img)
+        plan.backward(params, cams_dev, dimg, grad)
+        e.record()
+        e.synchronize()
+        if it >= 2:
+            times.append(s.elapsed_time(e))
+    ok, need = plan.check()
+    plan.close()
+    return (float(np.median(times)) if ok else float("inf")), need
+
+
+def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=None, pair_capacity=None,
+             candidates=None, use_cache=True):
+    """Best ((tile_w, tile_h), ppt) for this workload, plus the table of timings."""
+    n = int(params.shape[1] if scene_offset is None else scene_offset[-1])
+    so = [0, n] if scene_offset is None else list(scene_offset)
+    raw = np.ascontiguousarray(cam_records).view(np.uint8).tobytes()
+    dev = torch.cuda.get_device_name(params.device)
+    key = "%s|%s" % (dev, _signature(params, n, raw, W, H, so, view_scene))
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        ent = cache[key]
+        return (tuple(ent["tile"]), ent["ppt"]), ent["table"]
+    cams_dev = vbm.cameras_to_device(cam_records, params.device)
+    cap = pair_capacity if pair_capacity is not None else max(1 << 20, 64 * n * n_views)
+    cap = min(cap, (1 << 31) - 1)
+    table = []
+    for tile, ppt in (candidates or CANDIDATES):
+        ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, cap)
+        table.append({"tile": list(tile), "ppt": ppt, "ms": ms, "pairs_needed": need})
+    best = min(table, key=lambda r: r["ms"])
+    if use_cache:
+        cache[key] = {"tile": best["tile"], "ppt": best["ppt"], "table": table}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + ".%d.tmp" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return (tuple(best["tile"]), best["ppt"]), table

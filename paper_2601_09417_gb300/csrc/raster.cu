@@ -1,11 +1,12 @@
 // Front-to-back alpha compositing of the binned splats and its reverse-order
 // backward (Sec. 4.4, "as in" 3D Gaussian Splatting).
 //
-// One block per image tile.  Each thread owns PPT pixels of one tile column
-// (rows ly, ly + TH/PPT, ...), so the per-splat work that only depends on the
-// column (shared-memory loads, dx, A' dx^2, B' dx) is done once per thread,
-// and the per-pixel arithmetic of two pixels is issued as packed FP32x2
-// operations (__ffma2_rn / __fmul2_rn / __fadd2_rn, sm_100+).
+// One block per image tile.  Each thread owns PPT consecutive pixels of one
+// tile column, so the per-splat work that only depends on the column
+// (shared-memory loads, dx, A' dx^2, B' dx) is done once per thread, the
+// per-pixel arithmetic of two pixels is issued as packed FP32x2 operations
+// (__ffma2_rn / __fmul2_rn / __fadd2_rn, sm_100+), and each warp covers a
+// compact rectangle of the tile.
 //
 // A tile's depth-ordered list is staged through shared memory NT entries at a
 // time.  While staging, each entry is tested against the tile: the minimum of
@@ -15,7 +16,10 @@
 // dropped and the rest compacted in list order.  A dropped entry would have
 // been skipped by every pixel, so the image, the saved state and the
 // gradients are unchanged; the original list position travels with each
-// entry for the contributor count.
+// entry for the contributor count.  Each staged entry also carries the
+// bounding box of its alpha >= 1/255 ellipse; a warp whose pixel rectangle
+// misses that box skips the entry with one warp-uniform test (no pixel of
+// the warp could composite it).
 //
 // The conic is pre-scaled by -log2(e)/2 when staged, so the exponent is one
 // ex2.approx.ftz per (pixel, splat) pair; its rounding sequence is fixed
@@ -27,9 +31,10 @@
 // The backward walks each tile's list from the back, starting at the largest
 // contributor count of the block, recovers the transmittance by division and
 // accumulates per-(view, splat) gradients: per splat, the nine partials are
-// summed over a warp with shuffles (skipped by ballot when no lane
-// contributes), over the block through shared memory in groups of 32 splats,
-// and then added to global memory with nine atomics per (splat, tile).
+// summed over a warp by a 12-shuffle reduce-scatter (skipped by ballot when
+// no lane contributes), over the block through shared memory in groups of 32 splats,
+// and then added to global memory with nine atomics per (splat, tile).  A warp
+// also skips entries beyond the largest contributor count of its pixels.
 #include "vbm_internal.h"
 
 namespace vbm {
@@ -69,9 +74,10 @@ __device__ __forceinline__ float rect_min_quadratic(float u, float v, float A, f
 }
 
 struct TileGeom {
-    int vrel, px, py0, rows_step;
+    int vrel, px, py0;
     float pxc;
-    float x0, x1, y0, y1;   // pixel-centre rectangle of the tile (clipped to the image)
+    float x0, x1, y0, y1;       // pixel-centre rectangle of the tile (clipped to the image)
+    float wx0, wx1, wy0, wy1;   // pixel-centre rectangle of this thread's warp (clipped)
 };
 
 template <int NT, int PPT>
@@ -85,13 +91,19 @@ __device__ __forceinline__ TileGeom tile_geom(int tw, int TX, int TY, int W, int
     const int tt = blockIdx.x - t.vrel * tiles_per_view;
     const int ty = tt / TX, tx = tt - ty * TX;
     t.px = tx * tw + (int)(threadIdx.x % tw);
-    t.rows_step = th / PPT;
-    t.py0 = ty * th + (int)(threadIdx.x / tw);
+    t.py0 = ty * th + (int)(threadIdx.x / tw) * PPT;
     t.pxc = t.px + 0.5f;
     t.x0 = tx * tw + 0.5f;
     t.x1 = min(tx * tw + tw, W) - 0.5f;
     t.y0 = ty * th + 0.5f;
     t.y1 = min(ty * th + th, H) - 0.5f;
+    // a warp holds threads [32 w, 32 w + 32): whole tile rows when tw divides 32
+    const int w = threadIdx.x >> 5;
+    const int g0 = (32 * w) / tw, g1 = (32 * w + 31) / tw;
+    t.wx0 = t.x0;
+    t.wx1 = t.x1;
+    t.wy0 = ty * th + g0 * PPT + 0.5f;
+    t.wy1 = fminf((float)(ty * th + (g1 + 1) * PPT), (float)H) - 0.5f;
     return t;
 }
 
@@ -102,11 +114,12 @@ template <int NT>
 __device__ __forceinline__ int stage_entries(int base, int end, int list_begin, const uint32_t *__restrict__ pair_item,
                                              const float4 *__restrict__ geo, const float4 *__restrict__ col,
                                              const float *__restrict__ conic_c, const TileGeom &tg, float4 *s_geo,
-                                             float4 *s_col, float2 *s_cp, uint32_t *s_item, int *s_warp)
+                                             float4 *s_col, float2 *s_cp, float4 *s_box, uint32_t *s_item,
+                                             int *s_warp)
 {
     const int idx = base + (int)threadIdx.x;
     bool keep = false;
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), c = g;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), c = g, box = g;
     float cc = 0.f;
     uint32_t it = 0;
     if (idx < end) {
@@ -115,7 +128,13 @@ __device__ __forceinline__ int stage_entries(int base, int end, int list_begin, 
         cc = conic_c[it];
         c = col[it];
         const float q = rect_min_quadratic(g.x, g.y, g.z, g.w, cc, tg.x0, tg.x1, tg.y0, tg.y1);
-        keep = 0.5f * q <= logf(255.f * c.w) + kCullMargin;
+        const float tau = 2.f * (logf(255.f * c.w) + kCullMargin);
+        keep = 0.5f * q <= 0.5f * tau;
+        // bounding box of {q <= tau}: half-widths sqrt(tau C / det), sqrt(tau A / det) of the conic
+        const float det = g.z * cc - g.w * g.w;
+        const float hx = sqrtf(fmaxf(tau, 0.f) * cc / det) * 1.0001f + 1e-3f;
+        const float hy = sqrtf(fmaxf(tau, 0.f) * g.z / det) * 1.0001f + 1e-3f;
+        box = make_float4(g.x - hx, g.x + hx, g.y - hy, g.y + hy);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
@@ -134,6 +153,7 @@ __device__ __forceinline__ int stage_entries(int base, int end, int list_begin, 
         s_geo[slot] = make_float4(g.x, g.y, g.z * kHalfLog2e, g.w * kNegLog2e);
         s_cp[slot] = make_float2(cc * kHalfLog2e, __int_as_float(idx - list_begin));
         s_col[slot] = c;
+        s_box[slot] = box;
         if (s_item) s_item[slot] = it;
     }
     __syncthreads();
@@ -155,6 +175,7 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
     __shared__ float4 s_geo[NT];
     __shared__ float4 s_col[NT];
     __shared__ float2 s_cp[NT];
+    __shared__ float4 s_box[NT];
     __shared__ int s_warp[NT / 32];
     const TileGeom tg = tile_geom<NT, PPT>(tw, TX, TY, W, H);
     const int2 rg = ranges[blockIdx.x];
@@ -163,7 +184,7 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
     bool inside[PPT], done[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-        const int py = tg.py0 + k * tg.rows_step;
+        const int py = tg.py0 + k;
         pyc[k] = py + 0.5f;
         inside[k] = tg.px < W && py < H;
         done[k] = !inside[k];
@@ -178,9 +199,11 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
         for (int k = 0; k < PPT; k++) all_done &= done[k];
         if (__syncthreads_count(all_done) == NT) break;
         const int n = stage_entries<NT>(base, rg.y, rg.x, pair_item, geo, col, conic_c, tg, s_geo, s_col, s_cp,
-                                        nullptr, s_warp);
+                                        s_box, nullptr, s_warp);
         if (all_done) continue;
         for (int j = 0; j < n; j++) {
+            const float4 bx = s_box[j];
+            if (bx.y < tg.wx0 || bx.x > tg.wx1 || bx.w < tg.wy0 || bx.z > tg.wy1) continue;   // warp-uniform
             const float4 g = s_geo[j];
             const float2 cp = s_cp[j];
             const float4 c = s_col[j];
@@ -234,7 +257,7 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         if (!inside[k]) continue;
-        const int64_t pix = (int64_t)(tg.py0 + k * tg.rows_step) * W + tg.px;
+        const int64_t pix = (int64_t)(tg.py0 + k) * W + tg.px;
         img[(v * 3 + 0) * HW + pix] = C0[k] + T[k] * bg0;
         img[(v * 3 + 1) * HW + pix] = C1[k] + T[k] * bg1;
         img[(v * 3 + 2) * HW + pix] = C2[k] + T[k] * bg2;
@@ -245,11 +268,44 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
     }
 }
 
-__device__ __forceinline__ float warp_sum(float x)
+// One reduce-scatter step across lanes l and l ^ (1 << bit): for each pair
+// (a, b) of the lane's partial sums, the lane keeps a (lower half) or b (upper
+// half) and adds the partner's copy of the same element.
+template <int NP>
+__device__ __forceinline__ void rs_step(const float (&in)[2 * NP], float (&out)[NP], int bit)
 {
+    const bool hi = (threadIdx.x >> bit) & 1;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    return x;
+    for (int i = 0; i < NP; i++) {
+        const float a = in[i], b = in[NP + i];
+        const float send = hi ? a : b;
+        const float keep = hi ? b : a;
+        out[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << bit);
+    }
+}
+
+// Sums nine values over the 32 lanes of a warp with 12 shuffles (instead of
+// 45 for nine butterfly reductions).  Returns the sum of value
+// kRsIndex[lane >> 1] (lanes with an odd index hold the same sum as their
+// even neighbour); entries 15 of the table mark lanes that hold no value.
+constexpr uint64_t kRsIndex = 0xFFF8F765FF43F210ull;   // nibble m = value held by lanes 2m, 2m+1
+
+__device__ __forceinline__ int rs_value_index(int lane) { return (int)((kRsIndex >> (4 * (lane >> 1))) & 15); }
+
+__device__ __forceinline__ float reduce_scatter9(const float (&v)[9])
+{
+    const float a[10] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], 0.f};
+    float b[5];
+    rs_step<5>(a, b, 4);                       // pairs (0,5) (1,6) (2,7) (3,8) (4,-)
+    const float b6[6] = {b[0], b[1], b[2], b[3], b[4], 0.f};
+    float c[3];
+    rs_step<3>(b6, c, 3);                      // pairs (0,3) (1,4) (2,-)
+    const float c4[4] = {c[0], c[1], c[2], 0.f};
+    float d[2];
+    rs_step<2>(c4, d, 2);                      // pairs (0,2) (1,-)
+    float e[1];
+    rs_step<1>(d, e, 1);                       // pair (0,1)
+    return e[0] + __shfl_xor_sync(0xffffffffu, e[0], 1);
 }
 
 constexpr int kGroup = 32;   // splats per block-level gradient reduction
@@ -269,6 +325,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
     __shared__ float4 s_geo[NT];
     __shared__ float4 s_col[NT];
     __shared__ float2 s_cp[NT];
+    __shared__ float4 s_box[NT];
     __shared__ uint32_t s_item[NT];
     __shared__ int s_warp[NW];
     __shared__ float s_red[NW][kGroup][9];
@@ -282,7 +339,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
     int my_max = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-        const int py = tg.py0 + k * tg.rows_step;
+        const int py = tg.py0 + k;
         pyc[k] = py + 0.5f;
         T[k] = 1.f;
         dC0[k] = dC1[k] = dC2[k] = 0.f;
@@ -308,18 +365,27 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
     __syncthreads();
     const int max_nc = s_max;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp_max_nc = __reduce_max_sync(0xffffffffu, my_max);
     for (int hi = max_nc; hi > 0; hi -= NT) {
         const int lo = max(0, hi - NT);
         const int n = stage_entries<NT>(rg.x + lo, rg.x + hi, rg.x, pair_item, geo, col, conic_c, tg, s_geo, s_col,
-                                        s_cp, s_item, s_warp);
+                                        s_cp, s_box, s_item, s_warp);
         // walk the compacted batch backwards in groups of kGroup splats
         for (int g_hi = n; g_hi > 0; g_hi -= kGroup) {
             const int g_lo = max(0, g_hi - kGroup);
             for (int j = g_hi - 1; j >= g_lo; j--) {
-                const float4 g = s_geo[j];
+                const int slot = j - g_lo;
                 const float2 cp = s_cp[j];
-                const float4 c = s_col[j];
                 const int pos = __float_as_int(cp.y);
+                const float4 bx = s_box[j];
+                // warp-uniform: no pixel of this warp contributed this entry
+                if (pos >= warp_max_nc || bx.y < tg.wx0 || bx.x > tg.wx1 || bx.w < tg.wy0 || bx.z > tg.wy1) {
+                    const int vi = rs_value_index(lane);
+                    if (!(lane & 1) && vi < 9) s_red[warp][slot][vi] = 0.f;
+                    continue;
+                }
+                const float4 g = s_geo[j];
+                const float4 c = s_col[j];
                 const float dx = __fsub_rn(g.x, tg.pxc);
                 const float t0 = __fmul_rn(__fmul_rn(g.z, dx), dx);
                 const float bdx = __fmul_rn(g.w, dx);
@@ -329,22 +395,23 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
+                    if (pos >= nc[k]) continue;
                     const float dy = __fsub_rn(g.y, pyc[k]);
                     const float t = __fmaf_rn(__fmul_rn(cp.x, dy), dy, t0);
                     const float p2 = __fmaf_rn(bdx, dy, t);
                     const float G = ex2_approx(p2);
                     const float raw = __fmul_rn(c.w, G);
                     const float alpha = fminf(kAlphaMax, raw);
-                    if (pos < nc[k] && p2 <= 0.f && alpha >= kAlphaMin) {
+                    if (p2 <= 0.f && alpha >= kAlphaMin) {
                         any = true;
-                        const float om = 1.f - alpha;
-                        T[k] = T[k] / om;
+                        const float r_om = __frcp_rn(1.f - alpha);
+                        T[k] = T[k] * r_om;
                         const float wgt = alpha * T[k];
                         acc[6] += wgt * dC0[k];
                         acc[7] += wgt * dC1[k];
                         acc[8] += wgt * dC2[k];
-                        const float dLda = (c.x * T[k] * dC0[k] + c.y * T[k] * dC1[k] + c.z * T[k] * dC2[k]) -
-                                           (S0[k] * dC0[k] + S1[k] * dC1[k] + S2[k] * dC2[k] + tail[k]) / om;
+                        const float dLda = (c.x * dC0[k] + c.y * dC1[k] + c.z * dC2[k]) * T[k] -
+                                           (S0[k] * dC0[k] + S1[k] * dC1[k] + S2[k] * dC2[k] + tail[k]) * r_om;
                         S0[k] += c.x * wgt;
                         S1[k] += c.y * wgt;
                         S2[k] += c.z * wgt;
@@ -360,17 +427,9 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
                         }
                     }
                 }
-                const int slot = j - g_lo;
-                if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                    for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
-                    if (lane == 0)
-#pragma unroll
-                        for (int q = 0; q < 9; q++) s_red[warp][slot][q] = acc[q];
-                } else if (lane == 0) {
-#pragma unroll
-                    for (int q = 0; q < 9; q++) s_red[warp][slot][q] = 0.f;
-                }
+                const int vi = rs_value_index(lane);
+                const float sum = __any_sync(0xffffffffu, any) ? reduce_scatter9(acc) : 0.f;
+                if (!(lane & 1) && vi < 9) s_red[warp][slot][vi] = sum;
             }
             __syncthreads();
             const int cnt = g_hi - g_lo;
