@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--config", default="c1")
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default=None, help="WxH, skips the autotuner (with --ppt)")
+    ap.add_argument("--ppt", type=int, default=1, help="pixels per thread with --tile")
+    ap.add_argument("--persistent", action="store_true", help="persistent compositing kernels with --tile")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warmup + steps of the batched step without timing (for ncu captures)")
     return ap.parse_args()
 
 
@@ -57,27 +62,9 @@ def parse():
 
 def make_workload(cfg_key, device):
     """Volume -> Gaussians (vbm_build) and DVR targets (vbm_render_dvr), all on the GPU."""
-    import torch
-    from paper_2601_09417_gb300 import vbm
-    from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, config, orbit_cameras, volume_for_config
-    from vbm_inputs.cameras import camera_array
-    cfg = config(cfg_key)
-    F = volume_for_config(cfg)
-    G = cfg["G"]
-    dims = (G, G, G)
-    tf = vbm.make_tf(TF_KNOTS_X, TF_KNOTS_RGBA)
-    bank = vbm.bank_build(cfg["levels"], 0)
-    Fd = torch.from_numpy(F).to(device)
-    params, n = vbm.build(Fd, dims, tf, bank, vbm.make_select(cfg["K_tot"]), capacity=2 * cfg["K_tot"])
-    params = params[:, :n].contiguous()
-    cams = orbit_cameras(dims, cfg["views"], cfg["width"], cfg["height"])
-    recs = camera_array(cams)
-    cams_dev = vbm.cameras_to_device(recs, device)
-    rgba = torch.zeros((cfg["views"], 4, cfg["height"], cfg["width"]), device=device)
-    vbm.render_dvr(Fd, dims, tf, cams_dev, cfg["views"], cfg["width"], cfg["height"], 0.5, rgba)
-    targets = rgba[:, :3].contiguous()
-    torch.cuda.synchronize()
-    return cfg, F, params, n, recs, cams, targets
+    from paper_2601_09417_gb300.workloads import make_workload as build
+    w = build(cfg_key, device)
+    return w.cfg, w.volumes, w.params, w.n, w.cam_records, w.cams, w.targets
 
 
 # --------------------------------------------------------------------- clocks
@@ -190,6 +177,14 @@ def cpu_baseline(cfg, P_host, cams, targets_host):
                       "over all %d Gaussians; %.2f s per view" % (len(cams), len(cams), P_host.shape[1], t_view)}
 
 
+def _gpu_id(torch, device, local):
+    """nvidia-smi id of the device (its UUID when torch reports one)."""
+    uuid = str(getattr(torch.cuda.get_device_properties(device), "uuid", "") or "")
+    if not uuid:
+        return str(local)
+    return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the same workload, bounded samples."""
     rank = int(os.environ.get("RANK", "0"))
@@ -240,18 +235,37 @@ def main():
 
     cfg, F, params, n, recs, cams, targets = make_workload(args.config, device)
     V, H, W = cfg["views"], cfg["height"], cfg["width"]
-    ft = FineTuner(params, recs, targets, extent=cfg["G"])
+    if args.tile:
+        tile, ppt, pers, tune_table = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.persistent, []
+    else:
+        from paper_2601_09417_gb300.autotune import autotune
+        (tile, ppt, pers), tune_table = autotune(params, recs, V, W, H)
+    if args.profile_only:
+        ftp = FineTuner(params, recs, targets, extent=cfg["G"], tile=tile, ppt=ppt, persistent=pers)
+        for _ in range(args.warmup + args.steps):
+            ftp.step_batched()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_only": True, "tile": "%dx%d" % tile, "ppt": ppt, "steps": args.steps}))
+        return
+    params0 = params.clone()
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
     def flush():
         flush_buf.fill_(1)
 
-    # profiling hooks: events around the compositing kernels, recorded inside the graph
+    # ---------------------------------------------------------- batched form
+    ft = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], tile=tile, ppt=ppt, persistent=pers)
+    # profiling hooks: events around the compositing kernels (recorded inside the
+    # graph) and the per-pixel evaluated-entry count of every forward
     kev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for e in kev:          # torch creates the underlying cudaEvent on the first record
         e.record()
     torch.cuda.synchronize()
-    ft.plan.set_profile(kev)
+    n_eval = torch.zeros((V, H, W), dtype=torch.int32, device=device)
+    ft.plan.set_profile(kev, n_eval)
+    bufs = ft.plan.buffers()
+    n_contrib = vbm.device_tensor(bufs.n_contrib, (V, H, W), np.int32)
+    n_pairs_dev = vbm.device_tensor(bufs.n_pairs, (1,), np.int64)
     ft.capture()
     for _ in range(args.warmup):
         ft.step_graph()
@@ -259,22 +273,18 @@ def main():
     ok, need, bad = ft.check()
     if not ok:
         raise RuntimeError("pair capacity too small: %d needed" % need)
-
     launches0 = vbm.kernel_launches()
     ft.step_batched()
     torch.cuda.synchronize()
     launches_per_step = vbm.kernel_launches() - launches0
 
-    # ------------------------------------------------------------ timed region
-    props = torch.cuda.get_device_properties(device)
-    uuid = str(getattr(props, "uuid", "")) or str(local)
-    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else uuid))
+    clocks = ClockSampler(_gpu_id(torch, device, local))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     t_wall0 = time.perf_counter()
-    step_ms, fwd_ms, bwd_ms = [], [], []
+    step_ms, fwd_ms, bwd_ms, p_fwd, p_bwd, pairs = [], [], [], 0, 0, []
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush()
@@ -285,6 +295,9 @@ def main():
         step_ms.append(s_ev.elapsed_time(e_ev))
         fwd_ms.append(kev[0].elapsed_time(kev[1]))
         bwd_ms.append(kev[2].elapsed_time(kev[3]))
+        p_fwd += int(n_eval.sum().item())
+        p_bwd += int(n_contrib.sum().item())
+        pairs.append(int(n_pairs_dev.item()))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     if world > 1:
@@ -297,59 +310,61 @@ def main():
         total_ms = t.item()
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
+    ok, need, bad = ft.check()
+    del ft
 
-    # ----------------------------------------------------- plain (per view) form
-    plain_steps = args.plain_steps if args.plain_steps is not None else max(3, min(args.steps, 20))
-    ft.plan.set_profile(None)
-    for _ in range(2):
-        ft.step_plain()
-    plain = time_steps(ft.step_plain, plain_steps, flush)
+    # ------------------------------------------ plain form: one view per launch
+    # sequence, default tile settings, no graph; same initial state and steps
+    plain_steps = args.plain_steps if args.plain_steps is not None else args.steps
+    ftp = FineTuner(params0.clone(), recs, targets, extent=cfg["G"])
+    for _ in range(args.warmup):
+        ftp.step_plain()
+    plain = time_steps(ftp.step_plain, plain_steps, flush)
     plain_ms = sum(plain) / len(plain)
+    del ftp
 
     # ------------------------------------------------------------ end to end
+    fte = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], tile=tile, ppt=ppt, persistent=pers)
     host_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets)
     host_l = torch.empty(1, dtype=torch.float64, pin_memory=True)
-    ft.plan.set_profile(kev)
-    ft.capture()
-    for _ in range(2):
-        ft.step_host(host_t, host_l)
-    e2e = time_steps(lambda: ft.step_host(host_t, host_l), args.steps, flush)
+    fte.capture()
+    for _ in range(args.warmup):
+        fte.step_host(host_t, host_l)
+    e2e = time_steps(lambda: fte.step_host(host_t, host_l), args.steps, flush)
     e2e_ms = sum(e2e) / len(e2e)
+    del fte
 
-    # ------------------------------------------------------- algorithmic work
-    n_eval = torch.zeros((V, H, W), dtype=torch.int32, device=device)
-    ft.plan.set_profile(None, n_eval)
-    ft.plan.forward(ft.params, ft.cams, ft.img)
-    torch.cuda.synchronize()
-    st = ft.plan.buffers()
-    p_fwd = int(n_eval.sum().item())
-    p_bwd = int(vbm.device_tensor(st.n_contrib, (V, H, W), np.int32).sum().item())
-    n_pairs = int(vbm.device_tensor(st.n_pairs, (1,), np.int64).item())
+    # ------------------------------------------------------------- roofline
     f_fwd = sum(fwd_ms) / len(fwd_ms)
     f_bwd = sum(bwd_ms) / len(bwd_ms)
     peak_tflops = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     if f_bwd >= f_fwd:
-        kname, flops, kms = "raster_bwd", p_bwd * BWD_FLOP_PER_PAIR, f_bwd
+        kname, flops, kms = "raster_bwd", p_bwd * BWD_FLOP_PER_PAIR, sum(bwd_ms)
     else:
-        kname, flops, kms = "raster_fwd", p_fwd * FWD_FLOP_PER_PAIR, f_fwd
+        kname, flops, kms = "raster_fwd", p_fwd * FWD_FLOP_PER_PAIR, sum(fwd_ms)
     achieved = flops / (kms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": profiled_traffic(kname), "kernel": kname,
-                "kernel_ms": kms, "fwd_kernel_ms": f_fwd, "bwd_kernel_ms": f_bwd,
-                "pairs_fwd": p_fwd, "pairs_bwd": p_bwd,
+                "kernel_ms": kms / args.steps, "fwd_kernel_ms": f_fwd, "bwd_kernel_ms": f_bwd,
+                "pairs_fwd_per_step": p_fwd / args.steps, "pairs_bwd_per_step": p_bwd / args.steps,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock",
                 "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR}}
+    n_pairs = int(np.mean(pairs))
 
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
-                       "tile": "16x16", "pairs": n_pairs, "form": "batched, CUDA graph",
+                       "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "persistent": pers,
+                       "pairs_mean": n_pairs,
+                       "form": "batched, CUDA graph, autotuned",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "plain": {"value": 1e3 / plain_ms, "unit": "steps/s", "ms_per_step": plain_ms,
-                      "form": "one view per launch sequence, no graph"},
+                      "form": "one view per launch sequence, no graph, 16x16 tiles, default settings"},
+            "autotune": [{"tile": "%dx%d" % tuple(r["tile"]), "ppt": r["ppt"], "persistent": r["persistent"],
+                          "ms_fwd_bwd": r["ms"]} for r in tune_table],
             "batched_over_plain": plain_ms / ms_per_step,
             "raster_gpixel_per_s": V * H * W / (f_fwd * 1e-3) / 1e9,
             "e2e": {"value": 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(targets.numel() * 4),
@@ -359,7 +374,7 @@ def main():
     if clk is not None:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, ft.params.cpu().numpy(), cams, targets.cpu().numpy())
+        line["cpu_baseline"] = cpu_baseline(cfg, params0.cpu().numpy(), cams, targets.cpu().numpy())
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

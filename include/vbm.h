@@ -194,6 +194,8 @@ VBM_API vbm_status vbm_render_dvr(const float *d_volume, const int dims[3], cons
 typedef struct vbm_plan vbm_plan;
 
 #define VBM_PLAN_RECOMPUTE 1   /* keep no per-pixel state; backward recomputes it */
+#define VBM_PLAN_PERSISTENT 2  /* compositing kernels run as one persistent grid pulling tiles,
+                                  longest list first, from a work queue */
 
 /* Batch description.  Scenes are independent Gaussian sets stored as column
  * ranges [scene_offset[s], scene_offset[s+1]) of one parameter array; view v

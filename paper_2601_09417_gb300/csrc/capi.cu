@@ -171,6 +171,8 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->pair_item[0], pairs);
     ALLOC(p->pair_item[1], pairs);
     ALLOC(p->ranges, tiles);
+    ALLOC(p->tile_order, tiles);
+    ALLOC(p->tile_queue, 2);
     if (!(d->flags & VBM_PLAN_RECOMPUTE)) {
         ALLOC(p->T_final, pixels);
         ALLOC(p->n_contrib, pixels);
@@ -249,7 +251,6 @@ vbm_status vbm_raster_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     vbm_status s = check_call(p, params, stride, cams, vb, vc);
     if (s != VBM_OK) return s;
     VBM_ARG(bg && img, "null argument");
-    VBM_ARG(!(p->desc.flags & VBM_PLAN_RECOMPUTE), "recompute mode is not available for this call");
     cudaStream_t st = (cudaStream_t)stream;
     p->last_view_begin = vb;
     p->last_view_count = vc;

@@ -81,14 +81,14 @@ struct TileGeom {
 };
 
 template <int NT, int PPT>
-__device__ __forceinline__ TileGeom tile_geom(int tw, int TX, int TY, int W, int H)
+__device__ __forceinline__ TileGeom tile_geom(int tile, int tw, int TX, int TY, int W, int H)
 {
     constexpr int NPIX = NT * PPT;
     const int th = NPIX / tw;
     TileGeom t;
     const int tiles_per_view = TX * TY;
-    t.vrel = blockIdx.x / tiles_per_view;
-    const int tt = blockIdx.x - t.vrel * tiles_per_view;
+    t.vrel = tile / tiles_per_view;
+    const int tt = tile - t.vrel * tiles_per_view;
     const int ty = tt / TX, tx = tt - ty * TX;
     t.px = tx * tw + (int)(threadIdx.x % tw);
     t.py0 = ty * th + (int)(threadIdx.x / tw) * PPT;
@@ -160,15 +160,25 @@ __device__ __forceinline__ int stage_entries(int base, int end, int list_begin, 
     return total;
 }
 
-template <int NT, int PPT>
-__global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ ranges,
+// Per-pixel compositing state of a thread's pixels after the forward walk.
+template <int PPT>
+struct PixState {
+    float T[PPT];
+    int last[PPT];
+};
+
+// Forward walk of one tile.  COLOR = false computes only the per-pixel state
+// (final transmittance and last contributor), with exactly the decisions of
+// the full forward: the backward uses it when the state is not stored.
+template <int NT, int PPT, bool COLOR = true>
+__device__ __forceinline__ void fwd_tile(const int tile, const int2 *__restrict__ ranges,
                                                    const uint32_t *__restrict__ pair_item,
                                                    const float4 *__restrict__ geo, const float4 *__restrict__ col,
                                                    const float *__restrict__ conic_c, int W, int H, int tw, int TX,
                                                    int TY, int vb, float bg0, float bg1, float bg2,
                                                    float *__restrict__ img, float *__restrict__ alpha_out,
                                                    float *__restrict__ T_final, int32_t *__restrict__ n_contrib,
-                                                   int32_t *__restrict__ n_eval)
+                                                   int32_t *__restrict__ n_eval, PixState<PPT> *state = nullptr)
 {
     static_assert(PPT == 1 || PPT % 2 == 0, "pixels per thread: 1 or even");
     constexpr int STEP = PPT == 1 ? 1 : 2;
@@ -177,8 +187,8 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
     __shared__ float2 s_cp[NT];
     __shared__ float4 s_box[NT];
     __shared__ int s_warp[NT / 32];
-    const TileGeom tg = tile_geom<NT, PPT>(tw, TX, TY, W, H);
-    const int2 rg = ranges[blockIdx.x];
+    const TileGeom tg = tile_geom<NT, PPT>(tile, tw, TX, TY, W, H);
+    const int2 rg = ranges[tile];
     float pyc[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
     int last[PPT], evaluated[PPT];
     bool inside[PPT], done[PPT];
@@ -242,16 +252,26 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
                         done[kk] = true;
                         evaluated[kk] = pos + 1;
                     }
-                    const float wgt = blend ? alpha * T[kk] : 0.f;
-                    C0[kk] = __fmaf_rn(c.x, wgt, C0[kk]);
-                    C1[kk] = __fmaf_rn(c.y, wgt, C1[kk]);
-                    C2[kk] = __fmaf_rn(c.z, wgt, C2[kk]);
+                    if (COLOR) {
+                        const float wgt = blend ? alpha * T[kk] : 0.f;
+                        C0[kk] = __fmaf_rn(c.x, wgt, C0[kk]);
+                        C1[kk] = __fmaf_rn(c.y, wgt, C1[kk]);
+                        C2[kk] = __fmaf_rn(c.z, wgt, C2[kk]);
+                    }
                     T[kk] = blend ? testT : T[kk];
                     last[kk] = blend ? pos + 1 : last[kk];
                 }
             }
         }
     }
+    if (state) {
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            state->T[k] = T[k];
+            state->last[k] = last[k];
+        }
+    }
+    if (!COLOR) return;
     const int64_t HW = (int64_t)H * W;
     const int64_t v = vb + tg.vrel;
 #pragma unroll
@@ -262,8 +282,8 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(const int2 *__restrict__ rang
         img[(v * 3 + 1) * HW + pix] = C1[k] + T[k] * bg1;
         img[(v * 3 + 2) * HW + pix] = C2[k] + T[k] * bg2;
         if (alpha_out) alpha_out[v * HW + pix] = 1.f - T[k];
-        T_final[v * HW + pix] = T[k];
-        n_contrib[v * HW + pix] = last[k];
+        if (T_final) T_final[v * HW + pix] = T[k];
+        if (n_contrib) n_contrib[v * HW + pix] = last[k];
         if (n_eval) n_eval[v * HW + pix] = evaluated[k];
     }
 }
@@ -311,7 +331,7 @@ __device__ __forceinline__ float reduce_scatter9(const float (&v)[9])
 constexpr int kGroup = 32;   // splats per block-level gradient reduction
 
 template <int NT, int PPT>
-__global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ ranges,
+__device__ __forceinline__ void bwd_tile(const int tile, const int2 *__restrict__ ranges,
                                                    const uint32_t *__restrict__ pair_item,
                                                    const float4 *__restrict__ geo, const float4 *__restrict__ col,
                                                    const float *__restrict__ conic_c, int W, int H, int tw, int TX,
@@ -330,13 +350,19 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
     __shared__ int s_warp[NW];
     __shared__ float s_red[NW][kGroup][9];
     __shared__ int s_max;
-    const TileGeom tg = tile_geom<NT, PPT>(tw, TX, TY, W, H);
-    const int2 rg = ranges[blockIdx.x];
+    const TileGeom tg = tile_geom<NT, PPT>(tile, tw, TX, TY, W, H);
+    const int2 rg = ranges[tile];
     const int64_t HW = (int64_t)H * W;
     const int64_t v = vb + tg.vrel;
     float pyc[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], tail[PPT], S0[PPT], S1[PPT], S2[PPT];
     int nc[PPT];
     int my_max = 0;
+    PixState<PPT> rec;
+    if (!T_final) {   // recompute mode: replay the forward decisions of this tile
+        fwd_tile<NT, PPT, false>(tile, ranges, pair_item, geo, col, conic_c, W, H, tw, TX, TY, vb, bg0, bg1, bg2,
+                                 nullptr, nullptr, nullptr, nullptr, nullptr, &rec);
+        __syncthreads();
+    }
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         const int py = tg.py0 + k;
@@ -347,8 +373,8 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
         float dA = 0.f;
         if (tg.px < W && py < H) {
             const int64_t pix = (int64_t)py * W + tg.px;
-            T[k] = T_final[v * HW + pix];
-            nc[k] = n_contrib[v * HW + pix];
+            T[k] = T_final ? T_final[v * HW + pix] : rec.T[k];
+            nc[k] = T_final ? n_contrib[v * HW + pix] : rec.last[k];
             dC0[k] = dimg[(v * 3 + 0) * HW + pix];
             dC1[k] = dimg[(v * 3 + 1) * HW + pix];
             dC2[k] = dimg[(v * 3 + 2) * HW + pix];
@@ -445,6 +471,46 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(const int2 *__restrict__ rang
     }
 }
 
+// Kernels: one block per tile, or (PERSIST) a grid of SMs x resident blocks
+// whose blocks take tiles from an atomic queue in longest-list-first order.
+template <int NT, int PPT, bool PERSIST>
+__global__ void __launch_bounds__(NT) k_raster_fwd(const int *__restrict__ order, int *__restrict__ queue,
+                                                   int n_tiles, const int2 *__restrict__ ranges, const uint32_t *__restrict__ pair_item, const float4 *__restrict__ geo, const float4 *__restrict__ col, const float *__restrict__ conic_c, int W, int H, int tw, int TX, int TY, int vb, float bg0, float bg1, float bg2, float *__restrict__ img, float *__restrict__ alpha_out, float *__restrict__ T_final, int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval)
+{
+    if constexpr (!PERSIST) {
+        fwd_tile<NT, PPT>(blockIdx.x, ranges, pair_item, geo, col, conic_c, W, H, tw, TX, TY, vb, bg0, bg1, bg2, img, alpha_out, T_final, n_contrib, n_eval);
+    } else {
+        __shared__ int s_next;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+            __syncthreads();
+            const int q = s_next;
+            if (q >= n_tiles) return;
+            fwd_tile<NT, PPT>(order[q], ranges, pair_item, geo, col, conic_c, W, H, tw, TX, TY, vb, bg0, bg1, bg2, img, alpha_out, T_final, n_contrib, n_eval);
+        }
+    }
+}
+
+template <int NT, int PPT, bool PERSIST>
+__global__ void __launch_bounds__(NT) k_raster_bwd(const int *__restrict__ order, int *__restrict__ queue,
+                                                   int n_tiles, const int2 *__restrict__ ranges, const uint32_t *__restrict__ pair_item, const float4 *__restrict__ geo, const float4 *__restrict__ col, const float *__restrict__ conic_c, int W, int H, int tw, int TX, int TY, int vb, float bg0, float bg1, float bg2, const float *__restrict__ dimg, const float *__restrict__ dalpha, const float *__restrict__ T_final, const int32_t *__restrict__ n_contrib, float *__restrict__ gs, int64_t n_items)
+{
+    if constexpr (!PERSIST) {
+        bwd_tile<NT, PPT>(blockIdx.x, ranges, pair_item, geo, col, conic_c, W, H, tw, TX, TY, vb, bg0, bg1, bg2, dimg, dalpha, T_final, n_contrib, gs, n_items);
+    } else {
+        __shared__ int s_next;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+            __syncthreads();
+            const int q = s_next;
+            if (q >= n_tiles) return;
+            bwd_tile<NT, PPT>(order[q], ranges, pair_item, geo, col, conic_c, W, H, tw, TX, TY, vb, bg0, bg1, bg2, dimg, dalpha, T_final, n_contrib, gs, n_items);
+        }
+    }
+}
+
 int pixels_per_thread(const vbm_plan *p)
 {
     const int npix = p->desc.tile_w * p->desc.tile_h;
@@ -456,12 +522,22 @@ int pixels_per_thread(const vbm_plan *p)
 template <int NT, int PPT>
 vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img, float *alpha, cudaStream_t st)
 {
-    const int blocks = vc * p->TX * p->TY;
+    const int n_tiles = vc * p->TX * p->TY;
     record_event(p->prof_ev[0], st);
-    k_raster_fwd<NT, PPT><<<blocks, NT, 0, st>>>(p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
-                                                  p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb,
-                                                  bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib,
-                                                  p->prof_n_eval);
+    if (p->desc.flags & VBM_PLAN_PERSISTENT) {
+        static int per_sm = 0;
+        if (!per_sm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<NT, PPT, true>, NT, 0);
+        const int grid = std::max(1, std::min(n_tiles, num_sms() * std::max(per_sm, 1)));
+        k_raster_fwd<NT, PPT, true><<<grid, NT, 0, st>>>(
+            p->tile_order, p->tile_queue, n_tiles, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+            p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb, bg[0], bg[1], bg[2], img, alpha,
+            p->T_final, p->n_contrib, p->prof_n_eval);
+    } else {
+        k_raster_fwd<NT, PPT, false><<<n_tiles, NT, 0, st>>>(
+            nullptr, nullptr, n_tiles, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+            p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb, bg[0], bg[1], bg[2], img, alpha,
+            p->T_final, p->n_contrib, p->prof_n_eval);
+    }
     VBM_LAUNCH("raster_fwd");
     record_event(p->prof_ev[1], st);
     note_launches(1);
@@ -472,12 +548,22 @@ template <int NT, int PPT>
 vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const float *dimg, const float *dalpha,
                       cudaStream_t st)
 {
-    const int blocks = vc * p->TX * p->TY;
+    const int n_tiles = vc * p->TX * p->TY;
     record_event(p->prof_ev[2], st);
-    k_raster_bwd<NT, PPT><<<blocks, NT, 0, st>>>(p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
-                                                  p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb,
-                                                  bg[0], bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib,
-                                                  p->g_splat, p->last_items);
+    if (p->desc.flags & VBM_PLAN_PERSISTENT) {
+        static int per_sm = 0;
+        if (!per_sm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<NT, PPT, true>, NT, 0);
+        const int grid = std::max(1, std::min(n_tiles, num_sms() * std::max(per_sm, 1)));
+        k_raster_bwd<NT, PPT, true><<<grid, NT, 0, st>>>(
+            p->tile_order, p->tile_queue + 1, n_tiles, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col,
+            p->conic_c, p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb, bg[0], bg[1], bg[2], dimg,
+            dalpha, p->T_final, p->n_contrib, p->g_splat, p->last_items);
+    } else {
+        k_raster_bwd<NT, PPT, false><<<n_tiles, NT, 0, st>>>(
+            nullptr, nullptr, n_tiles, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+            p->desc.width, p->desc.height, p->desc.tile_w, p->TX, p->TY, vb, bg[0], bg[1], bg[2], dimg, dalpha,
+            p->T_final, p->n_contrib, p->g_splat, p->last_items);
+    }
     VBM_LAUNCH("raster_bwd");
     record_event(p->prof_ev[3], st);
     note_launches(1);

@@ -358,6 +358,36 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ tile, const int64_t *
     }
 }
 
+// Longest-list-first order of the tiles for the persistent compositing
+// kernels: tiles are grouped by floor(log2(length + 1)), longest group first
+// (order within a group is arbitrary; each tile is processed independently).
+// Also resets the two work-queue counters (forward, backward).
+__global__ void __launch_bounds__(1024) k_tile_order(const int2 *__restrict__ ranges, int n_tiles,
+                                                     int *__restrict__ order, int *__restrict__ queue)
+{
+    __shared__ int hist[32], base[32];
+    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    if (threadIdx.x < 2) queue[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const int2 r = ranges[t];
+        atomicAdd(&hist[__clz(r.y - r.x + 1)], 1);   // clz 31 = length 0 ... smaller clz = longer
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int c = 0; c < 32; c++) {
+            base[c] = run;
+            run += hist[c];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const int2 r = ranges[t];
+        order[atomicAdd(&base[__clz(r.y - r.x + 1)], 1)] = t;
+    }
+}
+
 int ceil_log2(int64_t x)
 {
     int b = 0;
@@ -420,6 +450,11 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     k_tile_ranges<<<grid, 256, 0, st>>>(p->pair_tile[p->pair_buf], p->d_n_pairs, p->ranges);
     VBM_LAUNCH("tile_ranges");
     note_launches(1);
+    if (p->desc.flags & VBM_PLAN_PERSISTENT) {
+        k_tile_order<<<1, 1024, 0, st>>>(p->ranges, (int)n_tiles, p->tile_order, p->tile_queue);
+        VBM_LAUNCH("tile_order");
+        note_launches(1);
+    }
     return VBM_OK;
 }
 

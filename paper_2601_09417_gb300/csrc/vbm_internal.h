@@ -125,6 +125,8 @@ struct vbm_plan {
     uint32_t *pair_item[2] = {nullptr, nullptr};
     int pair_buf = 0;                        // which buffer holds the sorted pairs
     int2 *ranges = nullptr;                  // [V * TX * TY]
+    int *tile_order = nullptr;               // [V * TX * TY] longest list first (persistent mode)
+    int *tile_queue = nullptr;               // [2] work-queue counters (forward, backward)
 
     // per pixel
     float *T_final = nullptr;

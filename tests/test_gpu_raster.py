@@ -21,12 +21,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0),
-             ppt=0):
+             ppt=0, persistent=False):
     params, cams_dev = to_device(P, cams)
     V = len(cams)
     so = [0, P.shape[1]] if scene_offset is None else scene_offset
     plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap,
-                    pixels_per_thread=ppt)
+                    pixels_per_thread=ppt, flags=vbm.PLAN_PERSISTENT if persistent else 0)
     img = torch.zeros((V, 3, H, W), device="cuda")
     alpha = torch.zeros((V, H, W), device="cuda")
     plan.forward(params, cams_dev, img, alpha, bg=bg)
@@ -83,13 +83,14 @@ def test_binning_bit_exact_given_gpu_depths(cuda_lib):
     assert np.array_equal(st["ranges"], ranges)
 
 
-@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((16, 16), 2), ((16, 16), 4), ((8, 8), 2), ((16, 8), 1),
-                                      ((16, 8), 4)])
-def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt):
+@pytest.mark.parametrize("tile,ppt,persistent", [((16, 16), 1, False), ((16, 16), 2, False), ((16, 16), 4, False),
+                                                 ((8, 8), 2, False), ((16, 8), 1, False), ((16, 8), 4, False),
+                                                 ((16, 16), 1, True), ((8, 8), 1, True)])
+def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt, persistent):
     W, H = 100, 76
     P, cams, cams32 = scene(seed=3, n=2500, V=2, W=W, H=H)
     bg = (0.1, 0.2, 0.05)
-    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt, persistent=persistent)
     st = plan_state(plan, 2)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(2, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -134,13 +135,13 @@ def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
     assert err.max() <= 1e-4, err.max()
 
 
-@pytest.mark.parametrize("ppt", [1, 2, 4])
-def test_backward_matches_oracle(cuda_lib, ppt):
+@pytest.mark.parametrize("ppt,persistent", [(1, False), (2, False), (4, False), (1, True)])
+def test_backward_matches_oracle(cuda_lib, ppt, persistent):
     W, H, V = 100, 76, 2
     P, cams, cams32 = scene(seed=5, n=2000, V=V, W=W, H=H)
     n = P.shape[1]
     bg = (0.05, 0.1, 0.2)
-    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg, ppt=ppt)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg, ppt=ppt, persistent=persistent)
     st = plan_state(plan, V)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -224,7 +225,8 @@ def test_uneven_multi_scene_batch(cuda_lib):
     so = np.concatenate([[0], np.cumsum(sizes)])
     view_scene = [0, 1, 1, 2, 0]
     _, cams, cams32 = scene(seed=0, n=1, V=5, W=W, H=H)
-    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, scene_offset=so, view_scene=view_scene)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, scene_offset=so, view_scene=view_scene,
+                                              persistent=True)
     ref = oraster.splat_forward(P.astype(np.float64), cams32, 16, 16, scene_offset=so, view_scene=view_scene)
     st = plan_state(plan, 5)
     assert st["n_items"] == sum(sizes[s] for s in view_scene)
@@ -264,3 +266,30 @@ def test_empty_and_culled_scenes(cuda_lib):
     P[0:3] = (R.T @ (np.array([0.0, 0.0, -5.0]) - t))[:, None]
     plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg)
     assert alpha.max() == 0 and np.allclose(img[0, 2], 0.75)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_recompute_mode_matches_stored_state(cuda_lib, persistent):
+    """VBM_PLAN_RECOMPUTE keeps no per-pixel state; the backward replays the forward's
+    decisions, so images are bit-identical and gradients equal up to atomic order."""
+    vbm = cuda_lib
+    W, H, V = 96, 80, 3
+    P, cams, cams32 = scene(seed=12, n=2000, V=V, W=W, H=H)
+    params, cams_dev = to_device(P, cams)
+    w = torch.from_numpy(np.random.default_rng(3).standard_normal((V, 3, H, W)).astype(np.float32)).cuda()
+    out = []
+    for flags in (0, vbm.PLAN_RECOMPUTE):
+        fl = flags | (vbm.PLAN_PERSISTENT if persistent else 0)
+        plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 22, flags=fl, tile_w=8, tile_h=8,
+                        pixels_per_thread=1)
+        img = torch.zeros((V, 3, H, W), device="cuda")
+        plan.forward(params, cams_dev, img)
+        grad = torch.zeros_like(params)
+        plan.backward(params, cams_dev, w, grad)
+        torch.cuda.synchronize()
+        out.append((img.cpu().numpy(), grad.cpu().numpy()))
+        if flags:
+            assert plan.buffers().T_final is None
+    assert np.array_equal(out[0][0], out[1][0])
+    nrm, elt = rel_group_error(out[1][1], out[0][1])
+    assert nrm < 1e-5 and elt < 1e-4, (nrm, elt)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import rel_group_error, scene, to_device
+from _helpers import read_device, rel_group_error, scene, to_device
 from oracle import adam as oadam
 from oracle import loss as oloss
 from oracle import raster as oraster
@@ -151,3 +151,113 @@ def test_full_step_matches_oracle_step(cuda_lib):
     d_ref = P64 - P.astype(np.float64)
     agree = np.sign(d_gpu) == np.sign(d_ref)
     assert agree.mean() > 0.97
+
+
+def test_gradient_central_differences_c1_full_size(cuda_lib):
+    """Full-size workload (128^3 volume -> ~5e4 Gaussians by vbm_build, 8 views of
+    512 x 512, DVR targets, 8 x 8 tiles): the gradient of the fine-tuning loss
+    (L1 + D-SSIM, lambda = 0.2) through the autograd Function against central
+    differences of the GPU loss on 64 sampled parameters (h = 1e-3, exact float32 step).
+    A sample is skipped where the loss is discontinuous between theta - h and theta + h:
+    the depth order of any tile's list changes, a tile rectangle moves, any pixel's
+    contributor count changes, or the perturbed Gaussian's own alpha crosses (or comes
+    within 1e-4 of) the 1/255 cut-off at a pixel of its tiles.  Tolerance: 5e-2 relative,
+    plus ten times the FP32 rounding noise of the changed pixels, plus twice the bound
+    on the L1 kink error from pixels whose residual changes sign."""
+    from paper_2601_09417_gb300.autograd import render
+    from paper_2601_09417_gb300.workloads import make_workload
+    vbm = cuda_lib
+    lam = 0.2
+    w = make_workload("c1")
+    V, H, W = w.targets.shape[0], w.targets.shape[2], w.targets.shape[3]
+    n = w.n
+    cams_dev = vbm.cameras_to_device(w.cam_records)
+    plan = vbm.Plan([0, n], V, W, H, tile_w=8, tile_h=8, pixels_per_thread=1, pair_capacity=1 << 25)
+    ws = vbm.loss_workspace(V, H, W)
+    scale = 1.0 / (V * 3 * H * W)
+
+    class Loss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, img):
+            L = torch.zeros(1, dtype=torch.float64, device="cuda")
+            d = torch.empty_like(img)
+            vbm.loss(img.contiguous(), w.targets, V, H, W, lam, scale, L, d, ws)
+            ctx.save_for_backward(d)
+            return L
+
+        @staticmethod
+        def backward(ctx, gL):
+            (d,) = ctx.saved_tensors
+            return d * gL.to(d.dtype)
+
+    P = w.params.detach().clone()
+    p = P.clone().requires_grad_(True)
+    Loss.apply(render(p, plan, cams_dev)).sum().backward()
+    g = p.grad.cpu().numpy()
+
+    def evaluate(Pt):
+        img = torch.zeros((V, 3, H, W), device="cuda")
+        plan.forward(Pt, cams_dev, img)
+        L = float(Loss.apply(img).item())
+        b = plan.buffers()
+        n_pairs = int(read_device(b.n_pairs, (1,), np.int64)[0])
+        st = dict(img=img, n_contrib=vbm.device_tensor(b.n_contrib, (V, H, W), np.int32).clone(),
+                  pair_item=vbm.device_tensor(b.pair_item, (n_pairs,), np.int32).clone(),
+                  pair_tile=vbm.device_tensor(b.pair_tile, (n_pairs,), np.int32).clone(),
+                  rect=read_device(b.rect, (b.n_items, 4), np.int32),
+                  geo=read_device(b.geo, (b.n_items, 4), np.float32),
+                  conic_c=read_device(b.conic_c, (b.n_items,), np.float32),
+                  col=read_device(b.col, (b.n_items, 4), np.float32))
+        return L, st
+
+    def own_alpha(st, item):
+        x0, y0, x1, y1 = st["rect"][item]
+        if x1 <= x0 or y1 <= y0:
+            return np.zeros(0)
+        xs = np.arange(x0 * 8, min(x1 * 8, W)) + 0.5
+        ys = np.arange(y0 * 8, min(y1 * 8, H)) + 0.5
+        Y, X = np.meshgrid(ys, xs, indexing="ij")
+        u, v_, A, B = st["geo"][item].astype(np.float64)
+        C, o = float(st["conic_c"][item]), float(st["col"][item][3])
+        dx, dy = u - X, v_ - Y
+        return o * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+
+    def same(a, b):
+        return a.shape == b.shape and bool(torch.equal(a, b))
+
+    rng = np.random.default_rng(11)
+    checked, tried = 0, 0
+    while checked < 64 and tried < 3000:
+        tried += 1
+        r, c = int(rng.integers(0, 14)), int(rng.integers(0, n))
+        if abs(g[r, c]) < 1e-2 * np.abs(g[r]).max():
+            continue
+        h = np.float32(1e-3)
+        Pp, Pm = P.clone(), P.clone()
+        Pp[r, c] += float(h)
+        Pm[r, c] -= float(h)
+        Lp, sp = evaluate(Pp)
+        Lm, sm = evaluate(Pm)
+        if not (same(sp["pair_item"], sm["pair_item"]) and same(sp["pair_tile"], sm["pair_tile"])
+                and same(sp["n_contrib"], sm["n_contrib"]) and np.array_equal(sp["rect"], sm["rect"])):
+            continue
+        flip = False
+        for v in range(V):
+            a_p, a_m = own_alpha(sp, v * n + c), own_alpha(sm, v * n + c)
+            if a_p.size and (np.minimum(np.abs(255 * a_p - 1), np.abs(255 * a_m - 1)).min() < 1e-4
+                             or np.any((a_p >= 1 / 255) != (a_m >= 1 / 255))):
+                flip = True
+                break
+        if flip:
+            continue
+        two_h = float(Pp[r, c].item()) - float(Pm[r, c].item())
+        d = sp["img"] - sm["img"]
+        changed = int(torch.count_nonzero(d).item())
+        kink = ((sp["img"] - w.targets) * (sm["img"] - w.targets) < 0)
+        kink_bound = float((d.abs() * kink).sum().item()) * (1 - lam) * scale / two_h
+        noise = np.sqrt(max(1, changed)) * 2 * 6e-8 * 3.0 * scale / two_h
+        fd = (Lp - Lm) / two_h
+        assert abs(fd - g[r, c]) <= 5e-2 * abs(g[r, c]) + 10 * noise + 2 * kink_bound, \
+            (r, c, fd, g[r, c], noise, kink_bound)
+        checked += 1
+    assert checked == 64, (checked, tried)
