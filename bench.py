@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--tile", default=None, help="WxH, skips the autotuner (with --ppt)")
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread with --tile")
     ap.add_argument("--persistent", action="store_true", help="persistent compositing kernels with --tile")
+    ap.add_argument("--gl", type=int, default=32, help="lanes per compositing group with --tile (8, 16, 32)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps of the batched step without timing (for ncu captures)")
     return ap.parse_args()
@@ -236,16 +237,19 @@ def main():
     cfg, F, params, n, recs, cams, targets = make_workload(args.config, device)
     V, H, W = cfg["views"], cfg["height"], cfg["width"]
     if args.tile:
-        tile, ppt, pers, tune_table = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.persistent, []
+        tile, ppt, gl, pers = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.gl, args.persistent
+        tune_table = []
     else:
         from paper_2601_09417_gb300.autotune import autotune
-        (tile, ppt, pers), tune_table = autotune(params, recs, V, W, H)
+        (tile, ppt, gl, pers), tune_table = autotune(params, recs, V, W, H)
+    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl)
     if args.profile_only:
-        ftp = FineTuner(params, recs, targets, extent=cfg["G"], tile=tile, ppt=ppt, persistent=pers)
+        ftp = FineTuner(params, recs, targets, extent=cfg["G"], **launch)
         for _ in range(args.warmup + args.steps):
             ftp.step_batched()
         torch.cuda.synchronize()
-        print(json.dumps({"profile_only": True, "tile": "%dx%d" % tile, "ppt": ppt, "steps": args.steps}))
+        print(json.dumps({"profile_only": True, "tile": "%dx%d" % tile, "ppt": ppt, "group_lanes": gl,
+                          "persistent": pers, "steps": args.steps}))
         return
     params0 = params.clone()
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=device)
@@ -254,7 +258,7 @@ def main():
         flush_buf.fill_(1)
 
     # ---------------------------------------------------------- batched form
-    ft = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], tile=tile, ppt=ppt, persistent=pers)
+    ft = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], **launch)
     # profiling hooks: events around the compositing kernels (recorded inside the
     # graph) and the per-pixel evaluated-entry count of every forward
     kev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -311,6 +315,19 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
     ok, need, bad = ft.check()
+
+    # forward alone (projection, binning, sort, compositing) and forward + loss +
+    # backward, all views in one call each, no graph: the Gpixel/s figures
+    def fwd_only():
+        ft.plan.forward(ft.params, ft.cams, ft.img, bg=ft.bg)
+
+    def fwd_bwd():
+        ft.plan.forward(ft.params, ft.cams, ft.img, bg=ft.bg)
+        vbm.loss(ft.img, ft.targets, V, H, W, ft.lam, ft.scale, ft.loss, ft.dimg, ft.ws)
+        ft.plan.backward(ft.params, ft.cams, ft.dimg, ft.grad, bg=ft.bg)
+    n_px = min(args.steps, 100)
+    fo = time_steps(fwd_only, n_px, flush)
+    fb = time_steps(fwd_bwd, n_px, flush)
     del ft
 
     # ------------------------------------------ plain form: one view per launch
@@ -324,7 +341,7 @@ def main():
     del ftp
 
     # ------------------------------------------------------------ end to end
-    fte = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], tile=tile, ppt=ppt, persistent=pers)
+    fte = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], **launch)
     host_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets)
     host_l = torch.empty(1, dtype=torch.float64, pin_memory=True)
@@ -356,17 +373,26 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
-                       "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "persistent": pers,
+                       "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "group_lanes": gl, "persistent": pers,
                        "pairs_mean": n_pairs,
                        "form": "batched, CUDA graph, autotuned",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "plain": {"value": 1e3 / plain_ms, "unit": "steps/s", "ms_per_step": plain_ms,
                       "form": "one view per launch sequence, no graph, 16x16 tiles, default settings"},
-            "autotune": [{"tile": "%dx%d" % tuple(r["tile"]), "ppt": r["ppt"], "persistent": r["persistent"],
-                          "ms_fwd_bwd": r["ms"]} for r in tune_table],
+            "autotune": {"candidates": len(tune_table),
+                         "fastest": [{"tile": "%dx%d" % tuple(r["tile"]), "ppt": r["ppt"],
+                                      "group_lanes": r["group_lanes"], "persistent": r["persistent"],
+                                      "ms_fwd_bwd": r["ms"]} for r in sorted(tune_table, key=lambda r: r["ms"])[:6]]},
             "batched_over_plain": plain_ms / ms_per_step,
-            "raster_gpixel_per_s": V * H * W / (f_fwd * 1e-3) / 1e9,
+            "step_ms_percentiles": {"p10": float(np.percentile(step_ms, 10)),
+                                    "p50": float(np.percentile(step_ms, 50)),
+                                    "p90": float(np.percentile(step_ms, 90))},
+            "gpixel_per_s": {"fwd": V * H * W / (float(np.median(fo)) * 1e-3) / 1e9,
+                             "fwd_loss_bwd": V * H * W / (float(np.median(fb)) * 1e-3) / 1e9,
+                             "raster_fwd_kernel": V * H * W / (f_fwd * 1e-3) / 1e9,
+                             "note": "fwd = projection + binning + sort + compositing of all views, one call, "
+                                     "median of %d; raster_fwd_kernel = the compositing kernel alone" % n_px},
             "e2e": {"value": 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(targets.numel() * 4),
                     "d2h_bytes_per_step": 8},
             "roofline": roofline, "gpu_launches": int(launches_per_step * args.steps),

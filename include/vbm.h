@@ -201,10 +201,11 @@ typedef struct vbm_plan vbm_plan;
  * ranges [scene_offset[s], scene_offset[s+1]) of one parameter array; view v
  * renders scene view_scene[v] (NULL means all views render scene 0).  Every
  * view has the same width x height.  Tiles are tile_w x tile_h pixels
- * (tile_w * tile_h in {64, 128, 256}); each compositing thread handles
- * pixels_per_thread pixels of one tile column (at least 32 threads per
- * tile).  pair_capacity bounds the number of (tile, Gaussian) pairs of one
- * call. */
+ * (tile_w 8 or 16, tile_w * tile_h in {64, 128, 256}); each compositing
+ * thread handles pixels_per_thread pixels of one tile column (at least 32
+ * threads per tile), and the threads of a warp form groups of group_lanes
+ * lanes that each walk the list entries reaching their own pixel block.
+ * pair_capacity bounds the number of (tile, Gaussian) pairs of one call. */
 typedef struct {
     int32_t n_scenes;
     int32_t n_views;
@@ -215,6 +216,7 @@ typedef struct {
     int64_t pair_capacity;
     int32_t flags;
     int32_t pixels_per_thread;     /* 0 = default (2); 1, 2 or 4 */
+    int32_t group_lanes;           /* 0 = default (32); 8, 16 or 32 lanes per compositing group */
 } vbm_plan_desc;
 
 /* Create a plan (allocates device memory, synchronous). */

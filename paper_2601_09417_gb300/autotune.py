@@ -1,12 +1,15 @@
 """Autotuner of the splatting launch configuration.
 
-Candidates are (tile shape, pixels per thread, persistent).  The tile shape sets how
-finely splats are binned (smaller tiles: more pairs to sort, fewer wasted
-evaluations per pixel); pixels per thread sets how many pixels of a tile
-column one thread composites and therefore the number of threads per block,
-which is also the number of list entries staged in shared memory per round;
-persistent runs the compositing kernels as one grid of resident blocks taking
-tiles longest-list-first from a work queue instead of one block per tile.
+Candidates are (tile shape, pixels per thread, lanes per group, persistent).
+The tile shape sets how finely splats are binned (smaller tiles: more pairs
+to sort, fewer wasted evaluations per pixel); pixels per thread sets how many
+pixels of a tile column one thread composites and therefore the number of
+threads per block, which is also the number of list entries staged in shared
+memory per round; lanes per group sets the pixel block whose own entry list a
+lane group walks (smaller groups: fewer idle lanes, more reductions per
+pixel in the backward); persistent runs the compositing kernels as one grid
+of resident blocks taking tiles longest-list-first from a work queue instead
+of one block per tile.
 Each candidate runs the batch's forward and backward calls on the caller's
 own Gaussians and cameras; the fastest (median of a few timed repetitions,
 CUDA events on the current stream) wins.  Results are cached in a JSON file
@@ -22,9 +25,13 @@ import torch
 
 from . import vbm
 
-CANDIDATES = [((16, 16), 1, False), ((16, 16), 2, False), ((16, 8), 1, False), ((16, 8), 2, False),
-              ((8, 8), 1, False), ((8, 8), 2, False), ((16, 16), 1, True), ((16, 8), 1, True), ((8, 8), 1, True)]
-DEFAULT = ((16, 16), 2, False)
+CANDIDATES = [(tile, ppt, gl, pers)
+              for tile in ((16, 16), (16, 8), (8, 8))
+              for ppt in (1, 2)
+              for gl in (8, 16, 32)
+              for pers in (False, True)]
+DEFAULT = ((16, 16), 2, 32, False)
+CACHE_FORMAT = "v2"
 
 
 def _cache_path():
@@ -42,12 +49,12 @@ def _signature(params, n, cam_bytes, W, H, scene_offset, view_scene):
     return h.hexdigest()[:16]
 
 
-def time_config(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, persistent, pair_capacity,
+def time_config(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent, pair_capacity,
                 iters=5):
     """Median ms of one forward + backward call of the whole batch with this configuration."""
     plan = vbm.Plan(scene_offset, n_views, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1],
                     pair_capacity=pair_capacity, pixels_per_thread=ppt,
-                    flags=vbm.PLAN_PERSISTENT if persistent else 0)
+                    flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=gl)
     img = torch.zeros((n_views, 3, H, W), device=params.device)
     dimg = torch.full_like(img, 1e-6)
     grad = torch.zeros_like(params)
@@ -68,12 +75,12 @@ def time_config(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile,
 
 def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=None, pair_capacity=None,
              candidates=None, use_cache=True):
-    """Best ((tile_w, tile_h), ppt, persistent) for this workload, plus the table of timings."""
+    """Best ((tile_w, tile_h), ppt, group_lanes, persistent) for this workload, plus the table of timings."""
     n = int(params.shape[1] if scene_offset is None else scene_offset[-1])
     so = [0, n] if scene_offset is None else list(scene_offset)
     raw = np.ascontiguousarray(cam_records).view(np.uint8).tobytes()
     dev = torch.cuda.get_device_name(params.device)
-    key = "%s|%s" % (dev, _signature(params, n, raw, W, H, so, view_scene))
+    key = "%s|%s|%s" % (CACHE_FORMAT, dev, _signature(params, n, raw, W, H, so, view_scene))
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -84,17 +91,19 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
             cache = {}
     if use_cache and key in cache:
         ent = cache[key]
-        return (tuple(ent["tile"]), ent["ppt"], ent["persistent"]), ent["table"]
+        return (tuple(ent["tile"]), ent["ppt"], ent["group_lanes"], ent["persistent"]), ent["table"]
     cams_dev = vbm.cameras_to_device(cam_records, params.device)
     cap = pair_capacity if pair_capacity is not None else max(1 << 20, 64 * n * n_views)
     cap = min(cap, (1 << 31) - 1)
     table = []
-    for tile, ppt, persistent in (candidates or CANDIDATES):
-        ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, persistent, cap)
-        table.append({"tile": list(tile), "ppt": ppt, "persistent": persistent, "ms": ms, "pairs_needed": need})
+    for tile, ppt, gl, persistent in (candidates or CANDIDATES):
+        ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, gl, persistent, cap)
+        table.append({"tile": list(tile), "ppt": ppt, "group_lanes": gl, "persistent": persistent, "ms": ms,
+                      "pairs_needed": need})
     best = min(table, key=lambda r: r["ms"])
     if use_cache:
-        cache[key] = {"tile": best["tile"], "ppt": best["ppt"], "persistent": best["persistent"], "table": table}
+        cache[key] = {"tile": best["tile"], "ppt": best["ppt"], "group_lanes": best["group_lanes"],
+                      "persistent": best["persistent"], "table": table}
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             tmp = path + ".%d.tmp" % os.getpid()
@@ -103,4 +112,4 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
             os.replace(tmp, path)
         except OSError:
             pass
-    return (tuple(best["tile"]), best["ppt"], best["persistent"]), table
+    return (tuple(best["tile"]), best["ppt"], best["group_lanes"], best["persistent"]), table

@@ -79,7 +79,7 @@ extern "C" {
 
 const char *vbm_last_error(void) { return g_last_error.c_str(); }
 
-int vbm_version(void) { return 100; }
+int vbm_version(void) { return 101; }
 
 int64_t vbm_kernel_launches(void) { return g_launches.load(); }
 
@@ -99,8 +99,10 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     VBM_ARG(d->n_scenes == 1 || d->view_scene != nullptr, "view_scene is required with several scenes");
     VBM_ARG(d->width > 0 && d->height > 0, "image size must be positive");
     const int tp = d->tile_w * d->tile_h;
-    VBM_ARG(d->tile_w > 0 && d->tile_h > 0 && (tp == 64 || tp == 128 || tp == 256),
-            "tile_w * tile_h must be 64, 128 or 256");
+    VBM_ARG((d->tile_w == 8 || d->tile_w == 16) && d->tile_h > 0 && (tp == 64 || tp == 128 || tp == 256),
+            "tile_w must be 8 or 16 and tile_w * tile_h 64, 128 or 256");
+    VBM_ARG(d->group_lanes == 0 || d->group_lanes == 8 || d->group_lanes == 16 || d->group_lanes == 32,
+            "group_lanes must be 0, 8, 16 or 32");
     VBM_ARG(d->pair_capacity > 0 && d->pair_capacity < ((int64_t)1 << 31), "pair_capacity out of range");
     VBM_ARG(d->pixels_per_thread == 0 || d->pixels_per_thread == 1 || d->pixels_per_thread == 2 ||
                 d->pixels_per_thread == 4,
@@ -172,12 +174,12 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->pair_item[1], pairs);
     ALLOC(p->ranges, tiles);
     ALLOC(p->tile_order, tiles);
-    ALLOC(p->tile_queue, 2);
+    ALLOC(p->tile_queue, kTileQueueWords);
     if (!(d->flags & VBM_PLAN_RECOMPUTE)) {
         ALLOC(p->T_final, pixels);
         ALLOC(p->n_contrib, pixels);
     }
-    p->sort_scratch.blocks = num_sms() * 2;
+    p->sort_scratch.blocks = num_sms() * 8;
     ALLOC(p->sort_scratch.hist, radix_sort_hist_words(p->sort_scratch.blocks));
     if (s == VBM_OK) p->sort_scratch.digit_total = p->sort_scratch.hist + 256 * (size_t)p->sort_scratch.blocks;
     p->scan_scratch.blocks = num_sms() * 2;

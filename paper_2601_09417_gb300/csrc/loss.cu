@@ -2,13 +2,18 @@
 // lambda (1 - SSIM), SSIM with an 11x11 Gaussian window (sigma 1.5), zero
 // padding, per colour plane (Sec. 4.4 computes the loss "as in" 3DGS).
 //
-// Two tiled passes over each plane, both with the separable window staged in
-// shared memory (a 32 x 16 output tile plus a 5-pixel halo):
+// Two tiled passes over each plane, each staging a 32 x 32 output tile plus a
+// 5-pixel halo in shared memory and applying the separable window as a
+// horizontal then a vertical pass:
 //   1. the five windowed moments of x and y -> per-pixel SSIM and the three
-//      maps its gradient needs (written to the workspace), plus per-block
-//      partial sums of |x - y| and SSIM;
+//      maps its gradient needs (written to the workspace as a float2 and a
+//      float plane), plus per-block sums of |x - y| and SSIM;
 //   2. windowed sums of those maps -> dL/dx per pixel.
-// A final one-block kernel adds the partial sums in double in a fixed order,
+// In both passes a thread slides the window along a row segment (horizontal)
+// or a column segment (vertical) held in registers, so each staged value is
+// read from shared memory once per pass; the moment pairs (x, y), (x^2, y^2)
+// and the map pair (g1, g2) are accumulated with packed FP32x2 FMAs.
+// A final one-block kernel adds the per-block sums in double in a fixed order,
 // so the loss value is deterministic.
 #include <cmath>
 
@@ -19,146 +24,236 @@ namespace {
 
 constexpr int kWin = 11;
 constexpr int kHalf = 5;
-constexpr int kTW = 32, kTH = 16;                  // output tile
+constexpr int kTW = 32, kTH = 32;                  // output tile
 constexpr int kSW = kTW + 2 * kHalf, kSH = kTH + 2 * kHalf;
-constexpr int kLossThreads = 256;
+constexpr int kSWP = kSW + 2;                      // padded row of the staged tile (zero-filled)
+constexpr int kSeg = 11, kSegs = 3;                // horizontal: 3 segments of <= 11 outputs per row
+constexpr int kVRows = 8;                          // vertical: 8 outputs per column segment
+constexpr int kLossThreads = 128;
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
+static_assert(kSegs * kSeg >= kTW && kSH * kSegs <= kLossThreads, "horizontal tasks");
+static_assert(kTW * (kTH / kVRows) == kLossThreads, "vertical tasks");
+static_assert((kSegs - 1) * kSeg + kSeg + kWin - 1 <= kSWP, "staged row covers the last segment");
 
 __constant__ float c_win[kWin];
 
-struct LossWs {
-    float *g1, *g2, *g3;
-    double *partial;   // [blocks][2]: sum |x - y|, sum ssim
-};
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Stage plane values (or value pairs) of rows [oy - 5, oy + kTH + 5) and columns
+// [ox - 5, ox + kTW + 5) into s[kSH][kSWP]; outside the image (and the pad
+// columns) they are zero.  Every load of a thread is issued before the first
+// store, so a block has all its staging loads in flight at once.
+constexpr int kStageIters = (kSH * kSWP + kLossThreads - 1) / kLossThreads;
+
+template <typename T, typename F>
+__device__ __forceinline__ void stage_tile(T (*s)[kSWP], int ox, int oy, int H, int W, F load)
+{
+    T val[kStageIters];
+#pragma unroll
+    for (int it = 0; it < kStageIters; it++) {
+        const int i = threadIdx.x + it * kLossThreads;
+        const int r = i / kSWP, c = i - r * kSWP;
+        const int gy = oy + r - kHalf, gx = ox + c - kHalf;
+        const bool in = i < kSH * kSWP && c < kSW && gy >= 0 && gy < H && gx >= 0 && gx < W;
+        val[it] = load(in, (int64_t)gy * W + gx);
+    }
+#pragma unroll
+    for (int it = 0; it < kStageIters; it++) {
+        const int i = threadIdx.x + it * kLossThreads;
+        if (i < kSH * kSWP) s[i / kSWP][i % kSWP] = val[it];
+    }
+}
 
 __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y,
-                                                          int H, int W, float *__restrict__ g1,
-                                                          float *__restrict__ g2, float *__restrict__ g3,
-                                                          double *__restrict__ partial)
+                                                          int H, int W, float2 *__restrict__ g12,
+                                                          float *__restrict__ g3, double *__restrict__ partial)
 {
-    __shared__ float sx[kSH][kSW], sy[kSH][kSW];
-    __shared__ float hs[5][kSH][kTW];
-    __shared__ double red[2][kLossThreads];
+    __shared__ __align__(16) float2 sxy[kSH][kSWP];
+    __shared__ __align__(16) float2 hm[kSH][kTW];   // horizontal sums of (x, y)
+    __shared__ __align__(16) float2 hq[kSH][kTW];   // of (x^2, y^2)
+    __shared__ float hp[kSH][kTW];                   // of x y
+    __shared__ float red[2][kLossThreads / 32];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kTW, oy = blockIdx.y * kTH;
     const int64_t base = (int64_t)plane * H * W;
-    for (int i = threadIdx.x; i < kSH * kSW; i += blockDim.x) {
-        const int r = i / kSW, c = i - r * kSW;
-        const int gy = oy + r - kHalf, gx = ox + c - kHalf;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        sx[r][c] = in ? x[base + (int64_t)gy * W + gx] : 0.f;
-        sy[r][c] = in ? y[base + (int64_t)gy * W + gx] : 0.f;
-    }
+    const float *xp = x + base, *yp = y + base;
+    stage_tile(sxy, ox, oy, H, W, [&](bool in, int64_t e) {
+        return in ? make_float2(xp[e], yp[e]) : make_float2(0.f, 0.f);
+    });
     __syncthreads();
-    for (int i = threadIdx.x; i < kSH * kTW; i += blockDim.x) {
-        const int r = i / kTW, c = i - r * kTW;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    const int t = threadIdx.x;
+    if (t < kSH * kSegs) {
+        const int r = t / kSegs, c0 = (t - r * kSegs) * kSeg;
+        float2 v[kSeg + kWin - 1], sq[kSeg + kWin - 1];
+        float pr[kSeg + kWin - 1];
 #pragma unroll
-        for (int k = 0; k < kWin; k++) {
-            const float w = c_win[k], xv = sx[r][c + k], yv = sy[r][c + k];
-            a += w * xv;
-            b += w * yv;
-            aa += w * xv * xv;
-            bb += w * yv * yv;
-            ab += w * xv * yv;
+        for (int j = 0; j < kSeg + kWin - 1; j++) {
+            v[j] = sxy[r][c0 + j];
+            sq[j] = __fmul2_rn(v[j], v[j]);
+            pr[j] = v[j].x * v[j].y;
         }
-        hs[0][r][c] = a; hs[1][r][c] = b; hs[2][r][c] = aa; hs[3][r][c] = bb; hs[4][r][c] = ab;
+#pragma unroll
+        for (int o = 0; o < kSeg; o++) {
+            float2 m = make_float2(0.f, 0.f), q = m;
+            float p = 0.f;
+#pragma unroll
+            for (int k = 0; k < kWin; k++) {
+                const float w = c_win[k];
+                m = __ffma2_rn(f2(w), v[o + k], m);
+                q = __ffma2_rn(f2(w), sq[o + k], q);
+                p = fmaf(w, pr[o + k], p);
+            }
+            if (c0 + o < kTW) {
+                hm[r][c0 + o] = m;
+                hq[r][c0 + o] = q;
+                hp[r][c0 + o] = p;
+            }
+        }
     }
     __syncthreads();
-    double l1 = 0.0, ss = 0.0;
-    for (int i = threadIdx.x; i < kTH * kTW; i += blockDim.x) {
-        const int r = i / kTW, c = i - r * kTW;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    const int c = t & 31, r0 = (t >> 5) * kVRows;
+    float l1 = 0.f, ss = 0.f;
+    float2 m_in[kVRows + kWin - 1], q_in[kVRows + kWin - 1];
+    float p_in[kVRows + kWin - 1];
+#pragma unroll
+    for (int j = 0; j < kVRows + kWin - 1; j++) {
+        m_in[j] = hm[r0 + j][c];
+        q_in[j] = hq[r0 + j][c];
+        p_in[j] = hp[r0 + j][c];
+    }
+    const int gx = ox + c;
+#pragma unroll
+    for (int o = 0; o < kVRows; o++) {
+        float2 m = make_float2(0.f, 0.f), q = m;
+        float p = 0.f;
 #pragma unroll
         for (int k = 0; k < kWin; k++) {
             const float w = c_win[k];
-            mx += w * hs[0][r + k][c];
-            my += w * hs[1][r + k][c];
-            exx += w * hs[2][r + k][c];
-            eyy += w * hs[3][r + k][c];
-            exy += w * hs[4][r + k][c];
+            m = __ffma2_rn(f2(w), m_in[o + k], m);
+            q = __ffma2_rn(f2(w), q_in[o + k], q);
+            p = fmaf(w, p_in[o + k], p);
         }
-        const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
+        const int gy = oy + r0 + o;
+        if (gy >= H || gx >= W) continue;
+        const float mx = m.x, my = m.y;
+        const float vx = q.x - mx * mx, vy = q.y - my * my, cxy = p - mx * my;
         const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
         const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
         const float iB1 = 1.f / B1, iB2 = 1.f / B2;
         const float ssim = A1 * A2 * iB1 * iB2;
         const int64_t e = base + (int64_t)gy * W + gx;
-        g1[e] = 2.f * my * (A2 - A1) * iB1 * iB2 - 2.f * mx * ssim * (iB1 - iB2);
-        g2[e] = -ssim * iB2;
+        g12[e] = make_float2(2.f * my * (A2 - A1) * iB1 * iB2 - 2.f * mx * ssim * (iB1 - iB2), -ssim * iB2);
         g3[e] = 2.f * A1 * iB1 * iB2;
-        l1 += fabs((double)sx[r + kHalf][c + kHalf] - (double)sy[r + kHalf][c + kHalf]);
+        const float2 xy = sxy[r0 + o + kHalf][c + kHalf];
+        l1 += fabsf(xy.x - xy.y);
         ss += ssim;
     }
-    red[0][threadIdx.x] = l1;
-    red[1][threadIdx.x] = ss;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < (unsigned)off) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + off];
-            red[1][threadIdx.x] += red[1][threadIdx.x + off];
-        }
-        __syncthreads();
+    l1 = warp_sum(l1);
+    ss = warp_sum(ss);
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = l1;
+        red[1][t >> 5] = ss;
     }
-    if (threadIdx.x == 0) {
-        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partial[2 * b] = red[0][0];
-        partial[2 * b + 1] = red[1][0];
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int w = 0; w < kLossThreads / 32; w++) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partial[2 * blk] = a;
+        partial[2 * blk + 1] = b;
     }
 }
 
 __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y,
-                                                          int H, int W, const float *__restrict__ g1,
-                                                          const float *__restrict__ g2, const float *__restrict__ g3,
-                                                          float lambda, float scale, float *__restrict__ dx)
+                                                          int H, int W, const float2 *__restrict__ g12,
+                                                          const float *__restrict__ g3, float lambda, float scale,
+                                                          float *__restrict__ dx)
 {
-    __shared__ float s[3][kSH][kSW];
-    __shared__ float hs[3][kSH][kTW];
+    __shared__ __align__(16) float2 s12[kSH][kSWP];   // (g1, g2) with halo
+    __shared__ float s3[kSH][kSWP];                   // g3 with halo
+    __shared__ __align__(16) float2 h12[kSH][kTW];
+    __shared__ float h3[kSH][kTW];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kTW, oy = blockIdx.y * kTH;
     const int64_t base = (int64_t)plane * H * W;
-    for (int i = threadIdx.x; i < kSH * kSW; i += blockDim.x) {
-        const int r = i / kSW, c = i - r * kSW;
-        const int gy = oy + r - kHalf, gx = ox + c - kHalf;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const int64_t e = base + (int64_t)gy * W + gx;
-        s[0][r][c] = in ? g1[e] : 0.f;
-        s[1][r][c] = in ? g2[e] : 0.f;
-        s[2][r][c] = in ? g3[e] : 0.f;
+    const float2 *p12 = g12 + base;
+    const float *p3 = g3 + base;
+    stage_tile(s12, ox, oy, H, W, [&](bool in, int64_t e) { return in ? p12[e] : make_float2(0.f, 0.f); });
+    stage_tile(s3, ox, oy, H, W, [&](bool in, int64_t e) { return in ? p3[e] : 0.f; });
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < kSH * kSegs) {
+        const int r = t / kSegs, c0 = (t - r * kSegs) * kSeg;
+        float2 a[kSeg + kWin - 1];
+        float b[kSeg + kWin - 1];
+#pragma unroll
+        for (int j = 0; j < kSeg + kWin - 1; j++) {
+            a[j] = s12[r][c0 + j];
+            b[j] = s3[r][c0 + j];
+        }
+#pragma unroll
+        for (int o = 0; o < kSeg; o++) {
+            float2 m = make_float2(0.f, 0.f);
+            float d = 0.f;
+#pragma unroll
+            for (int k = 0; k < kWin; k++) {
+                const float w = c_win[k];
+                m = __ffma2_rn(f2(w), a[o + k], m);
+                d = fmaf(w, b[o + k], d);
+            }
+            if (c0 + o < kTW) {
+                h12[r][c0 + o] = m;
+                h3[r][c0 + o] = d;
+            }
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSH * kTW; i += blockDim.x) {
-        const int r = i / kTW, c = i - r * kTW;
-        float a = 0.f, b = 0.f, d = 0.f;
+    const int c = t & 31, r0 = (t >> 5) * kVRows;
+    float2 a_in[kVRows + kWin - 1];
+    float b_in[kVRows + kWin - 1];
+#pragma unroll
+    for (int j = 0; j < kVRows + kWin - 1; j++) {
+        a_in[j] = h12[r0 + j][c];
+        b_in[j] = h3[r0 + j][c];
+    }
+    const int gx = ox + c;
+    float xs[kVRows], ys[kVRows];
+#pragma unroll
+    for (int o = 0; o < kVRows; o++) {     // issue the pixel loads first
+        const int gy = oy + r0 + o;
+        const bool in = gy < H && gx < W;
+        const int64_t e = base + (int64_t)gy * W + gx;
+        xs[o] = in ? x[e] : 0.f;
+        ys[o] = in ? y[e] : 0.f;
+    }
+#pragma unroll
+    for (int o = 0; o < kVRows; o++) {
+        float2 m = make_float2(0.f, 0.f);
+        float d = 0.f;
 #pragma unroll
         for (int k = 0; k < kWin; k++) {
             const float w = c_win[k];
-            a += w * s[0][r][c + k];
-            b += w * s[1][r][c + k];
-            d += w * s[2][r][c + k];
+            m = __ffma2_rn(f2(w), a_in[o + k], m);
+            d = fmaf(w, b_in[o + k], d);
         }
-        hs[0][r][c] = a; hs[1][r][c] = b; hs[2][r][c] = d;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kTH * kTW; i += blockDim.x) {
-        const int r = i / kTW, c = i - r * kTW;
-        const int gy = oy + r, gx = ox + c;
+        const int gy = oy + r0 + o;
         if (gy >= H || gx >= W) continue;
-        float a = 0.f, b = 0.f, d = 0.f;
-#pragma unroll
-        for (int k = 0; k < kWin; k++) {
-            const float w = c_win[k];
-            a += w * hs[0][r + k][c];
-            b += w * hs[1][r + k][c];
-            d += w * hs[2][r + k][c];
-        }
         const int64_t e = base + (int64_t)gy * W + gx;
-        const float xv = x[e], yv = y[e];
+        const float xv = xs[o], yv = ys[o];
         const float diff = xv - yv;
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        const float dssim = a + 2.f * xv * b + yv * d;
+        const float dssim = m.x + 2.f * xv * m.y + yv * d;
         dx[e] = scale * ((1.f - lambda) * sgn - lambda * dssim);
     }
 }
@@ -228,13 +323,14 @@ vbm_status loss_fwd_bwd(const float *img, const float *target, int n_images, int
     if (s != VBM_OK) return s;
     const size_t n = (size_t)n_images * 3 * H * W;
     char *p = (char *)ws;
-    float *g1 = (float *)p, *g2 = g1 + n, *g3 = g2 + n;
+    float2 *g12 = (float2 *)p;
+    float *g3 = (float *)(g12 + n);
     size_t off = (3 * n * sizeof(float) + 255) / 256 * 256;
     double *partial = (double *)(p + off);
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, n_images * 3);
-    k_ssim_fwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g1, g2, g3, partial);
+    k_ssim_fwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g12, g3, partial);
     VBM_LAUNCH("ssim_fwd");
-    k_ssim_bwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g1, g2, g3, lambda, (float)scale, dimg);
+    k_ssim_bwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g12, g3, lambda, (float)scale, dimg);
     VBM_LAUNCH("ssim_bwd");
     k_loss_final<<<1, 256, 0, st>>>(partial, (int64_t)grid.x * grid.y * grid.z, (double)n, (double)lambda, scale,
                                     loss, accumulate);

@@ -16,6 +16,8 @@
 // in a CUDA graph without knowing the pair count on the host.  No kernel
 // waits on another block: the radix sort is reduce-then-scan (upsweep
 // histograms, one scan block, downsweep scatter).
+#include <algorithm>
+
 #include "vbm_internal.h"
 
 namespace vbm {
@@ -36,6 +38,9 @@ __device__ __forceinline__ int64_t chunk_of(int64_t n, int blocks)
 
 // Per-block digit histogram of keys in the block's chunk: hist[d * blocks + b],
 // and the per-digit totals over all blocks (digit_total, zeroed before).
+// Equal digits within a warp are counted with one shared-memory atomic
+// (__match_any_sync groups them), so keys that share their high bits do not
+// serialise on one counter.
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                                 const int64_t *__restrict__ d_n, int shift,
                                                                 uint32_t *__restrict__ hist,
@@ -48,8 +53,20 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
     const int64_t chunk = chunk_of(n, gridDim.x);
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(n, beg + chunk);
-    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x)
-        atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = beg; b < end; b += kSortTile) {       // uniform trip count across the block
+        uint32_t d[kSortItems];
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {           // all loads of the tile first
+            const int64_t i = b + it * kSortThreads + threadIdx.x;
+            d[it] = i < end ? (keys[i] >> shift) & (kRadix - 1) : (uint32_t)(kRadix + lane);
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
+            if (d[it] < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d[it]], (uint32_t)__popc(peers));
+        }
+    }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
         hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
@@ -113,11 +130,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_offsets(uint32_t *__rest
     }
 }
 
-// Stable scatter of the block's chunk, tile by tile.  Within a tile, warp w
-// owns elements [w * 32 * kSortItems, (w + 1) * 32 * kSortItems) and walks
-// them 32 at a time; the rank of an element among equal digits is
-// (elements of that digit in earlier tiles of this block) + (in earlier
-// warps of this tile) + (earlier in this warp), found with __match_any_sync.
+// Stable scatter of the block's chunk, one tile of kSortTile elements at a
+// time.  Ranking: within a tile, warp w owns elements [w * 32 * kSortItems,
+// (w + 1) * 32 * kSortItems) and walks them 32 at a time; the rank of an
+// element among equal digits of the warp is (earlier iterations of this warp)
+// + (earlier lanes of this iteration, from __match_any_sync).  The tile is
+// then exchanged through shared memory into digit order (digit start in the
+// tile + elements of that digit in earlier warps + rank), and written out
+// with consecutive threads on consecutive elements, so each digit's run of
+// the tile goes to global memory as contiguous stores.
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
                                                                   const uint32_t *__restrict__ vals_in,
                                                                   uint32_t *__restrict__ keys_out,
@@ -125,20 +146,25 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
                                                                   const int64_t *__restrict__ d_n, int shift,
                                                                   const uint32_t *__restrict__ hist)
 {
-    __shared__ uint32_t run[kRadix];
-    __shared__ uint32_t tile_total[kRadix];
+    static_assert(kSortThreads == kRadix, "one thread per digit in the per-tile digit scans");
+    __shared__ uint32_t run[kRadix];        // global position of the next element of each digit
+    __shared__ uint32_t tstart[kRadix];     // first position of each digit in the exchanged tile
     __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    __shared__ uint32_t s_key[kSortTile];
+    __shared__ uint32_t s_val[kSortTile];
+    __shared__ uint32_t warp_sums[32];
     const int64_t n = *d_n;
     const int64_t chunk = chunk_of(n, gridDim.x);
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = min(n, beg + chunk);
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] = hist[(int64_t)d * gridDim.x + blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (beg >= end) return;                 // uniform across the block
+    const int t = threadIdx.x;
+    run[t] = hist[(int64_t)t * gridDim.x + blockIdx.x];
+    const int warp = t >> 5, lane = t & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (int64_t tbase = beg; tbase < end; tbase += kSortTile) {
-        for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
 #pragma unroll
-            for (int w = 0; w < kSortWarps; w++) wcnt[w][d] = 0;
+        for (int w = 0; w < kSortWarps; w++) wcnt[w][t] = 0;
         __syncthreads();
         uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
         const int64_t wbase = tbase + (int64_t)warp * 32 * kSortItems;
@@ -148,43 +174,51 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
             const bool valid = i < end;
             k[it] = valid ? keys_in[i] : 0u;
             v[it] = valid ? vals_in[i] : 0u;
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            rank[it] = 0;
-            if (valid) {
-                const uint32_t d = (k[it] >> shift) & (kRadix - 1);
-                const uint32_t peers = __match_any_sync(vmask, d);
-                const int leader = __ffs(peers) - 1;
-                const uint32_t prior = wcnt[warp][d];
-                rank[it] = prior + __popc(peers & lt_mask);
-                __syncwarp(vmask);
-                if (lane == leader) wcnt[warp][d] = prior + __popc(peers);
-            }
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int64_t i = wbase + it * 32 + lane;
+            const bool valid = i < end;
+            const uint32_t d = valid ? (k[it] >> shift) & (kRadix - 1) : (uint32_t)(kRadix + lane);
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t prior = valid ? wcnt[warp][d] : 0u;
+            rank[it] = prior + __popc(peers & lt_mask);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = prior + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-            uint32_t s = 0;
+        // thread t = digit t: exclusive offsets over the warps, then over the digits
+        uint32_t tot = 0;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; w++) {
-                const uint32_t c = wcnt[w][d];
-                wcnt[w][d] = s;
-                s += c;
-            }
-            tile_total[d] = s;
+        for (int w = 0; w < kSortWarps; w++) {
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = tot;
+            tot += c;
         }
+        tstart[t] = block_exclusive_scan(tot, warp_sums, nullptr);
         __syncthreads();
 #pragma unroll
         for (int it = 0; it < kSortItems; it++) {
             const int64_t i = wbase + it * 32 + lane;
             if (i < end) {
                 const uint32_t d = (k[it] >> shift) & (kRadix - 1);
-                const uint32_t pos = run[d] + wcnt[warp][d] + rank[it];
-                keys_out[pos] = k[it];
-                vals_out[pos] = v[it];
+                const uint32_t lpos = tstart[d] + wcnt[warp][d] + rank[it];
+                s_key[lpos] = k[it];
+                s_val[lpos] = v[it];
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] += tile_total[d];
+        const int cnt = (int)min((int64_t)kSortTile, end - tbase);
+        for (int i = t; i < cnt; i += kSortThreads) {
+            const uint32_t key = s_key[i];
+            const uint32_t d = (key >> shift) & (kRadix - 1);
+            const uint32_t pos = run[d] + (uint32_t)i - tstart[d];
+            keys_out[pos] = key;
+            vals_out[pos] = s_val[i];
+        }
+        __syncthreads();
+        run[t] += tot;
         __syncthreads();
     }
 }
@@ -361,30 +395,63 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ tile, const int64_t *
 // Longest-list-first order of the tiles for the persistent compositing
 // kernels: tiles are grouped by floor(log2(length + 1)), longest group first
 // (order within a group is arbitrary; each tile is processed independently).
-// Also resets the two work-queue counters (forward, backward).
-__global__ void __launch_bounds__(1024) k_tile_order(const int2 *__restrict__ ranges, int n_tiles,
-                                                     int *__restrict__ order, int *__restrict__ queue)
+// Two grid-stride kernels over the tiles: group sizes, then placement.  Lanes
+// of a warp with the same group share one atomic.  The scratch q holds the two
+// work-queue counters (q[0], q[1]), the group sizes (q[2 + g]) and the group
+// cursors (q[34 + g]); it is zeroed before the first kernel.
+constexpr int kOrderThreads = 256;
+
+__device__ __forceinline__ int tile_group(const int2 *__restrict__ ranges, int t, int n_tiles, int lane)
 {
-    __shared__ int hist[32], base[32];
+    if (t >= n_tiles) return 32 + lane;                 // no group: unique per lane
+    const int2 r = ranges[t];
+    return __clz(r.y - r.x + 1);                        // 31 = length 0; smaller = longer
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *__restrict__ ranges, int n_tiles,
+                                                                    int *__restrict__ q)
+{
+    __shared__ int hist[32];
     if (threadIdx.x < 32) hist[threadIdx.x] = 0;
-    if (threadIdx.x < 2) queue[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        const int2 r = ranges[t];
-        atomicAdd(&hist[__clz(r.y - r.x + 1)], 1);   // clz 31 = length 0 ... smaller clz = longer
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * kOrderThreads;
+    for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {   // uniform per block
+        const int g = tile_group(ranges, t0 + (int)threadIdx.x, n_tiles, lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, g);
+        if (g < 32 && lane == __ffs(peers) - 1) atomicAdd(&hist[g], __popc(peers));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int c = 0; c < 32; c++) {
-            base[c] = run;
-            run += hist[c];
+    if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&q[2 + threadIdx.x], hist[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_group_place(const int2 *__restrict__ ranges, int n_tiles,
+                                                                    int *__restrict__ q, int *__restrict__ order)
+{
+    __shared__ int base[32];
+    if (threadIdx.x < 32) {
+        const int c = q[2 + threadIdx.x];
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if ((int)threadIdx.x >= off) incl += y;
         }
+        base[threadIdx.x] = incl - c;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        const int2 r = ranges[t];
-        order[atomicAdd(&base[__clz(r.y - r.x + 1)], 1)] = t;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int stride = gridDim.x * kOrderThreads;
+    for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {
+        const int t = t0 + (int)threadIdx.x;
+        const int g = tile_group(ranges, t, n_tiles, lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, g);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (g < 32 && lane == leader) first = atomicAdd(&q[34 + g], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (g < 32) order[base[g] + first + __popc(peers & lt_mask)] = t;
     }
 }
 
@@ -404,12 +471,15 @@ int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, i
 {
     int cur = 0;
     if (n_max <= 0) return cur;
+    // fixed grid for the largest count this call can see (graph capture), at
+    // most s.blocks; with fewer elements the trailing blocks have empty chunks
+    const int blocks = (int)std::min<int64_t>(s.blocks, (n_max + kSortTile - 1) / kSortTile);
     for (int shift = 0; shift < bits; shift += kRadixBits) {
         cudaMemsetAsync(s.digit_total, 0, kRadix * sizeof(uint32_t), st);
-        k_radix_upsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], d_n, shift, s.hist, s.digit_total);
-        k_radix_offsets<<<kRadix, kSortThreads, 0, st>>>(s.hist, s.digit_total, s.blocks);
-        k_radix_downsweep<<<s.blocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], d_n,
-                                                             shift, s.hist);
+        k_radix_upsweep<<<blocks, kSortThreads, 0, st>>>(keys[cur], d_n, shift, s.hist, s.digit_total);
+        k_radix_offsets<<<kRadix, kSortThreads, 0, st>>>(s.hist, s.digit_total, blocks);
+        k_radix_downsweep<<<blocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], d_n,
+                                                           shift, s.hist);
         cur = 1 - cur;
         note_launches(3);
     }
@@ -451,9 +521,14 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     VBM_LAUNCH("tile_ranges");
     note_launches(1);
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
-        k_tile_order<<<1, 1024, 0, st>>>(p->ranges, (int)n_tiles, p->tile_order, p->tile_queue);
-        VBM_LAUNCH("tile_order");
-        note_launches(1);
+        VBM_CUDA(cudaMemsetAsync(p->tile_queue, 0, kTileQueueWords * sizeof(int), st));
+        const int64_t og_need = (n_tiles + kOrderThreads - 1) / kOrderThreads;
+        const int og = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 2, og_need));
+        k_tile_group_count<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue);
+        VBM_LAUNCH("tile_group_count");
+        k_tile_group_place<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->tile_order);
+        VBM_LAUNCH("tile_group_place");
+        note_launches(2);
     }
     return VBM_OK;
 }

@@ -69,10 +69,12 @@ FilterBank make_filters(int wavelet);
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs over the low
 // `bits` bits of the key; the element count is read from d_n on the device.
 // Results end in (keys[0], vals[0]) or (keys[1], vals[1]): the returned index.
+constexpr int kTileQueueWords = 2 + 32 + 32;
+
 struct SortScratch {
     uint32_t *hist = nullptr;          // radix * blocks counters
     uint32_t *digit_total = nullptr;   // radix counters (inside the same allocation)
-    int blocks = 0;                    // <= 1024
+    int blocks = 0;                    // largest sort grid (hist has radix x blocks counters)
 };
 size_t radix_sort_hist_words(int blocks);
 int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,
@@ -126,7 +128,8 @@ struct vbm_plan {
     int pair_buf = 0;                        // which buffer holds the sorted pairs
     int2 *ranges = nullptr;                  // [V * TX * TY]
     int *tile_order = nullptr;               // [V * TX * TY] longest list first (persistent mode)
-    int *tile_queue = nullptr;               // [2] work-queue counters (forward, backward)
+    int *tile_queue = nullptr;               // [kTileQueueWords]: work-queue counters (forward, backward),
+                                             // then tile-group sizes and cursors of the ordering
 
     // per pixel
     float *T_final = nullptr;

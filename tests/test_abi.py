@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert hasattr(handle, n), n
     assert names == set(lib.EXPORTED)
-    assert lib.version() == 100
+    assert lib.version() == 101
 
 
 def test_struct_sizes_match_header(lib):

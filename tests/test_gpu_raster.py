@@ -21,12 +21,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0),
-             ppt=0, persistent=False):
+             ppt=0, persistent=False, gl=0):
     params, cams_dev = to_device(P, cams)
     V = len(cams)
     so = [0, P.shape[1]] if scene_offset is None else scene_offset
     plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap,
-                    pixels_per_thread=ppt, flags=vbm.PLAN_PERSISTENT if persistent else 0)
+                    pixels_per_thread=ppt, flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=gl)
     img = torch.zeros((V, 3, H, W), device="cuda")
     alpha = torch.zeros((V, H, W), device="cuda")
     plan.forward(params, cams_dev, img, alpha, bg=bg)
@@ -83,14 +83,19 @@ def test_binning_bit_exact_given_gpu_depths(cuda_lib):
     assert np.array_equal(st["ranges"], ranges)
 
 
-@pytest.mark.parametrize("tile,ppt,persistent", [((16, 16), 1, False), ((16, 16), 2, False), ((16, 16), 4, False),
-                                                 ((8, 8), 2, False), ((16, 8), 1, False), ((16, 8), 4, False),
-                                                 ((16, 16), 1, True), ((8, 8), 1, True)])
-def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt, persistent):
+@pytest.mark.parametrize("tile,ppt,persistent,gl", [((16, 16), 1, False, 32), ((16, 16), 2, False, 32),
+                                                    ((16, 16), 4, False, 32), ((8, 8), 2, False, 32),
+                                                    ((16, 8), 1, False, 32), ((16, 8), 4, False, 32),
+                                                    ((16, 16), 1, True, 32), ((8, 8), 1, True, 32),
+                                                    ((8, 8), 1, True, 8), ((8, 8), 1, False, 16),
+                                                    ((16, 16), 1, False, 8), ((16, 16), 2, True, 16),
+                                                    ((16, 8), 4, False, 8), ((8, 8), 2, False, 8)])
+def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt, persistent, gl):
     W, H = 100, 76
     P, cams, cams32 = scene(seed=3, n=2500, V=2, W=W, H=H)
     bg = (0.1, 0.2, 0.05)
-    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt, persistent=persistent)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt, persistent=persistent,
+                                      gl=gl)
     st = plan_state(plan, 2)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(2, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -135,13 +140,15 @@ def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
     assert err.max() <= 1e-4, err.max()
 
 
-@pytest.mark.parametrize("ppt,persistent", [(1, False), (2, False), (4, False), (1, True)])
-def test_backward_matches_oracle(cuda_lib, ppt, persistent):
+@pytest.mark.parametrize("ppt,persistent,gl", [(1, False, 32), (2, False, 32), (4, False, 32), (1, True, 32),
+                                               (1, False, 8), (1, True, 16), (2, False, 8), (4, True, 16)])
+def test_backward_matches_oracle(cuda_lib, ppt, persistent, gl):
     W, H, V = 100, 76, 2
     P, cams, cams32 = scene(seed=5, n=2000, V=V, W=W, H=H)
     n = P.shape[1]
     bg = (0.05, 0.1, 0.2)
-    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg, ppt=ppt, persistent=persistent)
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg, ppt=ppt, persistent=persistent,
+                                              gl=gl)
     st = plan_state(plan, V)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -226,7 +233,7 @@ def test_uneven_multi_scene_batch(cuda_lib):
     view_scene = [0, 1, 1, 2, 0]
     _, cams, cams32 = scene(seed=0, n=1, V=5, W=W, H=H)
     plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, scene_offset=so, view_scene=view_scene,
-                                              persistent=True)
+                                              persistent=True, gl=8)
     ref = oraster.splat_forward(P.astype(np.float64), cams32, 16, 16, scene_offset=so, view_scene=view_scene)
     st = plan_state(plan, 5)
     assert st["n_items"] == sum(sizes[s] for s in view_scene)
@@ -268,8 +275,8 @@ def test_empty_and_culled_scenes(cuda_lib):
     assert alpha.max() == 0 and np.allclose(img[0, 2], 0.75)
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_recompute_mode_matches_stored_state(cuda_lib, persistent):
+@pytest.mark.parametrize("persistent,gl", [(False, 32), (True, 32), (True, 8)])
+def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl):
     """VBM_PLAN_RECOMPUTE keeps no per-pixel state; the backward replays the forward's
     decisions, so images are bit-identical and gradients equal up to atomic order."""
     vbm = cuda_lib
@@ -281,7 +288,7 @@ def test_recompute_mode_matches_stored_state(cuda_lib, persistent):
     for flags in (0, vbm.PLAN_RECOMPUTE):
         fl = flags | (vbm.PLAN_PERSISTENT if persistent else 0)
         plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 22, flags=fl, tile_w=8, tile_h=8,
-                        pixels_per_thread=1)
+                        pixels_per_thread=1, group_lanes=gl)
         img = torch.zeros((V, 3, H, W), device="cuda")
         plan.forward(params, cams_dev, img)
         grad = torch.zeros_like(params)

@@ -81,7 +81,7 @@ def spectral_noise(G, amp_exponent, k_range, seed):
     amp[band] = kmag[band] ** (-amp_exponent)
     phase = rng.uniform(0.0, 2.0 * np.pi, size=kmag.shape)
     spec = amp * np.exp(1j * phase)
-    field = np.fft.irfftn(spec, s=(G, G, G))
+    field = np.fft.irfftn(spec, s=(G, G, G), axes=(0, 1, 2))
     field -= field.mean()
     std = field.std()
     if std > 0:
