@@ -62,10 +62,18 @@ def parse():
 # ------------------------------------------------------------------ workload
 
 def make_workload(cfg_key, device):
-    """Volume -> Gaussians (vbm_build) and DVR targets (vbm_render_dvr), all on the GPU."""
+    """Volume(s) -> Gaussians (vbm_build) and DVR targets (vbm_render_dvr), all on the GPU."""
     from paper_2601_09417_gb300.workloads import make_workload as build
-    w = build(cfg_key, device)
-    return w.cfg, w.volumes, w.params, w.n, w.cam_records, w.cams, w.targets
+    return build(cfg_key, device)
+
+
+def workload_extent(cfg):
+    """Scene extent for the learning rate of the means (largest volume edge)."""
+    return max(cfg["edges"]) if "edges" in cfg else cfg["G"]
+
+
+# Oracle timing window for workloads whose full view would take minutes on one core.
+CPU_CROP = {"c4": 256}
 
 
 # --------------------------------------------------------------------- clocks
@@ -155,27 +163,47 @@ def profiled_traffic(kernel):
 
 # ------------------------------------------------------------- cpu baseline
 
-def cpu_baseline(cfg, P_host, cams, targets_host):
-    """FP64 oracle, one view of the step plus Adam over all Gaussians, scaled to a step."""
+def cpu_baseline(cfg, w, P_host, targets_host):
+    """FP64 oracle on the host: one view of the step (projection, binning, compositing, loss,
+    backward; a centred window of it for the largest workloads, scaled by pixel count) times
+    the number of views, plus Adam over all Gaussians."""
     from oracle import adam as oadam
     from oracle import loss as oloss
     from oracle import raster as oraster
     from vbm_inputs.cameras import cameras_as_float32
-    c32 = cameras_as_float32(cams)
-    P64 = P_host.astype(np.float64)
+    V = len(w.cams)
+    so = [0, w.n] if w.scene_offset is None else [int(x) for x in w.scene_offset]
+    s0 = 0 if w.view_scene is None else int(w.view_scene[0])
+    P64 = P_host[:, so[s0]:so[s0 + 1]].astype(np.float64)
+    cam = dict(cameras_as_float32(w.cams)[0])
+    H, W = targets_host.shape[2], targets_host.shape[3]
+    tgt = targets_host[:1].astype(np.float64)
+    crop = CPU_CROP.get(cfg["key"])
+    scale = 1.0
+    if crop and crop < min(W, H):
+        x0, y0 = (W - crop) // 2, (H - crop) // 2
+        cam["cx"] -= x0
+        cam["cy"] -= y0
+        cam["width"] = cam["height"] = crop
+        tgt = tgt[:, :, y0:y0 + crop, x0:x0 + crop]
+        scale = (W * H) / float(crop * crop)
     t0 = time.perf_counter()
-    fwd = oraster.splat_forward(P64, [c32[0]])
-    _, dimg = oloss.loss_and_grad(fwd["img"], targets_host[:1].astype(np.float64))
-    dimg *= 1.0 / len(cams)
-    grad, _, _ = oraster.splat_backward(fwd, P64, [c32[0]], dimg)
-    t_view = time.perf_counter() - t0
+    fwd = oraster.splat_forward(P64, [cam])
+    _, dimg = oloss.loss_and_grad(fwd["img"], tgt)
+    dimg *= 1.0 / V
+    oraster.splat_backward(fwd, P64, [cam], dimg)
+    t_view = (time.perf_counter() - t0) * scale
     t1 = time.perf_counter()
-    oadam.adam_step(P64, grad, np.zeros_like(P64), np.zeros_like(P64), 1, oadam.default_lrs(cfg["G"]))
+    P_all = P_host.astype(np.float64)
+    oadam.adam_step(P_all, np.zeros_like(P_all), np.zeros_like(P_all), np.zeros_like(P_all), 1,
+                    oadam.default_lrs(workload_extent(cfg)))
     t_adam = time.perf_counter() - t1
-    t_step = len(cams) * t_view + t_adam
+    t_step = V * t_view + t_adam
+    what = ("a %dx%d window of 1 of %d views (x%.0f for the full view)" % (crop, crop, V, scale)
+            if scale != 1.0 else "1 of %d views" % V)
     return {"value": 1.0 / t_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": "1 of %d views (projection, binning, compositing, loss, backward) timed, x%d, plus Adam "
-                      "over all %d Gaussians; %.2f s per view" % (len(cams), len(cams), P_host.shape[1], t_view)}
+            "sample": "%s (projection, binning, compositing, loss, backward) timed, x%d, plus Adam over all %d "
+                      "Gaussians; %.2f s per view" % (what, V, P_host.shape[1], t_view)}
 
 
 def _gpu_id(torch, device, local):
@@ -197,12 +225,13 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "workload inputs are built on the GPU"}))
         return
     torch.cuda.set_device(device)
-    cfg, F, params, n, recs, cams, targets = make_workload(args.config, device)
-    P = params.cpu().numpy()
-    T = targets.cpu().numpy()
+    w = make_workload(args.config, device)
+    cfg, n = w.cfg, w.n
+    P = w.params.cpu().numpy()
+    T = w.targets.cpu().numpy()
     vals = []
     for _ in range(max(1, min(args.steps, 3))):
-        vals.append(cpu_baseline(cfg, P, cams, T))
+        vals.append(cpu_baseline(cfg, w, P, T))
     v = statistics.median([x["value"] for x in vals])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True,
@@ -234,17 +263,20 @@ def main():
     torch.cuda.set_device(device)
     vbm.load()
 
-    cfg, F, params, n, recs, cams, targets = make_workload(args.config, device)
-    V, H, W = cfg["views"], cfg["height"], cfg["width"]
+    w = make_workload(args.config, device)
+    cfg, params, n, recs, cams, targets = w.cfg, w.params, w.n, w.cam_records, w.cams, w.targets
+    V, H, W = targets.shape[0], targets.shape[2], targets.shape[3]
+    batch = dict(scene_offset=w.scene_offset, view_scene=w.view_scene, extent=workload_extent(cfg))
     if args.tile:
         tile, ppt, gl, pers = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.gl, args.persistent
         tune_table = []
     else:
         from paper_2601_09417_gb300.autotune import autotune
-        (tile, ppt, gl, pers), tune_table = autotune(params, recs, V, W, H)
+        (tile, ppt, gl, pers), tune_table = autotune(params, recs, V, W, H, scene_offset=w.scene_offset,
+                                                      view_scene=w.view_scene)
     launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl)
     if args.profile_only:
-        ftp = FineTuner(params, recs, targets, extent=cfg["G"], **launch)
+        ftp = FineTuner(params, recs, targets, **batch, **launch)
         for _ in range(args.warmup + args.steps):
             ftp.step_batched()
         torch.cuda.synchronize()
@@ -258,7 +290,7 @@ def main():
         flush_buf.fill_(1)
 
     # ---------------------------------------------------------- batched form
-    ft = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], **launch)
+    ft = FineTuner(params0.clone(), recs, targets, **batch, **launch)
     # profiling hooks: events around the compositing kernels (recorded inside the
     # graph) and the per-pixel evaluated-entry count of every forward
     kev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -333,7 +365,7 @@ def main():
     # ------------------------------------------ plain form: one view per launch
     # sequence, default tile settings, no graph; same initial state and steps
     plain_steps = args.plain_steps if args.plain_steps is not None else args.steps
-    ftp = FineTuner(params0.clone(), recs, targets, extent=cfg["G"])
+    ftp = FineTuner(params0.clone(), recs, targets, **batch)
     for _ in range(args.warmup):
         ftp.step_plain()
     plain = time_steps(ftp.step_plain, plain_steps, flush)
@@ -341,7 +373,7 @@ def main():
     del ftp
 
     # ------------------------------------------------------------ end to end
-    fte = FineTuner(params0.clone(), recs, targets, extent=cfg["G"], **launch)
+    fte = FineTuner(params0.clone(), recs, targets, **batch, **launch)
     host_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets)
     host_l = torch.empty(1, dtype=torch.float64, pin_memory=True)
@@ -351,6 +383,29 @@ def main():
     e2e = time_steps(lambda: fte.step_host(host_t, host_l), args.steps, flush)
     e2e_ms = sum(e2e) / len(e2e)
     del fte
+
+    # --------------------------------------- forward-only frames (single view)
+    fwd_only = None
+    if cfg.get("fwd_only") and w.scene_offset is None:
+        from vbm_inputs import orbit_cameras
+        from vbm_inputs.cameras import camera_array
+        fw, fh = cfg["fwd_only"]
+        cams1 = orbit_cameras((cfg["G"],) * 3, 1, fw, fh)
+        cd1 = vbm.cameras_to_device(camera_array(cams1), device)
+        plan1 = vbm.Plan([0, n], 1, fw, fh, tile_w=tile[0], tile_h=tile[1], pixels_per_thread=ppt, group_lanes=gl,
+                         flags=vbm.PLAN_PERSISTENT if pers else 0, pair_capacity=min((1 << 31) - 1, 64 * n))
+        img1 = torch.zeros((1, 3, fh, fw), device=device)
+
+        def frame():
+            plan1.forward(params0, cd1, img1)
+        for _ in range(max(3, args.warmup)):
+            frame()
+        fo_ms = time_steps(frame, min(args.steps, 100), flush)
+        ok1, need1 = plan1.check()
+        fwd_only = {"image": "%dx%d" % (fw, fh), "frames_per_s": 1e3 / float(np.median(fo_ms)),
+                    "ms_per_frame": float(np.median(fo_ms)), "pairs_ok": bool(ok1),
+                    "form": "projection + binning + sort + compositing of one view, one call"}
+        plan1.close()
 
     # ------------------------------------------------------------- roofline
     f_fwd = sum(fwd_ms) / len(fwd_ms)
@@ -397,10 +452,12 @@ def main():
                     "d2h_bytes_per_step": 8},
             "roofline": roofline, "gpu_launches": int(launches_per_step * args.steps),
             "wall_s_timed": wall}
+    if fwd_only is not None:
+        line["fwd_only"] = fwd_only
     if clk is not None:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, params0.cpu().numpy(), cams, targets.cpu().numpy())
+        line["cpu_baseline"] = cpu_baseline(cfg, w, params0.cpu().numpy(), targets.cpu().numpy())
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

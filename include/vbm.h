@@ -272,7 +272,7 @@ typedef struct {
     const int64_t *n_pairs;   /* device scalar                                     */
     const float *T_final;     /* [V][H][W] (absolute views; NULL in recompute mode) */
     const int32_t *n_contrib; /* [V][H][W]                                         */
-    const float *g_splat;     /* [9][n_items] after a backward: du dv dA dB dC dopac dr dg db */
+    const float *g_splat;     /* [n_items][12] after a backward: du dv dA dB dC dopac dr dg db, 3 unused */
 } vbm_plan_buffers;
 
 VBM_API vbm_status vbm_plan_get_buffers(vbm_plan *plan, vbm_plan_buffers *out);

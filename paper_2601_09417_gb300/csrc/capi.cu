@@ -158,6 +158,7 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->geo, items);
     ALLOC(p->col, items);
     ALLOC(p->conic_c, items);
+    ALLOC(p->cull, items);
     ALLOC(p->depth, items);
     ALLOC(p->rect, items);
     ALLOC(p->radius, items);
@@ -167,7 +168,7 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->valA[0], items);
     ALLOC(p->valA[1], items);
     ALLOC(p->offsets, items + 1);
-    ALLOC(p->g_splat, 9 * items);
+    ALLOC(p->g_splat, kGradStride * items);
     ALLOC(p->pair_tile[0], pairs);
     ALLOC(p->pair_tile[1], pairs);
     ALLOC(p->pair_item[0], pairs);

@@ -101,7 +101,7 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                                  const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
                                  const int64_t *__restrict__ view_item_offset, int vb, int TX, int TY, int tw, int th,
                                  float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
-                                 float *__restrict__ depth, int4 *__restrict__ rect, int32_t *__restrict__ radius,
+                                 float4 *__restrict__ cull, float *__restrict__ depth, int4 *__restrict__ rect, int32_t *__restrict__ radius,
                                  uint32_t *__restrict__ touched, uint32_t *__restrict__ keyA,
                                  uint32_t *__restrict__ valA)
 {
@@ -140,6 +140,13 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
         float vv = cam.fy * (st.t[1] / st.t[2]) + cam.cy;
         geo[item] = make_float4(u, vv, A, B);
         conic_c[item] = C;
+        // For the compositing kernels' culling: the bounding box of
+        // {q <= tau}, tau = 2 (ln(255 o) + margin), has half-widths
+        // sqrt(tau a) and sqrt(tau c) (the conic's determinant is 1 / det),
+        // slightly widened; and the ratios of the edge minimisers.
+        const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
+        cull[item] = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f,
+                                 -st.b / st.a, -st.b / st.c);
         r_int = (int)r;
         int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
         int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
@@ -151,6 +158,7 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     } else {
         geo[item] = make_float4(0.f, 0.f, 0.f, 0.f);
         conic_c[item] = 0.f;
+        cull[item] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     rect[item] = rc;
     radius[item] = r_int;
@@ -189,7 +197,7 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
         const int64_t item = view_item_offset[v] - view_item_offset[vb] + gl;
         float g9[9];
 #pragma unroll
-        for (int k = 0; k < 9; k++) g9[k] = gs[k * n_items + item];
+        for (int k = 0; k < 9; k++) g9[k] = gs[item * kGradStride + k];
         const vbm_camera cam = cams[v];
         ProjState st;
         project_state(P, stride, g, cam, st);
@@ -287,7 +295,8 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     k_preprocess_fwd<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
                                               p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
                                               p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
-                                              p->desc.tile_h, p->geo, p->col, p->conic_c, p->depth, p->rect,
+                                              p->desc.tile_h, p->geo, p->col, p->conic_c, p->cull, p->depth,
+                                              p->rect,
                                               p->radius, p->touched, p->keyA[0], p->valA[0]);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);

@@ -22,6 +22,11 @@ constexpr float kEigFloor = 0.1f;       // lambda_max = mid + sqrt(max(0.1, mid^
 constexpr float kRadiusSigmas = 3.0f;   // r = ceil(3 sqrt(lambda_max))
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
+// Natural-log margin of the compositing kernels' culling tests (far above the
+// rounding of the quantities compared).
+constexpr float kCullMargin = 1e-3f;
+// Floats per item of the splat-gradient records: du dv dA dB dC dopacity dr dg db, padding.
+constexpr int kGradStride = 12;
 constexpr float kTMin = 1e-4f;
 constexpr float kCoordClamp = 1e7f;
 
@@ -113,6 +118,7 @@ struct vbm_plan {
     float4 *geo = nullptr;
     float4 *col = nullptr;
     float *conic_c = nullptr;
+    float4 *cull = nullptr;                  // [items] half-widths of the alpha >= 1/255 box, B / C, B / A
     float *depth = nullptr;
     int4 *rect = nullptr;
     int32_t *radius = nullptr;
@@ -120,7 +126,7 @@ struct vbm_plan {
     uint32_t *keyA[2] = {nullptr, nullptr};
     uint32_t *valA[2] = {nullptr, nullptr};
     int64_t *offsets = nullptr;             // [items + 1]
-    float *g_splat = nullptr;               // [6][items]
+    float *g_splat = nullptr;               // [items][kGradStride]
 
     // pairs
     uint32_t *pair_tile[2] = {nullptr, nullptr};

@@ -47,7 +47,7 @@ def plan_state(plan, n_views):
     if b.T_final:
         st["T_final"] = read_device(b.T_final, (plan.n_views, plan.height, plan.width), np.float32)
         st["n_contrib"] = read_device(b.n_contrib, (plan.n_views, plan.height, plan.width), np.int32)
-    st["g_splat"] = read_device(b.g_splat, (9, n), np.float32)
+    st["g_splat"] = np.ascontiguousarray(read_device(b.g_splat, (n, 12), np.float32)[:, :9].T)
     return st
 
 

@@ -1,0 +1,153 @@
+"""GPU parity at the full workload sizes, on samples the oracle can compute.
+
+  * c2 (256^3 turbulence, ~5e5 Gaussians, 16 views of 800x800), c3 (32 uneven
+    volumes, 128 views of 256x256, one batch) and c4 (512^3 shells, ~2.9e6
+    Gaussians, 8 views of 1024x1024, compositing state recomputed in the
+    backward): the FP64 oracle composites a random sample of tiles from the
+    GPU's own splat records and tile lists; images must agree to 1e-4 on those
+    tiles (pixels within 1e-5 of a cut-off excepted) and, with dL/dimg nonzero
+    on those tiles only, every per-splat gradient to 1e-3;
+  * the pair list of view 0 equals, bit for bit, the oracle's (tile, depth,
+    index) sort of the GPU's rectangles and depths;
+  * c1 (128^3, ~1e5 Gaussians): vbm_build's pyramid, kept indices and
+    Gaussians against the oracle's build at full size.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from _helpers import rel_group_error
+from oracle import raster as oraster
+
+pytestmark = pytest.mark.gpu
+
+
+def _take(vbm, ptr, shape, dtype, index):
+    """Rows `index` (host int64) of a plan buffer, copied to the host."""
+    t = vbm.device_tensor(ptr, shape, dtype)
+    return t[torch.from_numpy(index).cuda()].cpu().numpy()
+
+
+def _sample_tiles(ranges, n, rng):
+    nonempty = np.nonzero(ranges[:, 1] > ranges[:, 0])[0]
+    return np.sort(rng.choice(nonempty, size=min(n, nonempty.size), replace=False))
+
+
+@pytest.mark.parametrize("key,tile,ppt,gl,recompute", [("c2", (16, 8), 1, 16, False),
+                                                        ("c3", (16, 16), 2, 8, False),
+                                                        ("c4", (8, 8), 1, 16, True)])
+def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
+    from paper_2601_09417_gb300.workloads import make_workload
+    vbm = cuda_lib
+    w = make_workload(key)
+    V, H, W = w.targets.shape[0], w.targets.shape[2], w.targets.shape[3]
+    so = [0, w.n] if w.scene_offset is None else w.scene_offset
+    cams_dev = vbm.cameras_to_device(w.cam_records)
+    flags = vbm.PLAN_PERSISTENT | (vbm.PLAN_RECOMPUTE if recompute else 0)
+    plan = vbm.Plan(so, V, W, H, view_scene=w.view_scene, tile_w=tile[0], tile_h=tile[1], pixels_per_thread=ppt,
+                    group_lanes=gl, flags=flags, pair_capacity=min((1 << 31) - 1, 16 * w.n * V + (1 << 22)))
+    bg = (0.05, 0.1, 0.2)
+    img = torch.zeros((V, 3, H, W), device="cuda")
+    plan.forward(w.params, cams_dev, img, bg=bg)
+    ok, need = plan.check()
+    assert ok, need
+    b = plan.buffers()
+    TX, TY = (W + tile[0] - 1) // tile[0], (H + tile[1] - 1) // tile[1]
+    n_tiles = V * TX * TY
+    ranges = vbm.device_tensor(b.ranges, (n_tiles, 2), np.int32).cpu().numpy()
+    n_pairs = int(vbm.device_tensor(b.n_pairs, (1,), np.int64).item())
+    pair_item = vbm.device_tensor(b.pair_item, (n_pairs,), np.int32)
+    # --- binning of view 0, bit-exact given the GPU's rectangles and depths
+    n0 = int(so[1]) if w.view_scene is None else int(so[int(w.view_scene[0]) + 1] - so[int(w.view_scene[0])])
+    rect0 = vbm.device_tensor(b.rect, (n0, 4), np.int32).cpu().numpy()
+    depth0 = vbm.device_tensor(b.depth, (n0,), np.float32).cpu().numpy().astype(np.float64)
+    tiles0, items0, _ = oraster.bin_sort(np.zeros(n0, dtype=np.int32), rect0, depth0, TX, TY, 1)
+    end0 = int(ranges[:TX * TY, 1].max())
+    assert end0 == tiles0.size
+    assert np.array_equal(vbm.device_tensor(b.pair_tile, (end0,), np.int32).cpu().numpy(), tiles0)
+    assert np.array_equal(pair_item[:end0].cpu().numpy(), items0)
+    # --- sampled tiles: compact lists and the splats they reference
+    rng = np.random.default_rng(7)
+    sel = _sample_tiles(ranges, 48, rng)
+    lists = [pair_item[ranges[t, 0]:ranges[t, 1]].cpu().numpy().astype(np.int64) for t in sel]
+    used = np.unique(np.concatenate(lists))
+    remap = {int(it): i for i, it in enumerate(used)}
+    items_c, ranges_c = [], np.zeros((n_tiles, 2), dtype=np.int32)
+    for t, lst in zip(sel, lists):
+        ranges_c[t] = (len(items_c), len(items_c) + lst.size)
+        items_c.extend(remap[int(it)] for it in lst)
+    n_items = b.n_items
+    g = _take(vbm, b.geo, (n_items, 4), np.float32, used).astype(np.float64)
+    cc = _take(vbm, b.conic_c, (n_items,), np.float32, used).astype(np.float64)
+    col = _take(vbm, b.col, (n_items, 4), np.float32, used).astype(np.float64)
+    splat = np.stack([g[:, 0], g[:, 1], g[:, 2], g[:, 3], cc, col[:, 3]], axis=1)
+    ref = oraster.render(V, W, H, tile[0], tile[1], ranges_c, np.asarray(items_c, dtype=np.int32), splat,
+                         col[:, :3], np.array(bg))
+    pix = np.zeros((V, H, W), dtype=bool)
+    for t in sel:
+        v, tt = divmod(int(t), TX * TY)
+        ty, tx = divmod(tt, TX)
+        pix[v, ty * tile[1]:(ty + 1) * tile[1], tx * tile[0]:(tx + 1) * tile[0]] = True
+    good = pix & (ref["margin"] > 1e-5)
+    assert good.sum() > 0.99 * pix.sum() - 1
+    gpu_img = img.cpu().numpy()
+    err = np.abs(gpu_img - ref["img"]).transpose(1, 0, 2, 3)[:, good]
+    assert err.max() <= 1e-4, err.max()
+    # --- backward with dL/dimg on the sampled tiles only
+    wgt = rng.standard_normal((V, 3, H, W)).astype(np.float32) * good[:, None]
+    grad = torch.zeros_like(w.params)
+    plan.backward(w.params, cams_dev, torch.from_numpy(wgt).cuda(), grad, bg=bg)
+    torch.cuda.synchronize()
+    gs = _take(vbm, b.g_splat, (n_items, 12), np.float32, used)[:, :9]
+    g_ref, c_ref = oraster.render_bwd(V, W, H, tile[0], tile[1], ranges_c, np.asarray(items_c, dtype=np.int32), splat,
+                                      col[:, :3], np.array(bg), wgt.astype(np.float64))
+    for k in range(6):
+        nrm, elt = rel_group_error(gs[:, k], g_ref[:, k])
+        assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
+    for k in range(3):
+        nrm, elt = rel_group_error(gs[:, 6 + k], c_ref[:, k])
+        assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
+    plan.close()
+
+
+def test_build_full_size_c1(cuda_lib):
+    """vbm_build on the 128^3 workload volume against the oracle's build: pyramid to 2e-6
+    relative, kept indices bit-exact (decisions in float32 on the GPU's pyramid),
+    Gaussians to the same bounds as the small build test."""
+    from oracle.dwt import dwt3d, filter_bank, subband_slices, subbands
+    from oracle.mapping import map_coefficients, select_all
+    from oracle.tf import apply_tf_vectorised
+    from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, config, volume_for_config
+    vbm = cuda_lib
+    cfg = config("c1")
+    F = volume_for_config(cfg)
+    J, K_tot = cfg["levels"], cfg["K_tot"]
+    dims = F.shape[::-1]
+    bank = vbm.bank_build(J, 0)
+    coef = torch.zeros(4 * F.size, device="cuda")
+    keep = torch.zeros(F.size, dtype=torch.uint8, device="cuda")
+    params, count = vbm.build(torch.from_numpy(F).cuda(), dims, vbm.make_tf(TF_KNOTS_X, TF_KNOTS_RGBA), bank,
+                              vbm.make_select(K_tot), capacity=F.size, coef=coef, keep=keep)
+    torch.cuda.synchronize()
+    P = params.cpu().numpy()[:, :count]
+    A_gpu = coef.cpu().numpy().reshape(4, *F.shape)
+    keep_gpu = keep.cpu().numpy().reshape(F.shape).astype(bool)
+    # the library holds the knots in float32: the oracle takes the same values
+    x32 = TF_KNOTS_X.astype(np.float32).astype(np.float64)
+    rgba32 = TF_KNOTS_RGBA.astype(np.float32).astype(np.float64)
+    RF = apply_tf_vectorised(F.astype(np.float64), x32, rgba32)
+    fb = filter_bank(0)
+    A_ref = np.stack([dwt3d(RF[..., c], J, fb) for c in range(4)])
+    assert np.abs(A_gpu - A_ref).max() < 2e-6 * np.abs(A_ref).max()
+    masks, Ks, E, N = select_all(A_gpu, J, K_tot, dtype=np.float32)
+    for (j, o), m in zip(subbands(J), masks):
+        assert np.array_equal(keep_gpu[subband_slices(F.shape, j, o)], m), (j, o)
+    assert count == sum(int(m.sum()) for m in masks)
+    ref = map_coefficients(A_gpu.astype(np.float64), masks, J, vbm.bank_to_dicts(bank))
+    G = F.shape[0]
+    assert ref.shape == P.shape
+    assert np.allclose(P[0:3], ref[0:3], atol=1e-5 * G)
+    assert np.allclose(P[3:10], ref[3:10], atol=1e-6)
+    assert np.allclose(P[10], ref[10], atol=2e-5 * np.abs(ref[10]).max())
+    assert np.allclose(P[11:14], ref[11:14], rtol=1e-5, atol=1e-9)
