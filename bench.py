@@ -266,7 +266,8 @@ def main():
     w = make_workload(args.config, device)
     cfg, params, n, recs, cams, targets = w.cfg, w.params, w.n, w.cam_records, w.cams, w.targets
     V, H, W = targets.shape[0], targets.shape[2], targets.shape[3]
-    batch = dict(scene_offset=w.scene_offset, view_scene=w.view_scene, extent=workload_extent(cfg))
+    batch = dict(scene_offset=w.scene_offset, view_scene=w.view_scene, extent=workload_extent(cfg),
+                 recompute=bool(cfg.get("recompute", False)))
     if args.tile:
         tile, ppt, gl, pers = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.gl, args.persistent
         tune_table = []
@@ -298,9 +299,13 @@ def main():
         e.record()
     torch.cuda.synchronize()
     n_eval = torch.zeros((V, H, W), dtype=torch.int32, device=device)
-    ft.plan.set_profile(kev, n_eval)
     bufs = ft.plan.buffers()
-    n_contrib = vbm.device_tensor(bufs.n_contrib, (V, H, W), np.int32)
+    if bufs.n_contrib:
+        ft.plan.set_profile(kev, n_eval)
+        n_contrib = vbm.device_tensor(bufs.n_contrib, (V, H, W), np.int32)
+    else:   # recompute mode keeps no contributor counts: the profiling hook writes them
+        n_contrib = torch.zeros((V, H, W), dtype=torch.int32, device=device)
+        ft.plan.set_profile(kev, n_eval, n_contrib)
     n_pairs_dev = vbm.device_tensor(bufs.n_pairs, (1,), np.int64)
     ft.capture()
     for _ in range(args.warmup):
@@ -429,6 +434,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
                        "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "group_lanes": gl, "persistent": pers,
+                       "compositing_state": "recomputed in the backward" if batch["recompute"] else "stored",
                        "pairs_mean": n_pairs,
                        "form": "batched, CUDA graph, autotuned",
                        "l2": "flushed between steps (256 MiB write)",

@@ -332,8 +332,12 @@ VBM_API int64_t vbm_kernel_launches(void);
  * timing enabled; under stream capture they are recorded as external event
  * nodes).  d_n_eval (int32 [V][H][W]) receives, per pixel of a forward call,
  * the number of list entries evaluated (up to and including the one that
- * ended compositing).  The hooks stay set until changed. */
-VBM_API vbm_status vbm_plan_set_profile(vbm_plan *plan, void *const events[4], int32_t *d_n_eval);
+ * ended compositing); d_n_contrib (int32 [V][H][W]) receives the contributor
+ * count (one past the last blended entry) in plans created with
+ * VBM_PLAN_RECOMPUTE, which keep none of their own.  The hooks stay set until
+ * changed. */
+VBM_API vbm_status vbm_plan_set_profile(vbm_plan *plan, void *const events[4], int32_t *d_n_eval,
+                                        int32_t *d_n_contrib);
 
 #ifdef __cplusplus
 }

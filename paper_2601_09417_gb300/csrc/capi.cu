@@ -83,11 +83,12 @@ int vbm_version(void) { return 101; }
 
 int64_t vbm_kernel_launches(void) { return g_launches.load(); }
 
-vbm_status vbm_plan_set_profile(vbm_plan *p, void *const events[4], int32_t *d_n_eval)
+vbm_status vbm_plan_set_profile(vbm_plan *p, void *const events[4], int32_t *d_n_eval, int32_t *d_n_contrib)
 {
     VBM_ARG(p, "null plan");
     for (int i = 0; i < 4; i++) p->prof_ev[i] = events ? (cudaEvent_t)events[i] : nullptr;
     p->prof_n_eval = d_n_eval;
+    p->prof_n_contrib = d_n_contrib;
     return VBM_OK;
 }
 

@@ -147,32 +147,57 @@ struct WarpSlots {
     uint32_t item[32];
 };
 
-// Load entry [base + lane] of a tile list (if < end), test it against the
-// warp region and store it in the lane's slot.  Returns, for this lane's
-// group, the mask of slots whose alpha >= 1/255 box reaches the group's
-// pixels.  gmax (backward) holds each group's largest contributor count:
-// entries at or beyond it are not listed for that group.
+// One list entry's per-item data as loaded by a lane (it = kNoItem: none).
+constexpr uint32_t kNoItem = 0xffffffffu;
+
+struct Entry {
+    uint32_t it;
+    float4 g;       // u, v, A, B
+    float4 c;       // r, g, b, opacity
+    float4 cu;      // hx, hy, B / C, B / A
+    float cc;       // C
+};
+
+__device__ __forceinline__ uint32_t load_index(const uint32_t *__restrict__ pair_item, int idx, int end)
+{
+    return idx < end ? pair_item[idx] : kNoItem;
+}
+
+__device__ __forceinline__ Entry gather_entry(uint32_t it, const float4 *__restrict__ geo,
+                                              const float4 *__restrict__ col, const float *__restrict__ conic_c,
+                                              const float4 *__restrict__ cull)
+{
+    Entry e;
+    e.it = it;
+    if (it != kNoItem) {
+        e.g = geo[it];
+        e.cc = conic_c[it];
+        e.c = col[it];
+        e.cu = cull[it];
+    } else {
+        e.g = e.c = e.cu = make_float4(0.f, 0.f, 0.f, 0.f);
+        e.cc = 0.f;
+    }
+    return e;
+}
+
+// Test a lane's loaded entry (list position pos1 - 1) against the warp region
+// and store it in the lane's slot.  Returns, for this lane's group, the mask
+// of slots whose alpha >= 1/255 box reaches the group's pixels.  gmax
+// (backward) holds each group's largest contributor count: entries beyond it
+// are not listed for that group.
 template <int PPT, int GL>
-__device__ __forceinline__ uint32_t stage_round(int base, int end, int list_begin,
-                                                const uint32_t *__restrict__ pair_item,
-                                                const float4 *__restrict__ geo, const float4 *__restrict__ col,
-                                                const float *__restrict__ conic_c, const float4 *__restrict__ cull,
-                                                const WarpGeom &wg, WarpSlots &s, const int *gmax)
+__device__ __forceinline__ uint32_t commit_entry(const Entry &e, int pos1, const WarpGeom &wg, WarpSlots &s,
+                                                 const int *gmax)
 {
     using Gp = Groups<GL>;
     const int lane = threadIdx.x & 31;
-    const int idx = base + lane;
     uint32_t gbits = 0;       // bit g: entry reaches group g
-    if (idx < end) {
-        const uint32_t it = pair_item[idx];
-        const float4 g = geo[it];
-        const float cc = conic_c[it];
-        const float4 c = col[it];
-        const float4 cu = cull[it];     // hx, hy, B / C, B / A
-        const float q = rect_min_quadratic(g.x, g.y, g.z, g.w, cc, cu.z, cu.w, wg.x0, wg.x1, wg.y0, wg.y1);
-        const float tau = 2.f * (__logf(255.f * c.w) + kCullMargin);
+    if (e.it != kNoItem) {
+        const float4 g = e.g, cu = e.cu;
+        const float q = rect_min_quadratic(g.x, g.y, g.z, g.w, e.cc, cu.z, cu.w, wg.x0, wg.x1, wg.y0, wg.y1);
+        const float tau = 2.f * (__logf(255.f * e.c.w) + kCullMargin);
         if (0.5f * q <= 0.5f * tau) {
-            const int pos1 = idx - list_begin + 1;
             const float bx0 = g.x - cu.x, bx1 = g.x + cu.x, by0 = g.y - cu.y, by1 = g.y + cu.y;
 #pragma unroll
             for (int gi = 0; gi < Gp::NG; gi++) {
@@ -183,9 +208,9 @@ __device__ __forceinline__ uint32_t stage_round(int base, int end, int list_begi
             }
             if (gbits) {
                 s.geo[lane] = make_float4(g.x, g.y, g.z * kHalfLog2e, g.w * kNegLog2e);
-                s.cp[lane] = make_float2(cc * kHalfLog2e, __int_as_float(pos1));
-                s.col[lane] = c;
-                s.item[lane] = it;
+                s.cp[lane] = make_float2(e.cc * kHalfLog2e, __int_as_float(pos1));
+                s.col[lane] = e.c;
+                s.item[lane] = e.it;
             }
         }
     }
@@ -237,12 +262,22 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
         last[k] = 0;
         evaluated[k] = rg.y - rg.x;
     }
-    for (int base = rg.x; base < rg.y; base += 32) {
+    // rounds of 32 entries, software-pipelined: while round r is composited,
+    // the lane's entry of round r + 1 and its index in round r + 2 are in flight
+    const int lane = threadIdx.x & 31;
+    const int n_rounds = (rg.y - rg.x + 31) / 32;
+    Entry cur = gather_entry(load_index(pair_item, rg.x + lane, rg.y), geo, col, conic_c, cull);
+    uint32_t it_next = load_index(pair_item, rg.x + 32 + lane, rg.y);
+    for (int r = 0; r < n_rounds; r++) {
         bool all_done = true;
 #pragma unroll
         for (int k = 0; k < PPT; k++) all_done &= done[k];
         if (__all_sync(0xffffffffu, all_done)) break;
-        uint32_t m = stage_round<PPT, GL>(base, rg.y, rg.x, pair_item, geo, col, conic_c, cull, wg, s, nullptr);
+        const uint32_t it_after = load_index(pair_item, rg.x + 32 * (r + 2) + lane, rg.y);
+        const Entry nxt = gather_entry(it_next, geo, col, conic_c, cull);
+        uint32_t m = commit_entry<PPT, GL>(cur, 32 * r + lane + 1, wg, s, nullptr);
+        cur = nxt;
+        it_next = it_after;
         while (m) {                                    // no warp collectives inside
             const int j = __ffs(m) - 1;
             m &= m - 1;
@@ -445,10 +480,22 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     int vbase, vcnt;
     group_sum_layout<GL>(lane, vbase, vcnt);
     const uint32_t gmask = GL == 32 ? 0xffffffffu : (((1u << GL) - 1u) << (wg.g * GL));
-    for (int hi = wmax; hi > 0; hi -= 32) {
-        const int lo = max(0, hi - 32);
-        uint32_t m = stage_round<PPT, GL>(rg.x + lo, rg.x + hi, rg.x, pair_item, geo, col, conic_c, cull, wg, s,
-                                          gmax);
+    // rounds from the back: round r holds list positions [max(0, wmax - 32 (r + 1)), wmax - 32 r),
+    // software-pipelined as in the forward
+    const int n_rounds = (wmax + 31) / 32;
+    auto round_lo = [&](int r) { return max(0, wmax - 32 * (r + 1)); };
+    auto round_idx = [&](int r) { return rg.x + round_lo(r) + lane; };
+    auto round_end = [&](int r) { return rg.x + wmax - 32 * r; };
+    Entry cur = gather_entry(n_rounds > 0 ? load_index(pair_item, round_idx(0), round_end(0)) : kNoItem, geo, col,
+                             conic_c, cull);
+    uint32_t it_next = n_rounds > 1 ? load_index(pair_item, round_idx(1), round_end(1)) : kNoItem;
+    for (int r = 0; r < n_rounds; r++) {
+        const uint32_t it_after = r + 2 < n_rounds ? load_index(pair_item, round_idx(r + 2), round_end(r + 2))
+                                                   : kNoItem;
+        const Entry nxt = gather_entry(it_next, geo, col, conic_c, cull);
+        uint32_t m = commit_entry<PPT, GL>(cur, round_lo(r) + lane + 1, wg, s, gmax);
+        cur = nxt;
+        it_next = it_after;
         const int steps = __reduce_max_sync(0xffffffffu, __popc(m));
         for (int step = 0; step < steps; step++) {   // back to front
             int j = 0;
@@ -629,12 +676,13 @@ vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
         k_raster_fwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
             p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col,
             p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
-            bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib, p->prof_n_eval);
+            bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib,
+            p->prof_n_eval);
     } else {
         k_raster_fwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
             nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
             p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
-            bg[2], img, alpha, p->T_final, p->n_contrib, p->prof_n_eval);
+            bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib, p->prof_n_eval);
     }
     VBM_LAUNCH("raster_fwd");
     record_event(p->prof_ev[1], st);

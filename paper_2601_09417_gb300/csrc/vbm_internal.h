@@ -151,6 +151,7 @@ struct vbm_plan {
     // profiling hooks
     cudaEvent_t prof_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t *prof_n_eval = nullptr;
+    int32_t *prof_n_contrib = nullptr;       // contributor counts of recompute-mode forwards (profiling)
 
     // last forward call
     int32_t last_view_begin = -1, last_view_count = 0;

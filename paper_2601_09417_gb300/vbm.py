@@ -108,7 +108,7 @@ def load():
         "vbm_adam": (I32, [V, V, V, V, I64, I64, V, ctypes.POINTER(F32 * 5), F32, F32, F32, V, V]),
         "vbm_kernel_launches": (I64, []),
         "vbm_loss_static": (I32, [V, V, I32, I32, I32, F32, F64, V, I32, V, V]),
-        "vbm_plan_set_profile": (I32, [V, ctypes.POINTER(V * 4), V]),
+        "vbm_plan_set_profile": (I32, [V, ctypes.POINTER(V * 4), V, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -303,15 +303,16 @@ class Plan:
                                         vc, ctypes.byref(bgc), _ptr(dimg), _ptr(dalpha), _ptr(grad),
                                         int(bool(accumulate)), _stream()))
 
-    def set_profile(self, events=None, n_eval=None):
-        """Record cudaEvents around the compositing kernels and/or per-pixel evaluated counts."""
+    def set_profile(self, events=None, n_eval=None, n_contrib=None):
+        """Record cudaEvents around the compositing kernels and/or per-pixel evaluated counts
+        (and, for recompute-mode plans, per-pixel contributor counts)."""
         if events is None:
             arr = None
         else:
             arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
         _check(self._lib.vbm_plan_set_profile(self.handle, None if arr is None else ctypes.byref(arr),
-                                              _ptr(n_eval)))
-        self._profile_keepalive = (events, n_eval)
+                                              _ptr(n_eval), _ptr(n_contrib)))
+        self._profile_keepalive = (events, n_eval, n_contrib)
 
     def buffers(self):
         b = PlanBuffers()

@@ -115,7 +115,8 @@ def test_build_full_size_c1(cuda_lib):
     """vbm_build on the 128^3 workload volume against the oracle's build: pyramid to 2e-6
     relative, kept indices bit-exact (decisions in float32 on the GPU's pyramid),
     Gaussians to the same bounds as the small build test."""
-    from oracle.dwt import dwt3d, filter_bank, subband_slices, subbands
+    from oracle.dwt import dwt3d, subband_slices, subbands
+    from oracle.filters import filter_bank
     from oracle.mapping import map_coefficients, select_all
     from oracle.tf import apply_tf_vectorised
     from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, config, volume_for_config

@@ -35,7 +35,7 @@ CONFIGS = {
                views_per_volume=4, width=256, height=256),
     "c4": dict(key="c4", workload="512^3 supernova-like shells, J=5, ~3M Gaussians, 8 views 1024x1024",
                volume="supernova", G=512, seed=4, levels=5, K_tot=3000000,
-               views=8, width=1024, height=1024, fwd_only=(1920, 1080)),
+               views=8, width=1024, height=1024, fwd_only=(1920, 1080), recompute=True),
 }
 
 
