@@ -236,7 +236,10 @@ VBM_API vbm_status vbm_plan_check(vbm_plan *plan, void *stream, int64_t *pairs_n
  * x/z and y/z clamped to the image +15% for the Jacobian, 2D covariance
  * J W Sigma W^T J^T + 0.3 I, radius ceil(k sqrt(lambda_max)) with
  * k = min(3, sqrt(2 ln(255 o))), no tiles when o < 1/255), tile binning
- * ordered by depth (ties by Gaussian index), front-to-back compositing per
+ * (of the radius rectangle, the tiles where some pixel centre can see
+ * alpha >= 1/255, by the exact minimum of the quadratic form over the tile
+ * with a 1e-3 margin in the log) ordered by depth (ties by Gaussian index),
+ * front-to-back compositing per
  * pixel (alpha = min(0.99, o e^power), skip alpha < 1/255, stop before T
  * falls below 1e-4).  Writes d_img[V][3][H][W] = C + T bg and, if not NULL,
  * d_alpha[V][H][W] = 1 - T, at absolute view indices.  d_params: P[14]
@@ -273,6 +276,8 @@ typedef struct {
     const float *T_final;     /* [V][H][W] (absolute views; NULL in recompute mode) */
     const int32_t *n_contrib; /* [V][H][W]                                         */
     const float *g_splat;     /* [n_items][12] after a backward: du dv dA dB dC dopac dr dg db, 3 unused */
+    const float *cull;        /* [n_items][4]: half-widths of the alpha >= 1/255 box, B / C, B / A  */
+    const float *tau;         /* [n_items]: 2 (ln(255 o) + 1e-3), bound of the binning tile test  */
 } vbm_plan_buffers;
 
 VBM_API vbm_status vbm_plan_get_buffers(vbm_plan *plan, vbm_plan_buffers *out);

@@ -46,7 +46,9 @@ def _load():
         P = ctypes.c_void_p
         I64, I32 = ctypes.c_int64, ctypes.c_int
         lib.orc_project.argtypes = [I64, P, P, I64, P, I32, I32, P]
-        lib.orc_bin_sort.argtypes = [I64, P, P, P, I32, I32, I32, I64, P, P, P]
+        lib.orc_bin_sort.argtypes = [I64, P, P, P, I32, I32, I32, I64, P, P, P, P, P, I32, I32, I32, I32]
+        lib.orc_tile_min_q.argtypes = [ctypes.c_double] * 9
+        lib.orc_tile_min_q.restype = ctypes.c_double
         lib.orc_bin_sort.restype = I64
         lib.orc_render.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_render_bwd.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, I64]
@@ -84,8 +86,38 @@ def project(P, cam, gidx, tile_w, tile_h):
     return out
 
 
-def bin_sort(view_of, rect, depth, TX, TY, n_views, capacity=None):
-    """Sorted (tiles, items) pair lists and per-tile ranges (n_tiles, 2)."""
+def splat_records(splat, dtype=np.float64):
+    """Binning records [n][8] = u v A B C B/C B/A tau from splats (n, 6) = u v A B C opacity,
+    tau = 2 (ln(255 o) + 1e-3), in the given precision (float32: each value rounded as a
+    float32 implementation holds it, B/C and B/A divided in float32)."""
+    sp = np.asarray(splat, dtype=np.float64)
+    if dtype == np.float32:
+        f = sp.astype(np.float32)
+        out = np.zeros((sp.shape[0], 8), dtype=np.float32)
+        out[:, 0:5] = f[:, 0:5]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out[:, 5] = np.where(f[:, 4] != 0, f[:, 3] / f[:, 4], np.float32(0))
+            out[:, 6] = np.where(f[:, 2] != 0, f[:, 3] / f[:, 2], np.float32(0))
+        return out
+    out = np.zeros((sp.shape[0], 8))
+    out[:, 0:5] = sp[:, 0:5]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        out[:, 5] = np.where(sp[:, 4] != 0, sp[:, 3] / sp[:, 4], 0.0)
+        out[:, 6] = np.where(sp[:, 2] != 0, sp[:, 3] / sp[:, 2], 0.0)
+        out[:, 7] = np.where(sp[:, 5] > 0, 2.0 * (np.log(255.0 * np.maximum(sp[:, 5], 1e-300)) + 1e-3), -1.0)
+    return out
+
+
+def tile_min_q(u, v, A, B, C, x0, x1, y0, y1):
+    """Smallest A dx^2 + 2 B dx dy + C dy^2 over the rectangle [x0, x1] x [y0, y1] (FP64)."""
+    return _load().orc_tile_min_q(u, v, A, B, C, x0, x1, y0, y1)
+
+
+def bin_sort(view_of, rect, depth, TX, TY, n_views, capacity=None, splat64=None, splat32=None, tile=(16, 16),
+             image=None):
+    """Sorted (tiles, items) pair lists and per-tile ranges (n_tiles, 2).  With splat64 or
+    splat32 (binning records from splat_records) only the tiles passing the exact tile
+    test are listed; image = (W, H) is then required."""
     lib = _load()
     view_of = np.ascontiguousarray(view_of, dtype=np.int32)
     rect = np.ascontiguousarray(rect, dtype=np.int32).reshape(-1, 4)
@@ -95,8 +127,14 @@ def bin_sort(view_of, rect, depth, TX, TY, n_views, capacity=None):
     tiles = np.zeros(max(total, 1), dtype=np.int64)
     items = np.zeros(max(total, 1), dtype=np.int32)
     ranges = np.zeros((n_views * TY * TX, 2), dtype=np.int32)
+    sp64 = None if splat64 is None else np.ascontiguousarray(splat64, dtype=np.float64)
+    sp32 = None if splat32 is None else np.ascontiguousarray(splat32, dtype=np.float32)
+    W, H = image if image is not None else (0, 0)
+    if (sp64 is not None or sp32 is not None) and image is None:
+        raise ValueError("image size needed for the tile test")
     n = lib.orc_bin_sort(view_of.size, _p(view_of), _p(rect), _p(depth), TX, TY, n_views, cap,
-                         _p(tiles), _p(items), _p(ranges))
+                         _p(tiles), _p(items), _p(ranges), None if sp64 is None else _p(sp64),
+                         None if sp32 is None else _p(sp32), tile[0], tile[1], W, H)
     if n < 0:
         raise OverflowError("pair capacity exceeded")
     return tiles[:n], items[:n], ranges
@@ -187,8 +225,9 @@ def splat_forward(P, cams, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), scene_offse
         sel = view_of == v
         proj[sel] = project(P, cams[v], g_of[sel], tile_w, tile_h)
     rect = proj[:, [PJ["X0"], PJ["Y0"], PJ["X1"], PJ["Y1"]]].astype(np.int32)
-    tiles, items, ranges = bin_sort(view_of, rect, proj[:, PJ["DEPTH"]], TX, TY, V)
     splat = proj[:, [PJ["U"], PJ["V"], PJ["A"], PJ["B"], PJ["C"], PJ["OPAC"]]]
+    tiles, items, ranges = bin_sort(view_of, rect, proj[:, PJ["DEPTH"]], TX, TY, V,
+                                    splat64=splat_records(splat), tile=(tile_w, tile_h), image=(W, H))
     color = P[11:14, g_of].T
     bg = np.asarray(bg, dtype=np.float64)
     out = render(V, W, H, tile_w, tile_h, ranges, items, splat, color, bg)

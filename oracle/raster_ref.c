@@ -26,7 +26,11 @@
  * (fx x/z + cx, fy y/z + cy).  A Gaussian's tile rectangle covers the tiles
  * containing u - r .. u + r (and v - r .. v + r), clamped to the image:
  *   x0 = clamp(floor((u - r) / TW), 0, TX), x1 = clamp(floor((u + r) / TW) + 1, 0, TX)
- * computed exactly as integer divisions of floor(u) -/+ r.
+ * computed exactly as integer divisions of floor(u) -/+ r.  Of that
+ * rectangle, a tile is listed only if some point of the rectangle of its
+ * pixel centres can see alpha >= 1/255 (tile_min_q below, with a margin of
+ * CULL_MARGIN in the log): a pixel of an unlisted tile would skip the splat
+ * anyway, so images and gradients are those of the whole rectangle.
  * Order within a tile: ascending depth (camera z), ties by item index.
  *
  * Layouts (all row-major, double unless stated):
@@ -49,6 +53,7 @@
 #define ALPHA_MIN (1.0 / 255.0)
 #define T_MIN 1e-4
 #define COORD_CLAMP 1e7
+#define CULL_MARGIN 1e-3
 
 enum { CAM_R = 0, CAM_T = 9, CAM_FX = 12, CAM_FY, CAM_CX, CAM_CY, CAM_ZNEAR, CAM_W, CAM_H, CAM_N };
 
@@ -135,6 +140,78 @@ static void project_state(const double *P, int64_t n, int64_t i, const double *c
 }
 
 /* Projection of items: item it = (view of cam, Gaussian gidx[it]). */
+/*
+ * Binning tile test.  alpha = o e^(-q/2) >= 1/255 with q = A dx^2 + 2 B dx dy
+ * + C dy^2 (dx = x - u, dy = y - v) means q <= 2 ln(255 o).  The smallest q
+ * over the rectangle [x0, x1] x [y0, y1] of a tile's pixel centres is 0 if
+ * (u, v) lies inside; else it lies on an edge, where the 1D minimiser along
+ * the edge (dy = -(B / C) dx on a vertical edge, dx = -(B / A) dy on a
+ * horizontal one) is clamped to the edge.  The tile is listed when that
+ * minimum is <= tau = 2 (ln(255 o) + CULL_MARGIN).  Two copies: double for the
+ * FP64 pipeline, and float, operation by operation, for checking a float32
+ * implementation's lists bit for bit from its own float32 splat records
+ * (bc = B / C and ba = B / A rounded to float; compiled with
+ * -ffp-contract=off, so nothing is fused).
+ */
+static double tile_min_q(double u, double v, double A, double B, double C, double bc, double ba, double x0,
+                         double x1, double y0, double y1)
+{
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.0;
+    double best = INFINITY;
+    for (int e = 0; e < 2; e++) {
+        double dx = (e ? x1 : x0) - u;
+        double dy = fmin(fmax(v - bc * dx, y0), y1) - v;
+        double q = (A * dx) * dx + ((2.0 * B) * dx) * dy + (C * dy) * dy;
+        best = fmin(best, q);
+        double ey = (e ? y1 : y0) - v;
+        double ex = fmin(fmax(u - ba * ey, x0), x1) - u;
+        q = (A * ex) * ex + ((2.0 * B) * ex) * ey + (C * ey) * ey;
+        best = fmin(best, q);
+    }
+    return best;
+}
+
+static float tile_min_q_f32(float u, float v, float A, float B, float C, float bc, float ba, float x0, float x1,
+                            float y0, float y1)
+{
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.0f;
+    float best = INFINITY;
+    for (int e = 0; e < 2; e++) {
+        float dx = (e ? x1 : x0) - u;
+        float dy = fminf(fmaxf(v - bc * dx, y0), y1) - v;
+        float q = (A * dx) * dx + ((2.0f * B) * dx) * dy + (C * dy) * dy;
+        best = fminf(best, q);
+        float ey = (e ? y1 : y0) - v;
+        float ex = fminf(fmaxf(u - ba * ey, x0), x1) - u;
+        q = (A * ex) * ex + ((2.0f * B) * ex) * ey + (C * ey) * ey;
+        best = fminf(best, q);
+    }
+    return best;
+}
+
+/* The tile test, exported for the oracle's own tests. */
+double orc_tile_min_q(double u, double v, double A, double B, double C, double x0, double x1, double y0, double y1)
+{
+    return tile_min_q(u, v, A, B, C, B / C, B / A, x0, x1, y0, y1);
+}
+
+/* Is tile (tx, ty) listed for a splat record sp = u v A B C bc ba tau? */
+static int tile_listed(const double *sp, int tx, int ty, int tile_w, int tile_h, int W, int H)
+{
+    double x0 = tx * tile_w + 0.5, x1 = (tx * tile_w + tile_w < W ? tx * tile_w + tile_w : W) - 0.5;
+    double y0 = ty * tile_h + 0.5, y1 = (ty * tile_h + tile_h < H ? ty * tile_h + tile_h : H) - 0.5;
+    return tile_min_q(sp[0], sp[1], sp[2], sp[3], sp[4], sp[5], sp[6], x0, x1, y0, y1) <= sp[7];
+}
+
+static int tile_listed_f32(const float *sp, int tx, int ty, int tile_w, int tile_h, int W, int H)
+{
+    float x0 = (float)(tx * tile_w) + 0.5f;
+    float x1 = (float)(tx * tile_w + tile_w < W ? tx * tile_w + tile_w : W) - 0.5f;
+    float y0 = (float)(ty * tile_h) + 0.5f;
+    float y1 = (float)(ty * tile_h + tile_h < H ? ty * tile_h + tile_h : H) - 0.5f;
+    return tile_min_q_f32(sp[0], sp[1], sp[2], sp[3], sp[4], sp[5], sp[6], x0, x1, y0, y1) <= sp[7];
+}
+
 void orc_project(int64_t n_items, const int64_t *gidx, const double *P, int64_t n,
                  const double *cam, int tile_w, int tile_h, double *out)
 {
@@ -179,7 +256,13 @@ void orc_project(int64_t n_items, const int64_t *gidx, const double *P, int64_t 
         int64_t y0 = clampi(floordiv(fv - ri, tile_h), 0, TY);
         int64_t y1 = clampi(floordiv(fv + ri, tile_h) + 1, 0, TY);
         o[PJ_X0] = x0; o[PJ_X1] = x1; o[PJ_Y0] = y0; o[PJ_Y1] = y1;
-        o[PJ_TOUCHED] = (double)((x1 - x0) * (y1 - y0));
+        double sp[8] = {u, v, o[PJ_A], o[PJ_B], o[PJ_C], o[PJ_B] / o[PJ_C], o[PJ_B] / o[PJ_A],
+                        2.0 * (log(255.0 * st.opac) + CULL_MARGIN)};
+        int64_t listed = 0;
+        for (int64_t ty = y0; ty < y1; ty++)
+            for (int64_t tx = x0; tx < x1; tx++)
+                listed += tile_listed(sp, (int)tx, (int)ty, tile_w, tile_h, (int)cam[CAM_W], (int)cam[CAM_H]);
+        o[PJ_TOUCHED] = (double)listed;
         o[PJ_M_RECT] = fmin(fmin(dist_to_multiple(u - r, tile_w), dist_to_multiple(u + r, tile_w)),
                             fmin(dist_to_multiple(v - r, tile_h), dist_to_multiple(v + r, tile_h)));
     }
@@ -198,19 +281,33 @@ static int cmp_pair(const void *pa, const void *pb)
 }
 
 /*
- * Emit one (global tile, item) pair per tile of each item's rectangle, items
- * in index order and tiles row-major, then sort by (tile, depth, emission
- * order).  global tile = view * TY * TX + ty * TX + tx.  Writes the sorted
- * tiles and items and, per global tile, [start, end) into ranges (2 ints).
- * Returns the number of pairs, or -1 if it exceeds capacity.
+ * Emit one (global tile, item) pair per listed tile of each item's rectangle,
+ * items in index order and tiles row-major, then sort by (tile, depth,
+ * emission order).  global tile = view * TY * TX + ty * TX + tx.  A tile is
+ * listed by the test above on the splat records sp64 (double) or sp32 (float)
+ * [n][8] = u v A B C bc ba tau; with neither, every tile of the rectangle is.
+ * Writes the sorted tiles and items and, per global tile, [start, end) into
+ * ranges (2 ints).  Returns the number of pairs, or -1 if it exceeds capacity.
  */
+static int listed(const double *sp64, const float *sp32, int64_t it, int tx, int ty, int tile_w, int tile_h,
+                  int W, int H)
+{
+    if (sp64) return tile_listed(sp64 + 8 * it, tx, ty, tile_w, tile_h, W, H);
+    if (sp32) return tile_listed_f32(sp32 + 8 * it, tx, ty, tile_w, tile_h, W, H);
+    return 1;
+}
+
 int64_t orc_bin_sort(int64_t n_items, const int32_t *view_of, const int32_t *rect /* [n][4] x0 y0 x1 y1 */,
                      const double *depth, int TX, int TY, int n_views, int64_t capacity,
-                     int64_t *tiles_out, int32_t *items_out, int32_t *ranges)
+                     int64_t *tiles_out, int32_t *items_out, int32_t *ranges, const double *sp64,
+                     const float *sp32, int tile_w, int tile_h, int W, int H)
 {
     int64_t total = 0;
-    for (int64_t it = 0; it < n_items; it++)
-        total += (int64_t)(rect[4 * it + 2] - rect[4 * it]) * (rect[4 * it + 3] - rect[4 * it + 1]);
+    for (int64_t it = 0; it < n_items; it++) {
+        const int32_t *rc = rect + 4 * it;
+        for (int ty = rc[1]; ty < rc[3]; ty++)
+            for (int tx = rc[0]; tx < rc[2]; tx++) total += listed(sp64, sp32, it, tx, ty, tile_w, tile_h, W, H);
+    }
     if (total > capacity) return -1;
     pair_rec *pr = (pair_rec *)malloc((size_t)(total > 0 ? total : 1) * sizeof(pair_rec));
     int64_t k = 0;
@@ -218,6 +315,7 @@ int64_t orc_bin_sort(int64_t n_items, const int32_t *view_of, const int32_t *rec
         const int32_t *rc = rect + 4 * it;
         for (int ty = rc[1]; ty < rc[3]; ty++)
             for (int tx = rc[0]; tx < rc[2]; tx++) {
+                if (!listed(sp64, sp32, it, tx, ty, tile_w, tile_h, W, H)) continue;
                 pr[k].tile = (int64_t)view_of[it] * TY * TX + (int64_t)ty * TX + tx;
                 pr[k].depth = depth[it];
                 pr[k].order = k;

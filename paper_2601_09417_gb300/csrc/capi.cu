@@ -160,6 +160,7 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->col, items);
     ALLOC(p->conic_c, items);
     ALLOC(p->cull, items);
+    ALLOC(p->tau, items);
     ALLOC(p->depth, items);
     ALLOC(p->rect, items);
     ALLOC(p->radius, items);
@@ -298,6 +299,8 @@ vbm_status vbm_plan_get_buffers(vbm_plan *p, vbm_plan_buffers *o)
     o->T_final = p->T_final;
     o->n_contrib = p->n_contrib;
     o->g_splat = p->g_splat;
+    o->cull = (const float *)p->cull;
+    o->tau = p->tau;
     return VBM_OK;
 }
 

@@ -100,8 +100,9 @@ __device__ void project_state(const float *__restrict__ P, int64_t stride, int64
 __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
                                  const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
                                  const int64_t *__restrict__ view_item_offset, int vb, int TX, int TY, int tw, int th,
-                                 float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
-                                 float4 *__restrict__ cull, float *__restrict__ depth, int4 *__restrict__ rect, int32_t *__restrict__ radius,
+                                 int W, int H, float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
+                                 float4 *__restrict__ cull, float *__restrict__ tau_out, float *__restrict__ depth,
+                                 int4 *__restrict__ rect, int32_t *__restrict__ radius,
                                  uint32_t *__restrict__ touched, uint32_t *__restrict__ keyA,
                                  uint32_t *__restrict__ valA)
 {
@@ -110,60 +111,74 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     const int64_t g0 = scene_offset[scene];
     const int64_t ns = scene_offset[scene + 1] - g0;
     const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gl >= ns) return;
-    const int64_t g = g0 + gl;
-    const int64_t item = view_item_offset[v] - view_item_offset[vb] + gl;
-    const vbm_camera cam = cams[v];
-    ProjState st;
-    project_state(P, stride, g, cam, st);
-    float4 cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
-    col[item] = cg;
-    depth[item] = st.t[2];
-    uint32_t ntouch = 0;
-    int4 rc = make_int4(0, 0, 0, 0);
-    int r_int = 0;
-    // A splat whose opacity is below the 1/255 compositing cut-off can never be
-    // blended (alpha = o G <= o), so it gets no tiles.
-    if (!st.culled && st.opac >= kAlphaMin) {
-        float inv_det = 1.0f / st.det;
-        float A = st.c * inv_det, B = -st.b * inv_det, C = st.a * inv_det;
-        float mid = 0.5f * (st.a + st.c);
-        float disc = mid * mid - st.det;
-        float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
-        // Extent of the ellipse where o e^power >= 1/255 (capped at 3 sigma):
-        // pixels beyond it skip this splat anyway, so fewer tiles list it.
-        const float k = fminf(kRadiusSigmas, sqrtf(2.f * logf(255.f * st.opac)));
-        // Bounded so the integer rectangle arithmetic cannot overflow; any
-        // radius above 2^24 already spans every image narrower than 6.7M px.
-        float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
-        float u = cam.fx * (st.t[0] / st.t[2]) + cam.cx;
-        float vv = cam.fy * (st.t[1] / st.t[2]) + cam.cy;
-        geo[item] = make_float4(u, vv, A, B);
-        conic_c[item] = C;
-        // For the compositing kernels' culling: the bounding box of
-        // {q <= tau}, tau = 2 (ln(255 o) + margin), has half-widths
-        // sqrt(tau a) and sqrt(tau c) (the conic's determinant is 1 / det),
-        // slightly widened; and the ratios of the edge minimisers.
-        const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
-        cull[item] = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f,
-                                 -st.b / st.a, -st.b / st.c);
-        r_int = (int)r;
-        int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
-        int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
-        rc.x = min(max(floordiv_i(fu - r_int, tw), 0), TX);
-        rc.z = min(max(floordiv_i(fu + r_int, tw) + 1, 0), TX);
-        rc.y = min(max(floordiv_i(fv - r_int, th), 0), TY);
-        rc.w = min(max(floordiv_i(fv + r_int, th) + 1, 0), TY);
-        ntouch = (uint32_t)((rc.z - rc.x) * (rc.w - rc.y));
-    } else {
-        geo[item] = make_float4(0.f, 0.f, 0.f, 0.f);
-        conic_c[item] = 0.f;
-        cull[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool valid = gl < ns;        // every lane stays for the warp-wide tile count
+    TileTest tt = {};
+    bool has_tiles = false;
+    int64_t item = 0;
+    float depth_z = 0.f;
+    if (valid) {
+        const int64_t g = g0 + gl;
+        item = view_item_offset[v] - view_item_offset[vb] + gl;
+        const vbm_camera cam = cams[v];
+        ProjState st;
+        project_state(P, stride, g, cam, st);
+        float4 cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
+        col[item] = cg;
+        depth[item] = st.t[2];
+        depth_z = st.t[2];
+        int4 rc = make_int4(0, 0, 0, 0);
+        int r_int = 0;
+        // A splat whose opacity is below the 1/255 compositing cut-off can never be
+        // blended (alpha = o G <= o), so it gets no tiles.
+        if (!st.culled && st.opac >= kAlphaMin) {
+            float inv_det = 1.0f / st.det;
+            float A = st.c * inv_det, B = -st.b * inv_det, C = st.a * inv_det;
+            float mid = 0.5f * (st.a + st.c);
+            float disc = mid * mid - st.det;
+            float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
+            // Extent of the ellipse where o e^power >= 1/255 (capped at 3 sigma):
+            // pixels beyond it skip this splat anyway, so fewer tiles list it.
+            const float k = fminf(kRadiusSigmas, sqrtf(2.f * logf(255.f * st.opac)));
+            // Bounded so the integer rectangle arithmetic cannot overflow; any
+            // radius above 2^24 already spans every image narrower than 6.7M px.
+            float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
+            float u = cam.fx * (st.t[0] / st.t[2]) + cam.cx;
+            float vv = cam.fy * (st.t[1] / st.t[2]) + cam.cy;
+            geo[item] = make_float4(u, vv, A, B);
+            conic_c[item] = C;
+            // For the tile test and the compositing kernels' culling: tau =
+            // 2 (ln(255 o) + margin); the bounding box of {q <= tau} has
+            // half-widths sqrt(tau a) and sqrt(tau c) (the conic's determinant is
+            // 1 / det), slightly widened; the edge minimisers' ratios B / C and
+            // B / A are rounded divisions of the stored conic.
+            const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
+            const float bc = __fdiv_rn(B, C), ba = __fdiv_rn(B, A);
+            cull[item] = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc, ba);
+            tau_out[item] = tau;
+            r_int = (int)r;
+            int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
+            int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
+            rc.x = min(max(floordiv_i(fu - r_int, tw), 0), TX);
+            rc.z = min(max(floordiv_i(fu + r_int, tw) + 1, 0), TX);
+            rc.y = min(max(floordiv_i(fv - r_int, th), 0), TY);
+            rc.w = min(max(floordiv_i(fv + r_int, th) + 1, 0), TY);
+            tt = TileTest{u, vv, A, B, C, bc, ba, tau, rc};
+            has_tiles = true;
+        } else {
+            geo[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+            conic_c[item] = 0.f;
+            cull[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+            tau_out[item] = -1.f;
+        }
+        rect[item] = rc;
+        radius[item] = r_int;
     }
-    rect[item] = rc;
-    radius[item] = r_int;
+    // tiles of the rectangle that pass the exact tile test (the image size is
+    // the plan's, as in the pair emission, so both take the same decisions)
+    const uint32_t ntouch = count_listed(has_tiles, tt, tw, th, W, H);
+    if (!valid) return;
     touched[item] = ntouch;
-    keyA[item] = ntouch ? __float_as_uint(st.t[2]) : 0xFFFFFFFFu;
+    keyA[item] = ntouch ? __float_as_uint(depth_z) : 0xFFFFFFFFu;
     valA[item] = (uint32_t)item;
 }
 
@@ -295,9 +310,9 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     k_preprocess_fwd<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
                                               p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
                                               p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
-                                              p->desc.tile_h, p->geo, p->col, p->conic_c, p->cull, p->depth,
-                                              p->rect,
-                                              p->radius, p->touched, p->keyA[0], p->valA[0]);
+                                              p->desc.tile_h, p->desc.width, p->desc.height, p->geo, p->col,
+                                              p->conic_c, p->cull, p->tau, p->depth, p->rect, p->radius,
+                                              p->touched, p->keyA[0], p->valA[0]);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);
     return VBM_OK;

@@ -340,14 +340,17 @@ __global__ void k_set_i64(int64_t *dst, int64_t value)
 }
 
 // Pairs for the items in depth order: item sorted[s] owns [offsets[s],
-// offsets[s+1]) and writes one (tile, item) pair per tile of its rectangle,
-// row-major.  If the total exceeds the capacity nothing is emitted, the pair
-// count is set to 0 and the plan's status records the required size.
+// offsets[s+1]) and writes one (tile, item) pair per listed tile of its
+// rectangle (the tile test preprocess counted with), row-major.  If the
+// total exceeds the capacity nothing is emitted, the pair count is set to 0
+// and the plan's status records the required size.
 __global__ void k_emit_pairs(const uint32_t *__restrict__ sorted, const int64_t *__restrict__ offsets, int64_t n,
-                             const int4 *__restrict__ rect, const int64_t *__restrict__ view_item_offset, int vb,
-                             int vc, int TX, int TY, int64_t capacity, uint32_t *__restrict__ pair_tile,
-                             uint32_t *__restrict__ pair_item, int64_t *__restrict__ n_pairs,
-                             int64_t *__restrict__ status)
+                             const int4 *__restrict__ rect, const float4 *__restrict__ geo,
+                             const float *__restrict__ conic_c, const float4 *__restrict__ cull,
+                             const float *__restrict__ tau, const int64_t *__restrict__ view_item_offset, int vb,
+                             int vc, int TX, int TY, int tw, int th, int W, int H, int64_t capacity,
+                             uint32_t *__restrict__ pair_tile, uint32_t *__restrict__ pair_item,
+                             int64_t *__restrict__ n_pairs, int64_t *__restrict__ status)
 {
     const int64_t total = offsets[n];
     const bool overflow = total > capacity;
@@ -360,24 +363,30 @@ __global__ void k_emit_pairs(const uint32_t *__restrict__ sorted, const int64_t 
     }
     if (overflow) return;
     const int64_t base_item = view_item_offset[vb];
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t beg = offsets[s];
-        if (offsets[s + 1] == beg) continue;
-        const uint32_t item = sorted[s];
-        int lo = 0, hi = vc - 1;   // view of the item: last v with offset <= item
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (view_item_offset[vb + mid] - base_item <= (int64_t)item) lo = mid; else hi = mid - 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: emit_listed needs every lane of the warp
+    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += stride) {
+        const int64_t s = s0 + threadIdx.x;
+        bool has = false;
+        TileTest t = {};
+        uint32_t item = 0, tile0 = 0;
+        int64_t beg = 0;
+        if (s < n) {
+            beg = offsets[s];
+            has = offsets[s + 1] != beg;
         }
-        const int4 rc = rect[item];
-        const uint32_t tile0 = (uint32_t)lo * (uint32_t)(TX * TY);
-        int64_t o = beg;
-        for (int ty = rc.y; ty < rc.w; ty++)
-            for (int tx = rc.x; tx < rc.z; tx++) {
-                pair_tile[o] = tile0 + (uint32_t)(ty * TX + tx);
-                pair_item[o] = item;
-                o++;
+        if (has) {
+            item = sorted[s];
+            int lo = 0, hi = vc - 1;   // view of the item: last v with offset <= item
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (view_item_offset[vb + mid] - base_item <= (int64_t)item) lo = mid; else hi = mid - 1;
             }
+            const float4 g = geo[item], cu = cull[item];
+            t = TileTest{g.x, g.y, g.z, g.w, conic_c[item], cu.z, cu.w, tau[item], rect[item]};
+            tile0 = (uint32_t)lo * (uint32_t)(TX * TY);
+        }
+        emit_listed(has, t, tile0, item, beg, TX, tw, th, W, H, pair_tile, pair_item);
     }
 }
 
@@ -507,9 +516,10 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     gather_scan(p->touched, p->valA[a], n_items, p->offsets, p->scan_scratch, st);
     // 3. emit pairs
     const int grid = num_sms() * 4;
-    k_emit_pairs<<<grid, 256, 0, st>>>(p->valA[a], p->offsets, n_items, p->rect, p->d_view_item_offset, vb, vc,
-                                       p->TX, p->TY, p->desc.pair_capacity, p->pair_tile[0], p->pair_item[0],
-                                       p->d_n_pairs, p->d_status);
+    k_emit_pairs<<<grid, 256, 0, st>>>(p->valA[a], p->offsets, n_items, p->rect, p->geo, p->conic_c, p->cull,
+                                       p->tau, p->d_view_item_offset, vb, vc, p->TX, p->TY, p->desc.tile_w,
+                                       p->desc.tile_h, p->desc.width, p->desc.height, p->desc.pair_capacity,
+                                       p->pair_tile[0], p->pair_item[0], p->d_n_pairs, p->d_status);
     VBM_LAUNCH("emit_pairs");
     note_launches(1);
     // 4. stable sort of the pairs by tile

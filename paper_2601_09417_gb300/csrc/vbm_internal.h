@@ -27,6 +27,147 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kCullMargin = 1e-3f;
 // Floats per item of the splat-gradient records: du dv dA dB dC dopacity dr dg db, padding.
 constexpr int kGradStride = 12;
+
+#ifdef __CUDACC__
+// Binning tile test: smallest q = A dx^2 + 2 B dx dy + C dy^2 (dx = x - u,
+// dy = y - v) over the rectangle [x0, x1] x [y0, y1] of a tile's pixel
+// centres: 0 if (u, v) lies inside, else the least of the four edge minima,
+// each edge's 1D minimiser (dy = -bc dx, dx = -ba dy with bc = B / C,
+// ba = B / A) clamped to the edge.  A tile is listed for a splat when this is
+// <= tau = 2 (ln(255 o) + kCullMargin): alpha = o e^(-q/2) >= 1/255 needs
+// q <= 2 ln(255 o), so a pixel of an unlisted tile would skip the splat.
+// Every operation is an explicitly rounded float32 operation in a fixed order
+// (no contraction), so the decision is reproducible bit for bit.
+__device__ __forceinline__ float tile_min_q(float u, float v, float A, float B, float C, float bc, float ba,
+                                            float x0, float x1, float y0, float y1)
+{
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.f;
+    float best = __int_as_float(0x7f800000);
+    const float B2 = __fmul_rn(2.f, B);
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const float dx = __fsub_rn(e ? x1 : x0, u);
+        const float dy = __fsub_rn(fminf(fmaxf(__fsub_rn(v, __fmul_rn(bc, dx)), y0), y1), v);
+        float q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(B2, dx), dy)),
+                            __fmul_rn(__fmul_rn(C, dy), dy));
+        best = fminf(best, q);
+        const float ey = __fsub_rn(e ? y1 : y0, v);
+        const float ex = __fsub_rn(fminf(fmaxf(__fsub_rn(u, __fmul_rn(ba, ey)), x0), x1), u);
+        q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, ex), ex), __fmul_rn(__fmul_rn(B2, ex), ey)),
+                      __fmul_rn(__fmul_rn(C, ey), ey));
+        best = fminf(best, q);
+    }
+    return best;
+}
+
+// Is tile (tx, ty) of a tw x th grid over a W x H image listed for the splat?
+__device__ __forceinline__ bool tile_listed(float u, float v, float A, float B, float C, float bc, float ba,
+                                            float tau, int tx, int ty, int tw, int th, int W, int H)
+{
+    const float x0 = __fadd_rn((float)(tx * tw), 0.5f), x1 = __fsub_rn((float)min(tx * tw + tw, W), 0.5f);
+    const float y0 = __fadd_rn((float)(ty * th), 0.5f), y1 = __fsub_rn((float)min(ty * th + th, H), 0.5f);
+    return tile_min_q(u, v, A, B, C, bc, ba, x0, x1, y0, y1) <= tau;
+}
+
+// A splat's tile-test record and its radius rectangle (tiles [x, z) x [y, w)).
+struct TileTest {
+    float u, v, A, B, C, bc, ba, tau;
+    int4 rc;
+};
+
+// Rectangles of up to this many tiles are tested by their own lane; larger
+// ones by the whole warp, 32 tiles at a time (a few large splats would
+// otherwise hold their warp for the length of a serial loop).
+constexpr int kSerialTiles = 8;
+
+__device__ __forceinline__ TileTest shfl_test(const TileTest &t, int src)
+{
+    TileTest r;
+    r.u = __shfl_sync(0xffffffffu, t.u, src);
+    r.v = __shfl_sync(0xffffffffu, t.v, src);
+    r.A = __shfl_sync(0xffffffffu, t.A, src);
+    r.B = __shfl_sync(0xffffffffu, t.B, src);
+    r.C = __shfl_sync(0xffffffffu, t.C, src);
+    r.bc = __shfl_sync(0xffffffffu, t.bc, src);
+    r.ba = __shfl_sync(0xffffffffu, t.ba, src);
+    r.tau = __shfl_sync(0xffffffffu, t.tau, src);
+    r.rc.x = __shfl_sync(0xffffffffu, t.rc.x, src);
+    r.rc.y = __shfl_sync(0xffffffffu, t.rc.y, src);
+    r.rc.z = __shfl_sync(0xffffffffu, t.rc.z, src);
+    r.rc.w = __shfl_sync(0xffffffffu, t.rc.w, src);
+    return r;
+}
+
+__device__ __forceinline__ bool listed_k(const TileTest &t, int k, int tw, int th, int W, int H)
+{
+    const int cols = t.rc.z - t.rc.x;
+    return tile_listed(t.u, t.v, t.A, t.B, t.C, t.bc, t.ba, t.tau, t.rc.x + k % cols, t.rc.y + k / cols, tw, th,
+                       W, H);
+}
+
+// Number of listed tiles of this lane's rectangle (0 when !valid).  All 32
+// lanes of the warp must call it.
+__device__ __forceinline__ uint32_t count_listed(bool valid, const TileTest &t, int tw, int th, int W, int H)
+{
+    const int area = valid ? (t.rc.z - t.rc.x) * (t.rc.w - t.rc.y) : 0;
+    uint32_t cnt = 0;
+    if (area > 0 && area <= kSerialTiles)
+        for (int k = 0; k < area; k++) cnt += listed_k(t, k, tw, th, W, H) ? 1u : 0u;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t big = __ballot_sync(0xffffffffu, area > kSerialTiles); big; big &= big - 1) {
+        const int src = __ffs(big) - 1;
+        const TileTest b = shfl_test(t, src);
+        const int a = (b.rc.z - b.rc.x) * (b.rc.w - b.rc.y);
+        uint32_t c = 0;
+        for (int k0 = 0; k0 < a; k0 += 32) {
+            const int k = k0 + lane;
+            c += __popc(__ballot_sync(0xffffffffu, k < a && listed_k(b, k, tw, th, W, H)));
+        }
+        if (lane == src) cnt = c;
+    }
+    return cnt;
+}
+
+// Write (tile0 + tile id, item) for the listed tiles of this lane's
+// rectangle, row-major, from position beg.  All 32 lanes must call it.
+__device__ __forceinline__ void emit_listed(bool valid, const TileTest &t, uint32_t tile0, uint32_t item,
+                                            int64_t beg, int TX, int tw, int th, int W, int H,
+                                            uint32_t *__restrict__ pair_tile, uint32_t *__restrict__ pair_item)
+{
+    const int area = valid ? (t.rc.z - t.rc.x) * (t.rc.w - t.rc.y) : 0;
+    if (area > 0 && area <= kSerialTiles) {
+        const int cols = t.rc.z - t.rc.x;
+        int64_t o = beg;
+        for (int k = 0; k < area; k++)
+            if (listed_k(t, k, tw, th, W, H)) {
+                pair_tile[o] = tile0 + (uint32_t)((t.rc.y + k / cols) * TX + t.rc.x + k % cols);
+                pair_item[o] = item;
+                o++;
+            }
+    }
+    const int lane = threadIdx.x & 31;
+    for (uint32_t big = __ballot_sync(0xffffffffu, area > kSerialTiles); big; big &= big - 1) {
+        const int src = __ffs(big) - 1;
+        const TileTest b = shfl_test(t, src);
+        const uint32_t b_tile0 = __shfl_sync(0xffffffffu, tile0, src);
+        const uint32_t b_item = __shfl_sync(0xffffffffu, item, src);
+        int64_t o = __shfl_sync(0xffffffffu, (long long)beg, src);
+        const int cols = b.rc.z - b.rc.x;
+        const int a = cols * (b.rc.w - b.rc.y);
+        for (int k0 = 0; k0 < a; k0 += 32) {
+            const int k = k0 + lane;
+            const bool ok = k < a && listed_k(b, k, tw, th, W, H);
+            const uint32_t m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int64_t pos = o + __popc(m & ((1u << lane) - 1u));
+                pair_tile[pos] = b_tile0 + (uint32_t)((b.rc.y + k / cols) * TX + b.rc.x + k % cols);
+                pair_item[pos] = b_item;
+            }
+            o += __popc(m);
+        }
+    }
+}
+#endif
 constexpr float kTMin = 1e-4f;
 constexpr float kCoordClamp = 1e7f;
 
@@ -119,6 +260,7 @@ struct vbm_plan {
     float4 *col = nullptr;
     float *conic_c = nullptr;
     float4 *cull = nullptr;                  // [items] half-widths of the alpha >= 1/255 box, B / C, B / A
+    float *tau = nullptr;                    // [items] 2 (ln(255 o) + kCullMargin): bound of the tile test
     float *depth = nullptr;
     int4 *rect = nullptr;
     int32_t *radius = nullptr;

@@ -48,7 +48,17 @@ def plan_state(plan, n_views):
         st["T_final"] = read_device(b.T_final, (plan.n_views, plan.height, plan.width), np.float32)
         st["n_contrib"] = read_device(b.n_contrib, (plan.n_views, plan.height, plan.width), np.int32)
     st["g_splat"] = np.ascontiguousarray(read_device(b.g_splat, (n, 12), np.float32)[:, :9].T)
+    st["cull"] = read_device(b.cull, (n, 4), np.float32)
+    st["tau"] = read_device(b.tau, (n,), np.float32)
     return st
+
+
+def gpu_binning_records(st, items=None):
+    """The GPU's float32 binning records [n][8] = u v A B C B/C B/A tau of a plan state."""
+    sel = slice(None) if items is None else items
+    return np.stack([st["geo"][sel, 0], st["geo"][sel, 1], st["geo"][sel, 2], st["geo"][sel, 3],
+                     st["conic_c"][sel], st["cull"][sel, 2], st["cull"][sel, 3], st["tau"][sel]],
+                    axis=1).astype(np.float32)
 
 
 def gpu_splats_as_oracle(st):

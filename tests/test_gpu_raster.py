@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import gpu_splats_as_oracle, plan_state, rel_group_error, scene, to_device
+from _helpers import gpu_binning_records, gpu_splats_as_oracle, plan_state, rel_group_error, scene, to_device
 from oracle import raster as oraster
 from oracle.raster import PJ
 
@@ -69,14 +69,28 @@ def test_preprocess_matches_oracle(cuda_lib):
     assert flagged < 0.01 * 3 * n
 
 
-def test_binning_bit_exact_given_gpu_depths(cuda_lib):
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile):
+    """Pair lists, order and ranges equal, bit for bit, the oracle's (tile, depth, index)
+    sort of the GPU's rectangles and depths, with the oracle's float32 tile test on the
+    GPU's float32 splat records; the records' B/C and B/A are the float32 quotients of the
+    GPU's own conic, and the test removes pairs (the lists are shorter than the
+    rectangles)."""
     P, cams, cams32 = scene(seed=2, n=2500, V=3, W=100, H=76)
-    plan, *_ = _forward(cuda_lib, P, cams, 100, 76)
+    plan, *_ = _forward(cuda_lib, P, cams, 100, 76, tile=tile)
     st = plan_state(plan, 3)
     n = P.shape[1]
-    TX, TY = _tiles(100, 76, (16, 16))
+    TX, TY = _tiles(100, 76, tile)
     view_of = np.repeat(np.arange(3, dtype=np.int32), n)
-    tiles, items, ranges = oraster.bin_sort(view_of, st["rect"], st["depth"].astype(np.float64), TX, TY, 3)
+    rec = gpu_binning_records(st)
+    live = st["tau"] > 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        assert np.array_equal(rec[live, 5], (rec[live, 3] / rec[live, 4]).astype(np.float32))
+        assert np.array_equal(rec[live, 6], (rec[live, 3] / rec[live, 2]).astype(np.float32))
+    tiles, items, ranges = oraster.bin_sort(view_of, st["rect"], st["depth"].astype(np.float64), TX, TY, 3,
+                                            splat32=rec, tile=tile, image=(100, 76))
+    area = int(((st["rect"][:, 2] - st["rect"][:, 0]) * (st["rect"][:, 3] - st["rect"][:, 1])).sum())
+    assert tiles.size < area
     assert st["n_pairs"] == tiles.size > 0
     assert np.array_equal(st["pair_tile"].astype(np.int64), tiles)
     assert np.array_equal(st["pair_item"].astype(np.int64), items.astype(np.int64))

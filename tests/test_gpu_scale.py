@@ -62,7 +62,14 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
     n0 = int(so[1]) if w.view_scene is None else int(so[int(w.view_scene[0]) + 1] - so[int(w.view_scene[0])])
     rect0 = vbm.device_tensor(b.rect, (n0, 4), np.int32).cpu().numpy()
     depth0 = vbm.device_tensor(b.depth, (n0,), np.float32).cpu().numpy().astype(np.float64)
-    tiles0, items0, _ = oraster.bin_sort(np.zeros(n0, dtype=np.int32), rect0, depth0, TX, TY, 1)
+    geo0 = vbm.device_tensor(b.geo, (n0, 4), np.float32).cpu().numpy()
+    rec0 = np.stack([geo0[:, 0], geo0[:, 1], geo0[:, 2], geo0[:, 3],
+                     vbm.device_tensor(b.conic_c, (n0,), np.float32).cpu().numpy(),
+                     vbm.device_tensor(b.cull, (n0, 4), np.float32).cpu().numpy()[:, 2],
+                     vbm.device_tensor(b.cull, (n0, 4), np.float32).cpu().numpy()[:, 3],
+                     vbm.device_tensor(b.tau, (n0,), np.float32).cpu().numpy()], axis=1)
+    tiles0, items0, _ = oraster.bin_sort(np.zeros(n0, dtype=np.int32), rect0, depth0, TX, TY, 1, splat32=rec0,
+                                         tile=tile, image=(W, H))
     end0 = int(ranges[:TX * TY, 1].max())
     assert end0 == tiles0.size
     assert np.array_equal(vbm.device_tensor(b.pair_tile, (end0,), np.int32).cpu().numpy(), tiles0)

@@ -72,6 +72,58 @@ def test_every_visible_pixel_is_inside_the_tile_rectangle(seed):
     assert n_visible > 50
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_every_visible_pixel_is_in_a_listed_tile(seed):
+    """The binning lists, of each rectangle, only the tiles passing the exact tile test;
+    every pixel where o e^power >= 1/255 (evaluated at every pixel) lies in a listed tile,
+    and elongated splats leave some tiles of their rectangle unlisted."""
+    W, H = 96, 80
+    cams = orbit_cameras((32, 32, 32), 1, W, H)
+    P = gaussians_in_view(300, 32, seed=seed, scale_range=(0.3, 4.0), opacity_logit_range=(-5.0, 3.0))
+    out = raster.splat_forward(P, cams, 16, 16)
+    listed = set(zip(out["tiles"].tolist(), out["items"].tolist()))
+    jj, ii = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    tile_of = (jj // 16).astype(int) * ((W + 15) // 16) + (ii // 16).astype(int)
+    unlisted = 0
+    for g in range(300):
+        r = out["proj"][g]
+        if r[PJ["RADIUS"]] == 0 or r[PJ["OPAC"]] < 1 / 255:
+            continue
+        dx, dy = r[PJ["U"]] - ii, r[PJ["V"]] - jj
+        power = -0.5 * (r[PJ["A"]] * dx * dx + r[PJ["C"]] * dy * dy) - r[PJ["B"]] * dx * dy
+        vis = r[PJ["OPAC"]] * np.exp(power) >= 1 / 255
+        for t in np.unique(tile_of[vis]):
+            assert (int(t), g) in listed, (g, t)
+        area = (r[PJ["X1"]] - r[PJ["X0"]]) * (r[PJ["Y1"]] - r[PJ["Y0"]])
+        assert r[PJ["TOUCHED"]] <= area
+        unlisted += int(area - r[PJ["TOUCHED"]])
+    assert unlisted > 0
+
+
+def test_tile_min_q_is_the_minimum_over_the_rectangle():
+    """tile_min_q against brute-force minimisation of the quadratic form on a dense grid of
+    the rectangle (edges included), for random positive-definite conics and rectangles,
+    with the splat centre inside, beside and diagonal to the rectangle."""
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        L = rng.normal(size=(2, 2)) * rng.uniform(0.05, 2.0)
+        M = L @ L.T + np.eye(2) * rng.uniform(0.01, 0.5)
+        A, B, C = M[0, 0], M[0, 1], M[1, 1]
+        x0, y0 = rng.uniform(-10, 10, 2)
+        x1, y1 = x0 + rng.uniform(0.5, 12), y0 + rng.uniform(0.5, 12)
+        u, v = rng.uniform(-25, 25, 2)
+        xs, ys = np.linspace(x0, x1, 801), np.linspace(y0, y1, 801)
+        X, Y = np.meshgrid(xs, ys)
+        dX, dY = X - u, Y - v
+        brute = (A * dX * dX + 2 * B * dX * dY + C * dY * dY).min()
+        got = raster.tile_min_q(u, v, A, B, C, x0, x1, y0, y1)
+        assert got <= brute + 1e-9 * max(1.0, brute)
+        # the grid spacing bounds how far the grid minimum can lie above the true one
+        h = max(xs[1] - xs[0], ys[1] - ys[0])
+        slope = 2 * (abs(A) + abs(B) + abs(C)) * (max(abs(x1 - u), abs(x0 - u)) + max(abs(y1 - v), abs(y0 - v)))
+        assert brute - got <= slope * h + 1e-9
+
+
 def test_projection_covariance_is_symmetric_pd_and_culls():
     cams = orbit_cameras((32, 32, 32), 3, 80, 60)
     P = gaussians_in_view(200, 32, seed=3)
@@ -128,12 +180,16 @@ def test_binning_is_complete_and_ordered():
     out = raster.splat_forward(P, cams, 16, 16)
     tiles, items, ranges = out["tiles"], out["items"], out["ranges"]
     TX, TY = (70 + 15) // 16, (50 + 15) // 16
-    # every (item, tile-in-rect) pair appears exactly once
+    # every (item, listed tile of its rectangle) pair appears exactly once
     expect = set()
     for it, (x0, y0, x1, y1) in enumerate(out["rect"]):
+        u, v, A, B, C, o = out["splat"][it]
+        tau = 2.0 * (np.log(255.0 * o) + 1e-3) if o > 0 else -1.0
         for ty in range(y0, y1):
             for tx in range(x0, x1):
-                expect.add((out["view_of"][it] * TX * TY + ty * TX + tx, it))
+                r = (tx * 16 + 0.5, min(tx * 16 + 16, 70) - 0.5, ty * 16 + 0.5, min(ty * 16 + 16, 50) - 0.5)
+                if raster.tile_min_q(u, v, A, B, C, *r) <= tau:
+                    expect.add((out["view_of"][it] * TX * TY + ty * TX + tx, it))
     got = list(zip(tiles.tolist(), items.tolist()))
     assert len(got) == len(expect) and set(got) == expect
     depth = out["proj"][:, PJ["DEPTH"]]
