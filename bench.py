@@ -344,13 +344,9 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    from paper_2601_09417_gb300.replicas import job_rate
+    total_ms, value = job_rate(sum(step_ms), args.steps, device)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
     ok, need, bad = ft.check()
 
     # forward alone (projection, binning, sort, compositing) and forward + loss +
