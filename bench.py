@@ -378,7 +378,7 @@ def main():
     host_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets)
     host_l = torch.empty(1, dtype=torch.float64, pin_memory=True)
-    fte.capture()
+    fte.capture_host(host_t, host_l)
     for _ in range(args.warmup):
         fte.step_host(host_t, host_l)
     e2e = time_steps(lambda: fte.step_host(host_t, host_l), args.steps, flush)
@@ -394,7 +394,7 @@ def main():
         cams1 = orbit_cameras((cfg["G"],) * 3, 1, fw, fh)
         cd1 = vbm.cameras_to_device(camera_array(cams1), device)
         plan1 = vbm.Plan([0, n], 1, fw, fh, tile_w=tile[0], tile_h=tile[1], pixels_per_thread=ppt, group_lanes=gl,
-                         flags=vbm.PLAN_PERSISTENT if pers else 0, pair_capacity=min((1 << 31) - 1, 64 * n))
+                         flags=vbm.PLAN_PERSISTENT if pers else 0, pair_capacity=vbm.default_pair_capacity(n))
         img1 = torch.zeros((1, 3, fh, fw), device=device)
 
         def frame():

@@ -93,8 +93,9 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
         ent = cache[key]
         return (tuple(ent["tile"]), ent["ppt"], ent["group_lanes"], ent["persistent"]), ent["table"]
     cams_dev = vbm.cameras_to_device(cam_records, params.device)
-    cap = pair_capacity if pair_capacity is not None else max(1 << 20, 64 * n * n_views)
-    cap = min(cap, (1 << 31) - 1)
+    cap = pair_capacity if pair_capacity is not None else vbm.default_pair_capacity(
+        vbm.batch_items(so, n_views, view_scene))
+    cap = min(cap, vbm.MAX_PAIR_CAPACITY)
     table = []
     for tile, ppt, gl, persistent in (candidates or CANDIDATES):
         ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, gl, persistent, cap)

@@ -38,11 +38,11 @@ class FineTuner:
         self.scene_offset = np.asarray([0, self.n] if scene_offset is None else scene_offset, dtype=np.int64)
         self.view_scene = view_scene
         if pair_capacity is None:
-            pair_capacity = max(1 << 20, 64 * self.n * self.V)
+            pair_capacity = vbm.default_pair_capacity(vbm.batch_items(self.scene_offset, self.V, view_scene))
         self.tile, self.ppt, self.persistent = tuple(tile), int(ppt), bool(persistent)
         self.group_lanes = int(group_lanes)
         self.plan = vbm.Plan(self.scene_offset, self.V, self.W, self.H, view_scene=view_scene, tile_w=tile[0],
-                             tile_h=tile[1], pair_capacity=min(pair_capacity, (1 << 31) - 1), pixels_per_thread=ppt,
+                             tile_h=tile[1], pair_capacity=min(pair_capacity, vbm.MAX_PAIR_CAPACITY), pixels_per_thread=ppt,
                              flags=(vbm.PLAN_PERSISTENT if persistent else 0) |
                              (vbm.PLAN_RECOMPUTE if recompute else 0), group_lanes=group_lanes)
         self.img = torch.zeros((self.V, 3, self.H, self.W), device=self.device)
@@ -101,12 +101,49 @@ class FineTuner:
             self.capture()
         self.graph.replay()
 
-    def step_host(self, host_targets, host_loss):
-        """End-to-end step through host memory: copy this step's targets from pinned host
-        memory, run the captured step, read the loss back to pinned host memory."""
-        self.targets.copy_(host_targets, non_blocking=True)
-        self.step_graph()
+    def _step_from_host(self, host_targets, host_loss, side):
+        """The batched step with this step's targets copied from pinned host memory on a
+        side branch (overlapping projection, binning and the forward compositing, joined
+        before the loss) and the loss copied back to pinned host memory at the end."""
+        main = torch.cuda.current_stream(self.device)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            self.targets.copy_(host_targets, non_blocking=True)
+        self.plan.forward(self.params, self.cams, self.img, bg=self.bg)
+        main.wait_stream(side)
+        vbm.loss(self.img, self.targets, self.V, self.H, self.W, self.lam, self.scale, self.loss, self.dimg,
+                 self.ws)
+        self.plan.backward(self.params, self.cams, self.dimg, self.grad, bg=self.bg)
+        vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
+                 nonfinite=self.nonfinite)
         host_loss.copy_(self.loss, non_blocking=True)
+
+    def capture_host(self, host_targets, host_loss):
+        """Capture the end-to-end step (host targets in, host loss out) as a CUDA graph."""
+        side = torch.cuda.Stream(device=self.device)
+        warm = torch.cuda.Stream(device=self.device)
+        warm.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(warm):
+            snapshot = [t.clone() for t in (self.params, self.m, self.v, self.step_count)]
+            self._step_from_host(host_targets, host_loss, side)
+            for dst, src in zip((self.params, self.m, self.v, self.step_count), snapshot):
+                dst.copy_(src)
+        torch.cuda.current_stream(self.device).wait_stream(warm)
+        torch.cuda.synchronize(self.device)
+        self.host_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.host_graph):
+            self._step_from_host(host_targets, host_loss, side)
+        self._host_bufs = (host_targets, host_loss)
+        return self.host_graph
+
+    def step_host(self, host_targets, host_loss):
+        """End-to-end step through host memory: this step's targets are copied from pinned
+        host memory and its loss read back to pinned host memory, inside one replayed
+        graph (the target copy overlaps the forward)."""
+        if getattr(self, "host_graph", None) is None or self._host_bufs[0] is not host_targets \
+                or self._host_bufs[1] is not host_loss:
+            self.capture_host(host_targets, host_loss)
+        self.host_graph.replay()
 
     def check(self):
         """(ok, pairs_needed, nonfinite): synchronises."""

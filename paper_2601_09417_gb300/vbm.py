@@ -238,6 +238,25 @@ def render_dvr(volume, dims, tf, cams_dev, n_views, width, height, step, out):
                                  height, float(step), _ptr(out), _stream()))
 
 
+MAX_PAIR_CAPACITY = (1 << 31) - 1
+
+
+def default_pair_capacity(n_items):
+    """Pair capacity for a batch of n_items (view, Gaussian) items: 24 pairs per item
+    (about 1.3 are used on the benchmark workloads), at least 2^20, at most the ABI's
+    limit.  A call that needs more renders background and vbm_plan_check reports it."""
+    return int(min(MAX_PAIR_CAPACITY, max(1 << 20, 24 * int(n_items))))
+
+
+def batch_items(scene_offset, n_views, view_scene=None):
+    """(view, Gaussian) items of a batch: the sizes of the scenes its views render."""
+    so = np.asarray(scene_offset, dtype=np.int64)
+    if view_scene is None:
+        return int(n_views * (so[-1] - so[0]))
+    vs = np.asarray(view_scene, dtype=np.int64)
+    return int((so[vs + 1] - so[vs]).sum())
+
+
 class Plan:
     """Owner of a vbm_plan (device buffers of the splatting forward/backward)."""
 

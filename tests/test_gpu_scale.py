@@ -46,7 +46,7 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
     cams_dev = vbm.cameras_to_device(w.cam_records)
     flags = vbm.PLAN_PERSISTENT | (vbm.PLAN_RECOMPUTE if recompute else 0)
     plan = vbm.Plan(so, V, W, H, view_scene=w.view_scene, tile_w=tile[0], tile_h=tile[1], pixels_per_thread=ppt,
-                    group_lanes=gl, flags=flags, pair_capacity=min((1 << 31) - 1, 16 * w.n * V + (1 << 22)))
+                    group_lanes=gl, flags=flags, pair_capacity=vbm.default_pair_capacity(vbm.batch_items(so, V, w.view_scene)))
     bg = (0.05, 0.1, 0.2)
     img = torch.zeros((V, 3, H, W), device="cuda")
     plan.forward(w.params, cams_dev, img, bg=bg)
