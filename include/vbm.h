@@ -139,6 +139,17 @@ typedef struct {
  * Host only; writes *out. */
 VBM_API vbm_status vbm_bank_build(int levels, int wavelet, double tau, double ridge_rel, vbm_bank *out);
 
+#define VBM_BANK_ISOTROPIC 1     /* ablation "w/o transition bank": one shared isotropic covariance */
+#define VBM_BANK_UNIT_WEIGHT 2   /* ablation "w/o energy projection": w = 1 */
+
+/* Turn a bank into an ablation variant of Sec. 5.3, in place (host only).
+ * VBM_BANK_ISOTROPIC: every covariance becomes sigma_iso^2 I, with sigma_iso
+ * the mean over the bank's subbands of det(Sigma)^(1/6) (the paper's "average
+ * spatial extent in the full model"; centres and weights unchanged).
+ * VBM_BANK_UNIT_WEIGHT: every ridge weight w becomes 1.  VBM_ERR_ARG on an
+ * unknown flag or an empty bank. */
+VBM_API vbm_status vbm_bank_ablate(vbm_bank *bank, int32_t flags);
+
 /* Apply the TF to a volume: d_rf[4][n] = TF(d_volume[n]) (Sec. 3),
  * n = nx ny nz, planar RGBA. */
 VBM_API vbm_status vbm_tf_apply(const float *d_volume, int64_t n, const vbm_tf *tf, float *d_rf, void *stream);

@@ -123,3 +123,26 @@ def build_bank(levels, wavelet="bior4.4", tau=0.1, ridge_rel=1e-6):
         entries.append(dict(j=j, o=o, u=u, cov=cov, w=w, log_scale=log_scale, quat=quat,
                             roi_size=int(roi.sum())))
     return entries
+
+
+def ablate(entries, isotropic=False, unit_weight=False):
+    """Bank of the ablation variants of Sec. 5.3 (entries are not modified).
+
+    isotropic (w/o transition bank): every covariance becomes sigma_iso^2 I, with
+    sigma_iso the average spatial extent of the full bank, read as the mean over
+    its 7J+1 subbands of det(Sigma_{j,o})^(1/6) (the geometric-mean standard
+    deviation of each subband's Gaussian); centres and weights are kept.
+    unit_weight (w/o energy projection): w_{j,o} = 1.
+    """
+    out = [dict(e) for e in entries]
+    if isotropic:
+        sigma = float(np.mean([np.linalg.det(e["cov"]) ** (1.0 / 6.0) for e in entries]))
+        for e in out:
+            e["cov"] = sigma * sigma * np.eye(3)
+            e["log_scale"] = np.full(3, np.log(sigma))
+            e["quat"] = np.array([1.0, 0.0, 0.0, 0.0])
+    if unit_weight:
+        for e in out:
+            e["w"] = 1.0
+    return out
+

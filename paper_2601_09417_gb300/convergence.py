@@ -1,6 +1,8 @@
 """Convergence of the image-space fine-tuning from the VBM initialisation versus a
 random initialisation with the same number of Gaussians (the comparison behind the
-paper's fine-tuning experiments, Sec. 5.2 / Table 1, run here on a synthetic workload).
+paper's fine-tuning experiments, Sec. 5.2 / Table 1, run here on a synthetic workload),
+and the ablation variants of Sec. 5.3: the bank's covariances collapsed to one
+isotropic one, unit energy weights, and the Haar wavelet instead of bior4.4.
 
 Both runs use the same targets (vbm_render_dvr), cameras, loss, learning rates and
 launch configuration; only the initial Gaussians differ.  The random initialisation
@@ -13,6 +15,7 @@ the mean squared error over all views and channels, and the mean SSIM from the
 library's own loss kernel (11 x 11 Gaussian window, sigma 1.5).
 
     python -m paper_2601_09417_gb300.convergence --config c1 --steps 2000 --every 250
+    python -m paper_2601_09417_gb300.convergence --variants full,isotropic,unit_weight,haar,random
 """
 
 import argparse
@@ -74,6 +77,8 @@ def main():
     ap.add_argument("--tile", default="8x8")
     ap.add_argument("--ppt", type=int, default=1)
     ap.add_argument("--gl", type=int, default=16)
+    ap.add_argument("--variants", default="full,random",
+                    help="comma list of full, isotropic, unit_weight, haar, random")
     args = ap.parse_args()
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
@@ -83,9 +88,18 @@ def main():
     G = w.cfg["G"]
     tile = tuple(int(x) for x in args.tile.split("x"))
     launch = dict(tile=tile, ppt=args.ppt, group_lanes=args.gl, persistent=True, extent=G)
-    inits = {"vbm": w.params.clone(), "random": torch.from_numpy(random_init(w.n, G)).to(device)}
-    out = {"config": args.config, "gaussians": int(w.n), "views": int(w.targets.shape[0]), "steps": args.steps,
-           "curves": {}}
+    builds = {"full": dict(), "isotropic": dict(ablation=vbm.BANK_ISOTROPIC),
+              "unit_weight": dict(ablation=vbm.BANK_UNIT_WEIGHT), "haar": dict(wavelet=1)}
+    inits = {}
+    for name in args.variants.split(","):
+        if name == "random":
+            inits[name] = torch.from_numpy(random_init(w.n, G)).to(device)
+        elif name == "full":
+            inits[name] = w.params.clone()
+        else:
+            inits[name] = make_workload(args.config, device, **builds[name]).params.clone()
+    out = {"config": args.config, "gaussians": {k: int(v.shape[1]) for k, v in inits.items()},
+           "views": int(w.targets.shape[0]), "steps": args.steps, "curves": {}}
     for name, P in inits.items():
         ft = FineTuner(P.contiguous(), w.cam_records, w.targets, **launch)
         curve = run(ft, args.steps, args.every)

@@ -290,3 +290,37 @@ extern "C" vbm_status vbm_bank_build(int levels, int wavelet, double tau, double
     out->n_sub = n;
     return VBM_OK;
 }
+
+// Ablation variants of the bank (Sec. 5.3).  VBM_BANK_ISOTROPIC ("w/o
+// transition bank"): every covariance becomes sigma_iso^2 I, sigma_iso the
+// mean over the bank's subbands of det(Sigma_{j,o})^(1/6), the average
+// spatial extent of the full bank; centres and weights are kept.
+// VBM_BANK_UNIT_WEIGHT ("w/o energy projection"): every w_{j,o} = 1.
+extern "C" vbm_status vbm_bank_ablate(vbm_bank *bank, int32_t flags)
+{
+    VBM_ARG(bank, "null argument");
+    VBM_ARG(bank->n_sub >= 1 && bank->n_sub <= 64, "bank has no entries");
+    VBM_ARG((flags & ~(VBM_BANK_ISOTROPIC | VBM_BANK_UNIT_WEIGHT)) == 0, "unknown ablation flag");
+    if (flags & VBM_BANK_ISOTROPIC) {
+        double mean = 0.0;
+        for (int i = 0; i < bank->n_sub; i++) {
+            const double *c = bank->sub[i].cov;   // xx yy zz xy xz yz
+            const double det = c[0] * (c[1] * c[2] - c[5] * c[5]) - c[3] * (c[3] * c[2] - c[5] * c[4]) +
+                               c[4] * (c[3] * c[5] - c[1] * c[4]);
+            mean += std::pow(det, 1.0 / 6.0);
+        }
+        const double sigma = mean / bank->n_sub;
+        for (int i = 0; i < bank->n_sub; i++) {
+            vbm_bank_entry &e = bank->sub[i];
+            e.cov[0] = e.cov[1] = e.cov[2] = sigma * sigma;
+            e.cov[3] = e.cov[4] = e.cov[5] = 0.0;
+            for (int d = 0; d < 3; d++) e.log_scale[d] = (float)std::log(sigma);
+            e.quat[0] = 1.f;
+            e.quat[1] = e.quat[2] = e.quat[3] = 0.f;
+        }
+    }
+    if (flags & VBM_BANK_UNIT_WEIGHT)
+        for (int i = 0; i < bank->n_sub; i++) bank->sub[i].w = 1.0;
+    return VBM_OK;
+}
+

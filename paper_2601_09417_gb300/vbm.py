@@ -21,7 +21,7 @@ EXPORTED = ["vbm_last_error", "vbm_version", "vbm_bank_build", "vbm_tf_apply", "
             "vbm_build_workspace_size", "vbm_build", "vbm_render_dvr", "vbm_plan_create",
             "vbm_plan_destroy", "vbm_plan_check", "vbm_raster_fwd", "vbm_raster_bwd",
             "vbm_plan_get_buffers", "vbm_loss_workspace_size", "vbm_loss", "vbm_adam",
-            "vbm_kernel_launches", "vbm_plan_set_profile", "vbm_loss_static"]
+            "vbm_kernel_launches", "vbm_plan_set_profile", "vbm_loss_static", "vbm_bank_ablate"]
 
 
 class VbmError(RuntimeError):
@@ -90,6 +90,7 @@ def load():
         "vbm_last_error": (ctypes.c_char_p, []),
         "vbm_version": (ctypes.c_int, []),
         "vbm_bank_build": (I32, [I32, I32, F64, F64, ctypes.POINTER(Bank)]),
+        "vbm_bank_ablate": (I32, [ctypes.POINTER(Bank), I32]),
         "vbm_tf_apply": (I32, [V, I64, ctypes.POINTER(TF), V, V]),
         "vbm_dwt3d": (I32, [V, I32, ctypes.POINTER(ctypes.c_int * 3), I32, I32, V, V]),
         "vbm_build_workspace_size": (I32, [ctypes.POINTER(ctypes.c_int * 3), I32, ctypes.POINTER(S)]),
@@ -193,6 +194,16 @@ def kernel_launches():
 def bank_build(levels, wavelet=0, tau=0.1, ridge_rel=1e-6):
     bank = Bank()
     _check(load().vbm_bank_build(levels, wavelet, tau, ridge_rel, ctypes.byref(bank)))
+    return bank
+
+
+BANK_ISOTROPIC = 1
+BANK_UNIT_WEIGHT = 2
+
+
+def bank_ablate(bank, flags):
+    """Apply ablation flags (BANK_ISOTROPIC, BANK_UNIT_WEIGHT) to a bank in place."""
+    _check(load().vbm_bank_ablate(ctypes.byref(bank), int(flags)))
     return bank
 
 

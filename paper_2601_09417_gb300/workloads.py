@@ -33,10 +33,12 @@ class Workload:
         return self.targets.shape[0]
 
 
-def _build_one(F, levels, K_tot, device, tf):
+def _build_one(F, levels, K_tot, device, tf, wavelet=0, ablation=0):
     G = F.shape
     dims = (G[2], G[1], G[0])
-    bank = vbm.bank_build(levels, 0)
+    bank = vbm.bank_build(levels, wavelet)
+    if ablation:
+        vbm.bank_ablate(bank, ablation)
     Fd = torch.from_numpy(F).to(device)
     params, n = vbm.build(Fd, dims, tf, bank, vbm.make_select(K_tot), capacity=2 * K_tot + 1024)
     return Fd, dims, params[:, :n].contiguous(), n
@@ -50,7 +52,9 @@ def _render_targets(Fd, dims, tf, cams, width, height, device):
     return recs, rgba[:, :3].contiguous()
 
 
-def make_workload(key, device="cuda"):
+def make_workload(key, device="cuda", wavelet=0, ablation=0):
+    """Build workload `key`; wavelet 1 (Haar) and the bank ablation flags give the
+    ablation variants of Sec. 5.3 (the targets are the same DVR images)."""
     cfg = config(key)
     tf = vbm.make_tf(TF_KNOTS_X, TF_KNOTS_RGBA)
     if "edges" in cfg:                      # uneven batch of independent volumes
@@ -58,7 +62,7 @@ def make_workload(key, device="cuda"):
         for i, G in enumerate(cfg["edges"]):
             F = volume_for_config(cfg, i)
             K = int(cfg["K_tot_frac"] * G ** 3)
-            Fd, dims, P, n = _build_one(F, cfg["levels"], K, device, tf)
+            Fd, dims, P, n = _build_one(F, cfg["levels"], K, device, tf, wavelet, ablation)
             cams = orbit_cameras(dims, cfg["views_per_volume"], cfg["width"], cfg["height"])
             recs, tgt = _render_targets(Fd, dims, tf, cams, cfg["width"], cfg["height"], device)
             Ps.append(P)
@@ -72,7 +76,7 @@ def make_workload(key, device="cuda"):
         return Workload(cfg, params, int(so[-1]), np.concatenate(recs_all), cams_all, torch.cat(tgts),
                         scene_offset=np.asarray(so, dtype=np.int64), view_scene=np.asarray(vs, dtype=np.int32))
     F = volume_for_config(cfg)
-    Fd, dims, params, n = _build_one(F, cfg["levels"], cfg["K_tot"], device, tf)
+    Fd, dims, params, n = _build_one(F, cfg["levels"], cfg["K_tot"], device, tf, wavelet, ablation)
     cams = orbit_cameras(dims, cfg["views"], cfg["width"], cfg["height"])
     recs, targets = _render_targets(Fd, dims, tf, cams, cfg["width"], cfg["height"], device)
     torch.cuda.synchronize()

@@ -69,3 +69,21 @@ def test_host_bank_matches_oracle(lib, levels, wavelet):
         assert np.allclose(a["cov"], b["cov"], atol=1e-10)
         assert abs(a["w"] - b["w"]) < 1e-10 * b["w"]
         assert np.allclose(a["log_scale"], b["log_scale"], atol=1e-6)
+
+
+@pytest.mark.parametrize("wavelet,flags", [(0, 1), (0, 2), (1, 3)])
+def test_host_bank_ablation_matches_oracle(lib, wavelet, flags):
+    """vbm_bank_ablate (host only) against the oracle's ablation of the library's own bank."""
+    from oracle import bank as obank
+    bank = lib.bank_build(3, wavelet)
+    ref = obank.ablate(lib.bank_to_dicts(bank), isotropic=bool(flags & 1), unit_weight=bool(flags & 2))
+    got = lib.bank_to_dicts(lib.bank_ablate(bank, flags))
+    for a, b in zip(got, ref):
+        assert np.allclose(a["u"], b["u"], atol=0) and np.allclose(a["cov"], b["cov"], rtol=1e-12, atol=1e-14)
+        assert abs(a["w"] - b["w"]) <= 1e-12 * abs(b["w"])
+        assert np.allclose(a["log_scale"], b["log_scale"], atol=1e-6)
+        assert np.allclose(a["quat"], b["quat"], atol=1e-7)
+    with pytest.raises(lib.VbmError) as e:
+        lib.bank_ablate(lib.bank_build(2, 0), 8)
+    assert e.value.status == lib.VBM_ERR_ARG
+

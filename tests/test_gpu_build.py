@@ -71,9 +71,11 @@ def test_bank_matches_oracle(cuda_lib, levels, wavelet):
     assert matched >= 7 * min(levels, 3)
 
 
-def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True):
+def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0):
     dims = F.shape[::-1]
     bank = vbm.bank_build(J, wavelet)
+    if ablation:
+        vbm.bank_ablate(bank, ablation)
     sel = vbm.make_select(K_tot, energy_comp=energy_comp)
     n = F.size
     coef = torch.zeros(4 * n, device="cuda")
@@ -84,10 +86,13 @@ def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True):
             keep.cpu().numpy().reshape(F.shape).astype(bool), bank)
 
 
-@pytest.mark.parametrize("G,J,K_tot,seed", [(32, 2, 4096, 0), (64, 3, 20000, 1)])
-def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed):
+@pytest.mark.parametrize("G,J,K_tot,seed,ablation", [(32, 2, 4096, 0, 0), (64, 3, 20000, 1, 0), (32, 2, 4096, 0, 1),
+                                                      (32, 2, 4096, 0, 2)])
+def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation):
+    """vbm_build against the oracle: pyramid, kept indices (bit-exact), Gaussians; also
+    with the ablated banks of Sec. 5.3 (isotropic covariance, unit weight)."""
     F = blob_volume(G, 4 if G == 32 else 12, seed=seed)
-    P, count, A_gpu, keep_gpu, bank = _build(cuda_lib, F, J, K_tot)
+    P, count, A_gpu, keep_gpu, bank = _build(cuda_lib, F, J, K_tot, ablation=ablation)
     # 1. coefficient pyramid vs the FP64 oracle pipeline (TF + DWT)
     x, rgba = _tf32()
     RF = apply_tf_vectorised(F.astype(np.float64), x, rgba)

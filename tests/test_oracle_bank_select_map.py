@@ -36,6 +36,29 @@ def test_haar_bank_closed_form(j):
         assert np.allclose(e["quat"], [1, 0, 0, 0]) and np.allclose(np.exp(2 * e["log_scale"]), var)
 
 
+def test_ablated_banks_haar_closed_form():
+    """Ablation variants (Sec. 5.3) of the Haar bank, whose subband covariances are
+    (4^j - 1)/12 I: isotropic gives every subband sigma_iso^2 I with sigma_iso the mean
+    over the 7J + 1 subbands of sqrt((4^j - 1)/12), keeping centres and weights; unit
+    weight sets every w to 1 and changes nothing else."""
+    J = 2
+    entries = obank.build_bank(J, "haar")
+    sig = [np.sqrt((4.0 ** e["j"] - 1.0) / 12.0) for e in entries]
+    sigma_iso = float(np.mean(sig))
+    assert len(entries) == 7 * J + 1
+    assert sigma_iso == pytest.approx((7 * 0.5 + 8 * np.sqrt(15.0 / 12.0)) / 15.0, abs=1e-12)
+    iso = obank.ablate(entries, isotropic=True)
+    for e, a in zip(entries, iso):
+        assert np.allclose(a["cov"], sigma_iso ** 2 * np.eye(3), atol=1e-12)
+        assert np.allclose(a["log_scale"], np.log(sigma_iso), atol=1e-12)
+        assert np.array_equal(a["quat"], [1.0, 0.0, 0.0, 0.0])
+        assert np.array_equal(a["u"], e["u"]) and a["w"] == e["w"]
+    unit = obank.ablate(entries, unit_weight=True)
+    for e, a in zip(entries, unit):
+        assert a["w"] == 1.0 and np.array_equal(a["cov"], e["cov"]) and np.array_equal(a["u"], e["u"])
+    assert entries[0]["w"] != 1.0          # the input is not modified
+
+
 def test_bior44_bank_symmetry():
     """Symmetric 9/7 filters: low-pass atoms centred on 2^j k, high-pass atoms on
     2^j k + 2^{j-1} per axis; symmetric magnitude makes every covariance diagonal."""
