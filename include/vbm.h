@@ -199,9 +199,10 @@ VBM_API vbm_status vbm_render_dvr(const float *d_volume, const int dims[3], cons
 /* ----------------------------------------------------- fine-tuning step */
 
 /* A raster plan owns every buffer of the splatting forward/backward for a
- * fixed batch: per-(view, Gaussian) projected splats, the depth and tile
- * sorts, tile ranges and per-pixel compositing state (the saved context
- * between forward and backward).  One plan per stream. */
+ * fixed batch: per-(view, Gaussian) projected splats, per-tile pair counts,
+ * the (tile, depth, index)-ordered pair lists, tile ranges and per-pixel
+ * compositing state (the saved context between forward and backward).  One
+ * plan per stream. */
 typedef struct vbm_plan vbm_plan;
 
 #define VBM_PLAN_RECOMPUTE 1   /* keep no per-pixel state; backward recomputes it */

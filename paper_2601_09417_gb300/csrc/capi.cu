@@ -164,17 +164,12 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->depth, items);
     ALLOC(p->rect, items);
     ALLOC(p->radius, items);
-    ALLOC(p->touched, items);
-    ALLOC(p->keyA[0], items);
-    ALLOC(p->keyA[1], items);
-    ALLOC(p->valA[0], items);
-    ALLOC(p->valA[1], items);
-    ALLOC(p->offsets, items + 1);
+    ALLOC(p->listed, items);
     ALLOC(p->g_splat, kGradStride * items);
-    ALLOC(p->pair_tile[0], pairs);
-    ALLOC(p->pair_tile[1], pairs);
-    ALLOC(p->pair_item[0], pairs);
-    ALLOC(p->pair_item[1], pairs);
+    ALLOC(p->pair_key, pairs);
+    ALLOC(p->pair_tile, pairs);
+    ALLOC(p->pair_item, pairs);
+    ALLOC(p->tile_count, tiles);
     ALLOC(p->ranges, tiles);
     ALLOC(p->tile_order, tiles);
     ALLOC(p->tile_queue, kTileQueueWords);
@@ -182,12 +177,10 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
         ALLOC(p->T_final, pixels);
         ALLOC(p->n_contrib, pixels);
     }
-    p->sort_scratch.blocks = num_sms() * 8;
-    ALLOC(p->sort_scratch.hist, radix_sort_hist_words(p->sort_scratch.blocks));
-    if (s == VBM_OK) p->sort_scratch.digit_total = p->sort_scratch.hist + 256 * (size_t)p->sort_scratch.blocks;
-    p->scan_scratch.blocks = num_sms() * 2;
-    ALLOC(p->scan_scratch.block_sums, p->scan_scratch.blocks + 1);
-    ALLOC(p->d_n_items, 1);
+    p->bin_scratch.chunks = bin_chunks(tiles);
+    ALLOC(p->bin_scratch.chunk_sums, p->bin_scratch.chunks);
+    ALLOC(p->bin_scratch.long_tiles, tiles);
+    ALLOC(p->bin_scratch.long_count, 1);
     ALLOC(p->d_n_pairs, 1);
     ALLOC(p->d_status, 2);
 #undef ALLOC
@@ -204,6 +197,8 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     if (e == cudaSuccess) e = cudaMemcpy(p->d_scene_views, views.data(), sizeof(int32_t) * d->n_views, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, 2 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemset(p->d_n_pairs, 0, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemset(p->tile_count, 0, sizeof(uint32_t) * std::max<int64_t>(tiles, 1));
+    if (e == cudaSuccess) e = binning_setup();
     if (e != cudaSuccess) {
         plan_free(p);
         delete p;
@@ -292,8 +287,8 @@ vbm_status vbm_plan_get_buffers(vbm_plan *p, vbm_plan_buffers *o)
     o->depth = p->depth;
     o->rect = (const int32_t *)p->rect;
     o->radius = p->radius;
-    o->pair_tile = p->pair_tile[p->pair_buf];
-    o->pair_item = p->pair_item[p->pair_buf];
+    o->pair_tile = p->pair_tile;
+    o->pair_item = p->pair_item;
     o->ranges = (const int32_t *)p->ranges;
     o->n_pairs = p->d_n_pairs;
     o->T_final = p->T_final;

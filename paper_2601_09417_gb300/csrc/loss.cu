@@ -48,26 +48,38 @@ __device__ __forceinline__ float warp_sum(float v)
 
 // Stage plane values (or value pairs) of rows [oy - 5, oy + kTH + 5) and columns
 // [ox - 5, ox + kTW + 5) into s[kSH][kSWP]; outside the image (and the pad
-// columns) they are zero.  Every load of a thread is issued before the first
-// store, so a block has all its staging loads in flight at once.
-constexpr int kStageIters = (kSH * kSWP + kLossThreads - 1) / kLossThreads;
+// columns) they are zero.  Warp w stages rows w, w + 4, ...: lane l loads
+// columns l and 32 + l of each, so every load instruction reads consecutive
+// pixels of one row and the index arithmetic is per row, not per value.
+// Every load of a thread is issued before the first store.
+constexpr int kLossWarps = kLossThreads / 32;
+constexpr int kStageRows = (kSH + kLossWarps - 1) / kLossWarps;
+static_assert(kSWP > 32 && kSWP <= 64, "a staged row is two loads per lane");
 
 template <typename T, typename F>
 __device__ __forceinline__ void stage_tile(T (*s)[kSWP], int ox, int oy, int H, int W, F load)
 {
-    T val[kStageIters];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gx0 = ox - kHalf + lane, gx1 = gx0 + 32;
+    const bool in0 = gx0 >= 0 && gx0 < W;
+    const bool in1 = lane < kSW - 32 && gx1 >= 0 && gx1 < W;
+    T v0[kStageRows], v1[kStageRows];
 #pragma unroll
-    for (int it = 0; it < kStageIters; it++) {
-        const int i = threadIdx.x + it * kLossThreads;
-        const int r = i / kSWP, c = i - r * kSWP;
-        const int gy = oy + r - kHalf, gx = ox + c - kHalf;
-        const bool in = i < kSH * kSWP && c < kSW && gy >= 0 && gy < H && gx >= 0 && gx < W;
-        val[it] = load(in, (int64_t)gy * W + gx);
+    for (int k = 0; k < kStageRows; k++) {
+        const int r = warp + k * kLossWarps;
+        const int gy = oy + r - kHalf;
+        const bool rin = r < kSH && gy >= 0 && gy < H;
+        const int64_t row = (int64_t)gy * W;
+        v0[k] = load(rin && in0, row + gx0);
+        v1[k] = load(rin && in1, row + gx1);
     }
 #pragma unroll
-    for (int it = 0; it < kStageIters; it++) {
-        const int i = threadIdx.x + it * kLossThreads;
-        if (i < kSH * kSWP) s[i / kSWP][i % kSWP] = val[it];
+    for (int k = 0; k < kStageRows; k++) {
+        const int r = warp + k * kLossWarps;
+        if (r < kSH) {
+            s[r][lane] = v0[k];
+            if (lane < kSWP - 32) s[r][32 + lane] = v1[k];
+        }
     }
 }
 

@@ -4,7 +4,8 @@
 // layout P[14][stride], so the 14 loads of a warp are each one coalesced
 // 128-byte transaction.  The forward writes the per-item splat records the
 // rasteriser stages (geo = u, v, A, B; col = r, g, b, opacity; conic C), the
-// tile rectangle, the depth key of the depth sort and the tile count.  The
+// depth, the tile rectangle and the number of listed tiles, and adds the
+// item to the pair count of each listed tile.  The
 // backward recomputes the forward state from the parameters (cheaper than
 // storing it) and sums the per-view contributions of a Gaussian in
 // registers, so the parameter gradient is written once, without atomics.
@@ -103,8 +104,7 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                                  int W, int H, float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
                                  float4 *__restrict__ cull, float *__restrict__ tau_out, float *__restrict__ depth,
                                  int4 *__restrict__ rect, int32_t *__restrict__ radius,
-                                 uint32_t *__restrict__ touched, uint32_t *__restrict__ keyA,
-                                 uint32_t *__restrict__ valA)
+                                 uint32_t *__restrict__ listed, uint32_t *__restrict__ tile_count)
 {
     const int v = vb + blockIdx.y;
     const int scene = view_scene ? view_scene[v] : 0;
@@ -115,7 +115,6 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     TileTest tt = {};
     bool has_tiles = false;
     int64_t item = 0;
-    float depth_z = 0.f;
     if (valid) {
         const int64_t g = g0 + gl;
         item = view_item_offset[v] - view_item_offset[vb] + gl;
@@ -125,7 +124,6 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
         float4 cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
         col[item] = cg;
         depth[item] = st.t[2];
-        depth_z = st.t[2];
         int4 rc = make_int4(0, 0, 0, 0);
         int r_int = 0;
         // A splat whose opacity is below the 1/255 compositing cut-off can never be
@@ -174,12 +172,12 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
         radius[item] = r_int;
     }
     // tiles of the rectangle that pass the exact tile test (the image size is
-    // the plan's, as in the pair emission, so both take the same decisions)
-    const uint32_t ntouch = count_listed(has_tiles, tt, tw, th, W, H);
+    // the plan's, as in the pair placement, so both take the same decisions),
+    // counted per tile and recorded per item for the placement
+    const uint32_t word = listed_tiles(has_tiles, tt, tw, th, W, H, tile_count,
+                                       (uint32_t)(v - vb) * (uint32_t)(TX * TY), TX);
     if (!valid) return;
-    touched[item] = ntouch;
-    keyA[item] = ntouch ? __float_as_uint(depth_z) : 0xFFFFFFFFu;
-    valA[item] = (uint32_t)item;
+    listed[item] = word;
 }
 
 // Chain rule from the per-item splat gradient (du, dv, dA, dB, dC, dopacity,
@@ -312,7 +310,7 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
                                               p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
                                               p->desc.tile_h, p->desc.width, p->desc.height, p->geo, p->col,
                                               p->conic_c, p->cull, p->tau, p->depth, p->rect, p->radius,
-                                              p->touched, p->keyA[0], p->valA[0]);
+                                              p->listed, p->tile_count);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);
     return VBM_OK;

@@ -674,13 +674,13 @@ vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
         const int grid = persistent_grid(k_raster_fwd<PPT, GL, true>, n_items_w);
         k_raster_fwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
-            p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col,
+            p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col,
             p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
             bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib,
             p->prof_n_eval);
     } else {
         k_raster_fwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
-            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col, p->conic_c,
             p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
             bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib, p->prof_n_eval);
     }
@@ -701,12 +701,12 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
         const int grid = persistent_grid(k_raster_bwd<PPT, GL, true>, n_items_w);
         k_raster_bwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
-            p->tile_order, p->tile_queue + 1, n_items_w, nr, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col,
+            p->tile_order, p->tile_queue + 1, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col,
             p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
             bg[0], bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat);
     } else {
         k_raster_bwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
-            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item[p->pair_buf], p->geo, p->col, p->conic_c,
+            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col, p->conic_c,
             p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
             bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat);
     }

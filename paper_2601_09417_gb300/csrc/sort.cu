@@ -1,21 +1,28 @@
-// Tile binning with a depth order: scans, a stable LSD radix sort, pair
-// emission and tile ranges.
+// Tile binning with a depth order: per-tile pair counts, ranges, bucket
+// placement and a sort of each tile's list.
 //
 // The order the rasteriser needs is "by tile, then by depth, ties by item
-// index".  Instead of sorting every (tile, Gaussian) pair on a 64-bit
-// (tile | depth) key, the items are first sorted by their 32-bit depth key
-// (N x V elements), the pairs are then emitted in that depth order, and a
-// stable sort on the tile id alone (ceil(log2 #tiles) bits, usually two 8-bit
-// passes) groups them by tile.  Stability carries the depth order (and the
-// item-index tie break of the first stable sort) into every tile's list, so
-// the result equals the 64-bit sort while the large pair array is sorted on
-// ~16 key bits instead of ~45 and each pair is 8 bytes instead of 12.
+// index".  The projection counts, per tile, the items whose exact tile test
+// lists it; an exclusive scan of those counts gives every tile its range of
+// the pair array.  Each item then claims one slot per listed tile with an
+// atomic decrement of the tile's counter (which leaves every counter at zero
+// for the next call) and stores its 64-bit key (depth bits << 32 | item)
+// there.  The slots of a tile are filled in arbitrary order, so each tile's
+// list is sorted by that key: depth > 0 for every listed item, so the float
+// bits order like the depths, and the low word breaks ties by item index.
+// The result is unique, so it equals the oracle's (tile, depth, index) sort
+// bit for bit however the atomics interleave.
 //
-// Every kernel here runs on a fixed grid (a multiple of the SM count) and
-// reads element counts from device memory, so a whole step can be captured
-// in a CUDA graph without knowing the pair count on the host.  No kernel
-// waits on another block: the radix sort is reduce-then-scan (upsweep
-// histograms, one scan block, downsweep scatter).
+// Lists of up to 256 keys are sorted by one warp in registers (bitonic
+// network, keys i = 32 r + lane); longer lists go to a queue that blocks sort
+// with a bitonic network in shared memory (4096 keys), or, beyond that, with
+// the network's long-distance steps in global memory.
+//
+// Compared with sorting all pairs on a (tile | depth) key, nothing is sorted
+// globally: the pair array is written once by the placement and once by the
+// per-tile sort.  Every kernel runs on a grid fixed by the plan's sizes and
+// reads counts from device memory, so a whole step can be captured in a CUDA
+// graph without knowing the pair count on the host.
 #include <algorithm>
 
 #include "vbm_internal.h"
@@ -23,381 +30,411 @@
 namespace vbm {
 namespace {
 
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 8;                      // elements per thread per tile
-constexpr int kSortTile = kSortThreads * kSortItems;
-
-__device__ __forceinline__ int64_t chunk_of(int64_t n, int blocks)
-{
-    int64_t c = (n + blocks - 1) / blocks;
-    return (c + kSortTile - 1) / kSortTile * kSortTile;
-}
-
-// Per-block digit histogram of keys in the block's chunk: hist[d * blocks + b],
-// and the per-digit totals over all blocks (digit_total, zeroed before).
-// Equal digits within a warp are counted with one shared-memory atomic
-// (__match_any_sync groups them), so keys that share their high bits do not
-// serialise on one counter.
-__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
-                                                                const int64_t *__restrict__ d_n, int shift,
-                                                                uint32_t *__restrict__ hist,
-                                                                uint32_t *__restrict__ digit_total)
-{
-    __shared__ uint32_t h[kRadix];
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const int64_t n = *d_n;
-    const int64_t chunk = chunk_of(n, gridDim.x);
-    const int64_t beg = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, beg + chunk);
-    const int lane = threadIdx.x & 31;
-    for (int64_t b = beg; b < end; b += kSortTile) {       // uniform trip count across the block
-        uint32_t d[kSortItems];
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {           // all loads of the tile first
-            const int64_t i = b + it * kSortThreads + threadIdx.x;
-            d[it] = i < end ? (keys[i] >> shift) & (kRadix - 1) : (uint32_t)(kRadix + lane);
-        }
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
-            if (d[it] < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d[it]], (uint32_t)__popc(peers));
-        }
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-        hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
-        if (h[d]) atomicAdd(&digit_total[d], h[d]);
-    }
-}
-
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sums, uint32_t *total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t incl = x;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < nw ? warp_sums[lane] : 0u;
-        uint32_t wi = w;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += y;
-        }
-        if (lane < nw) warp_sums[lane] = wi - w;
-        if (lane == 31 && total) *total = wi;
-    }
-    __syncthreads();
-    const uint32_t r = warp_sums[warp] + incl - x;
-    __syncthreads();
-    return r;
-}
-
-// Digit-major exclusive offsets, one block per digit d: base(d) = sum of the
-// totals of the smaller digits, then a scan of digit d's per-block counts.
-__global__ void __launch_bounds__(kSortThreads) k_radix_offsets(uint32_t *__restrict__ hist,
-                                                                const uint32_t *__restrict__ digit_total, int blocks)
-{
-    __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t s_base;
-    const int d = blockIdx.x;
-    uint32_t lower = 0;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) lower += digit_total[i];
-    const uint32_t dummy = block_exclusive_scan(lower, warp_sums, &s_base);
-    (void)dummy;
-    __syncthreads();
-    uint32_t carry = s_base;
-    __syncthreads();
-    uint32_t *h = hist + (int64_t)d * blocks;
-    for (int b0 = 0; b0 < blocks; b0 += blockDim.x) {
-        const int b = b0 + threadIdx.x;
-        const uint32_t x = b < blocks ? h[b] : 0u;
-        __shared__ uint32_t chunk_total;
-        const uint32_t ex = block_exclusive_scan(x, warp_sums, &chunk_total);
-        if (b < blocks) h[b] = carry + ex;
-        __syncthreads();
-        carry += chunk_total;
-        __syncthreads();
-    }
-}
-
-// Stable scatter of the block's chunk, one tile of kSortTile elements at a
-// time.  Ranking: within a tile, warp w owns elements [w * 32 * kSortItems,
-// (w + 1) * 32 * kSortItems) and walks them 32 at a time; the rank of an
-// element among equal digits of the warp is (earlier iterations of this warp)
-// + (earlier lanes of this iteration, from __match_any_sync).  The tile is
-// then exchanged through shared memory into digit order (digit start in the
-// tile + elements of that digit in earlier warps + rank), and written out
-// with consecutive threads on consecutive elements, so each digit's run of
-// the tile goes to global memory as contiguous stores.
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
-                                                                  const uint32_t *__restrict__ vals_in,
-                                                                  uint32_t *__restrict__ keys_out,
-                                                                  uint32_t *__restrict__ vals_out,
-                                                                  const int64_t *__restrict__ d_n, int shift,
-                                                                  const uint32_t *__restrict__ hist)
-{
-    static_assert(kSortThreads == kRadix, "one thread per digit in the per-tile digit scans");
-    __shared__ uint32_t run[kRadix];        // global position of the next element of each digit
-    __shared__ uint32_t tstart[kRadix];     // first position of each digit in the exchanged tile
-    __shared__ uint32_t wcnt[kSortWarps][kRadix];
-    __shared__ uint32_t s_key[kSortTile];
-    __shared__ uint32_t s_val[kSortTile];
-    __shared__ uint32_t warp_sums[32];
-    const int64_t n = *d_n;
-    const int64_t chunk = chunk_of(n, gridDim.x);
-    const int64_t beg = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, beg + chunk);
-    if (beg >= end) return;                 // uniform across the block
-    const int t = threadIdx.x;
-    run[t] = hist[(int64_t)t * gridDim.x + blockIdx.x];
-    const int warp = t >> 5, lane = t & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int64_t tbase = beg; tbase < end; tbase += kSortTile) {
-#pragma unroll
-        for (int w = 0; w < kSortWarps; w++) wcnt[w][t] = 0;
-        __syncthreads();
-        uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
-        const int64_t wbase = tbase + (int64_t)warp * 32 * kSortItems;
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int64_t i = wbase + it * 32 + lane;
-            const bool valid = i < end;
-            k[it] = valid ? keys_in[i] : 0u;
-            v[it] = valid ? vals_in[i] : 0u;
-        }
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int64_t i = wbase + it * 32 + lane;
-            const bool valid = i < end;
-            const uint32_t d = valid ? (k[it] >> shift) & (kRadix - 1) : (uint32_t)(kRadix + lane);
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t prior = valid ? wcnt[warp][d] : 0u;
-            rank[it] = prior + __popc(peers & lt_mask);
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = prior + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // thread t = digit t: exclusive offsets over the warps, then over the digits
-        uint32_t tot = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; w++) {
-            const uint32_t c = wcnt[w][t];
-            wcnt[w][t] = tot;
-            tot += c;
-        }
-        tstart[t] = block_exclusive_scan(tot, warp_sums, nullptr);
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int64_t i = wbase + it * 32 + lane;
-            if (i < end) {
-                const uint32_t d = (k[it] >> shift) & (kRadix - 1);
-                const uint32_t lpos = tstart[d] + wcnt[warp][d] + rank[it];
-                s_key[lpos] = k[it];
-                s_val[lpos] = v[it];
-            }
-        }
-        __syncthreads();
-        const int cnt = (int)min((int64_t)kSortTile, end - tbase);
-        for (int i = t; i < cnt; i += kSortThreads) {
-            const uint32_t key = s_key[i];
-            const uint32_t d = (key >> shift) & (kRadix - 1);
-            const uint32_t pos = run[d] + (uint32_t)i - tstart[d];
-            keys_out[pos] = key;
-            vals_out[pos] = s_val[i];
-        }
-        __syncthreads();
-        run[t] += tot;
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------ gather scan
-
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 4;
+constexpr int kScanItems = 16;                        // tiles per thread of a scan chunk
+constexpr int kTilesPerChunk = kScanThreads * kScanItems;
+constexpr uint64_t kPadKey = ~0ull;
 
-__device__ __forceinline__ int64_t scan_chunk(int64_t n, int blocks)
-{
-    const int64_t t = kScanThreads * kScanItems;
-    int64_t c = (n + blocks - 1) / blocks;
-    return (c + t - 1) / t * t;
-}
+// ------------------------------------------------------------ tile ranges
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ counts,
-                                                              const uint32_t *__restrict__ idx, int64_t n,
-                                                              int64_t *__restrict__ block_sums)
-{
-    __shared__ int64_t red[kScanThreads];
-    const int64_t chunk = scan_chunk(n, gridDim.x);
-    const int64_t beg = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, beg + chunk);
-    int64_t s = 0;
-    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) s += counts[idx[i]];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < (unsigned)off) red[threadIdx.x] += red[threadIdx.x + off];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
-}
-
-// Exclusive scan of the per-block sums (blocks <= 1024) in one block; total at [blocks].
-__global__ void __launch_bounds__(1024) k_scan_top(int64_t *__restrict__ block_sums, int blocks)
-{
-    __shared__ int64_t warp_sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t x = (int)threadIdx.x < blocks ? block_sums[threadIdx.x] : 0;
-    int64_t incl = x;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int64_t w = warp_sums[lane];
-        int64_t wi = w;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += y;
-        }
-        warp_sums[lane] = wi - w;
-        if (lane == 31) block_sums[blocks] = wi;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < blocks) block_sums[threadIdx.x] = warp_sums[warp] + incl - x;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ counts,
-                                                            const uint32_t *__restrict__ idx, int64_t n,
-                                                            const int64_t *__restrict__ block_sums,
-                                                            int64_t *__restrict__ out)
+// Sum of the tile counts of each chunk of kTilesPerChunk tiles.
+__global__ void __launch_bounds__(kScanThreads) k_tile_chunk_sums(const uint32_t *__restrict__ tile_count,
+                                                                  int64_t n_tiles, int64_t *__restrict__ chunk_sums)
 {
     __shared__ int64_t warp_sums[kScanThreads / 32];
-    __shared__ int64_t carry;
-    const int64_t chunk = scan_chunk(n, gridDim.x);
-    const int64_t beg = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, beg + chunk);
-    if (threadIdx.x == 0) carry = block_sums[blockIdx.x];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t tb = beg; tb < end; tb += kScanThreads * kScanItems) {
-        int64_t v[kScanItems];
-        int64_t local = 0;
+    const int64_t beg = (int64_t)blockIdx.x * kTilesPerChunk;
+    int64_t s = 0;
 #pragma unroll
-        for (int it = 0; it < kScanItems; it++) {
-            const int64_t i = tb + (int64_t)threadIdx.x * kScanItems + it;
-            v[it] = i < end ? (int64_t)counts[idx[i]] : 0;
-            local += v[it];
-        }
-        int64_t incl = local;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
-        }
-        if (lane == 31) warp_sums[warp] = incl;
-        __syncthreads();
-        int64_t wpre = 0, tot = 0;
-        for (int w = 0; w < kScanThreads / 32; w++) {
-            if (w < warp) wpre += warp_sums[w];
-            tot += warp_sums[w];
-        }
-        int64_t run = carry + wpre + incl - local;
-#pragma unroll
-        for (int it = 0; it < kScanItems; it++) {
-            const int64_t i = tb + (int64_t)threadIdx.x * kScanItems + it;
-            if (i < end) out[i] = run;
-            run += v[it];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
+    for (int it = 0; it < kScanItems; it++) {
+        const int64_t t = beg + it * kScanThreads + threadIdx.x;
+        if (t < n_tiles) s += tile_count[t];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = block_sums[gridDim.x];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t tot = 0;
+        for (int w = 0; w < kScanThreads / 32; w++) tot += warp_sums[w];
+        chunk_sums[blockIdx.x] = tot;
+    }
 }
 
-// ------------------------------------------------------------- emission
-
-__global__ void k_set_i64(int64_t *dst, int64_t value)
+// Exclusive scan of the tile counts into ranges [begin, end) ((0, 0) for an
+// empty tile).  Each block adds up the sums of the chunks before its own and
+// of all chunks.  If the total exceeds the capacity every range is empty, the
+// pair count is 0, the counters are cleared and the status records the size
+// needed.  Also resets the long-list queue of the sort.
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict__ tile_count, int64_t n_tiles,
+                                                            const int64_t *__restrict__ chunk_sums, int chunks,
+                                                            int64_t capacity, int2 *__restrict__ ranges,
+                                                            int64_t *__restrict__ n_pairs,
+                                                            int64_t *__restrict__ status,
+                                                            uint32_t *__restrict__ long_count)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = value;
-}
-
-// Pairs for the items in depth order: item sorted[s] owns [offsets[s],
-// offsets[s+1]) and writes one (tile, item) pair per listed tile of its
-// rectangle (the tile test preprocess counted with), row-major.  If the
-// total exceeds the capacity nothing is emitted, the pair count is set to 0
-// and the plan's status records the required size.
-__global__ void k_emit_pairs(const uint32_t *__restrict__ sorted, const int64_t *__restrict__ offsets, int64_t n,
-                             const int4 *__restrict__ rect, const float4 *__restrict__ geo,
-                             const float *__restrict__ conic_c, const float4 *__restrict__ cull,
-                             const float *__restrict__ tau, const int64_t *__restrict__ view_item_offset, int vb,
-                             int vc, int TX, int TY, int tw, int th, int W, int H, int64_t capacity,
-                             uint32_t *__restrict__ pair_tile, uint32_t *__restrict__ pair_item,
-                             int64_t *__restrict__ n_pairs, int64_t *__restrict__ status)
-{
-    const int64_t total = offsets[n];
+    __shared__ int64_t red[2][kScanThreads / 32];
+    __shared__ int64_t warp_off[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t before = 0, total = 0;
+    for (int c = threadIdx.x; c < chunks; c += kScanThreads) {
+        const int64_t v = chunk_sums[c];
+        total += v;
+        if (c < (int)blockIdx.x) before += v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, off);
+        total += __shfl_xor_sync(0xffffffffu, total, off);
+    }
+    if (lane == 0) {
+        red[0][warp] = before;
+        red[1][warp] = total;
+    }
+    __syncthreads();
+    before = total = 0;
+    for (int w = 0; w < kScanThreads / 32; w++) {
+        before += red[0][w];
+        total += red[1][w];
+    }
     const bool overflow = total > capacity;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *n_pairs = overflow ? 0 : total;
+        *long_count = 0;
         if (overflow) {
             atomicOr((unsigned long long *)&status[0], (unsigned long long)kStatusCapacity);
             atomicMax((unsigned long long *)&status[1], (unsigned long long)total);
         }
     }
-    if (overflow) return;
-    const int64_t base_item = view_item_offset[vb];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform trip count: emit_listed needs every lane of the warp
-    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += stride) {
-        const int64_t s = s0 + threadIdx.x;
-        bool has = false;
-        TileTest t = {};
-        uint32_t item = 0, tile0 = 0;
-        int64_t beg = 0;
-        if (s < n) {
-            beg = offsets[s];
-            has = offsets[s + 1] != beg;
+    // thread t scans kScanItems consecutive tiles of the chunk
+    const int64_t t0 = (int64_t)blockIdx.x * kTilesPerChunk + (int64_t)threadIdx.x * kScanItems;
+    uint32_t c[kScanItems];
+    int64_t local = 0;
+#pragma unroll
+    for (int it = 0; it < kScanItems; it++) {
+        c[it] = t0 + it < n_tiles ? tile_count[t0 + it] : 0u;
+        local += c[it];
+    }
+    int64_t incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_off[warp] = incl;
+    __syncthreads();
+    int64_t run = before + incl - local;
+    for (int w = 0; w < warp; w++) run += warp_off[w];
+#pragma unroll
+    for (int it = 0; it < kScanItems; it++) {
+        const int64_t t = t0 + it;
+        if (t >= n_tiles) break;
+        if (overflow) {
+            ranges[t] = make_int2(0, 0);
+            tile_count[t] = 0u;
+        } else {
+            ranges[t] = c[it] ? make_int2((int)run, (int)(run + c[it])) : make_int2(0, 0);
         }
-        if (has) {
-            item = sorted[s];
-            int lo = 0, hi = vc - 1;   // view of the item: last v with offset <= item
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (view_item_offset[vb + mid] - base_item <= (int64_t)item) lo = mid; else hi = mid - 1;
-            }
-            const float4 g = geo[item], cu = cull[item];
-            t = TileTest{g.x, g.y, g.z, g.w, conic_c[item], cu.z, cu.w, tau[item], rect[item]};
-            tile0 = (uint32_t)lo * (uint32_t)(TX * TY);
-        }
-        emit_listed(has, t, tile0, item, beg, TX, tw, th, W, H, pair_tile, pair_item);
+        run += c[it];
     }
 }
 
-__global__ void k_tile_ranges(const uint32_t *__restrict__ tile, const int64_t *__restrict__ n_pairs,
-                              int2 *__restrict__ ranges)
+// ---------------------------------------------------------- placement
+
+// One thread per (view, Gaussian) item, in the projection's grid: the item's
+// key goes to one claimed slot of each listed tile (the projection's
+// listed-tile word; wide rectangles are tested again with the same code).
+// Nothing is placed when the pairs overflowed.
+__global__ void k_place_pairs(const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
+                              const int64_t *__restrict__ view_item_offset, int vb, const uint32_t *__restrict__ listed,
+                              const int4 *__restrict__ rect, const float4 *__restrict__ geo,
+                              const float *__restrict__ conic_c, const float4 *__restrict__ cull,
+                              const float *__restrict__ tau, const float *__restrict__ depth, int TX, int TY, int tw,
+                              int th, int W, int H, const int2 *__restrict__ ranges,
+                              uint32_t *__restrict__ tile_count, const int64_t *__restrict__ n_pairs,
+                              uint64_t *__restrict__ pair_key)
 {
-    const int64_t n = *n_pairs;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = tile[i];
-        if (i == 0 || tile[i - 1] != t) ranges[t].x = (int)i;
-        if (i == n - 1 || tile[i + 1] != t) ranges[t].y = (int)(i + 1);
+    if (*n_pairs == 0) return;
+    const int v = vb + blockIdx.y;
+    const int scene = view_scene ? view_scene[v] : 0;
+    const int64_t ns = scene_offset[scene + 1] - scene_offset[scene];
+    const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t word = 0;
+    TileTest t = {};
+    uint64_t key = 0;
+    if (gl < ns) {                     // every lane stays for the warp-wide placement
+        const int64_t item = view_item_offset[v] - view_item_offset[vb] + gl;
+        word = listed[item];
+        if (word) {
+            t.rc = rect[item];
+            key = ((uint64_t)__float_as_uint(depth[item]) << 32) | (uint64_t)(uint32_t)item;
+        }
+        if (word & kWideRect) {
+            const float4 g = geo[item], cu = cull[item];
+            t = TileTest{g.x, g.y, g.z, g.w, conic_c[item], cu.z, cu.w, tau[item], t.rc};
+        }
+    }
+    place_listed(word, t, (uint32_t)blockIdx.y * (uint32_t)(TX * TY), key, TX, tw, th, W, H, ranges, tile_count,
+                 pair_key);
+}
+
+// ---------------------------------------------------------- tile sort
+
+__device__ __forceinline__ void write_sorted(uint64_t k, int64_t i, uint32_t tile, uint32_t *__restrict__ pair_tile,
+                                             uint32_t *__restrict__ pair_item)
+{
+    pair_item[i] = (uint32_t)k;
+    pair_tile[i] = tile;
+}
+
+// Bitonic sort, ascending, of a warp's 32 keys (one per lane) through shuffles.
+__device__ __forceinline__ uint64_t warp_bitonic32(uint64_t a)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+            const uint64_t p = __shfl_xor_sync(0xffffffffu, (unsigned long long)a, j);
+            const uint64_t lo = a < p ? a : p, hi = a < p ? p : a;
+            a = lower == up ? lo : hi;
+        }
+    }
+    return a;
+}
+
+// Merge sort of up to G * kMergeE keys by a group of G threads (a warp or a
+// block): each thread sorts 8 consecutive keys with Batcher's odd-even merge
+// network (19 comparators), then runs of length L = 8, 16, ... are merged
+// pairwise, each thread writing 8 consecutive outputs of its pair after a
+// binary search for its start on the merge path.  Shared-memory word w is
+// stored at w + w / 16, so the 32 lanes' 8-key strides fall in different
+// banks.
+constexpr int kMergeE = 8;
+__host__ __device__ constexpr int padded(int w) { return w + (w >> 4); }
+
+__device__ __forceinline__ void cswap(uint64_t &a, uint64_t &b)
+{
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+__device__ __forceinline__ void sort8(uint64_t (&v)[8])
+{
+    cswap(v[0], v[1]); cswap(v[2], v[3]); cswap(v[4], v[5]); cswap(v[6], v[7]);
+    cswap(v[0], v[2]); cswap(v[1], v[3]); cswap(v[4], v[6]); cswap(v[5], v[7]);
+    cswap(v[1], v[2]); cswap(v[5], v[6]);
+    cswap(v[0], v[4]); cswap(v[1], v[5]); cswap(v[2], v[6]); cswap(v[3], v[7]);
+    cswap(v[2], v[4]); cswap(v[3], v[5]);
+    cswap(v[1], v[2]); cswap(v[3], v[4]); cswap(v[5], v[6]);
+}
+
+// Outputs [8t, 8t + 8) of the merge of the two sorted runs of length L that
+// contain position 8t (ties: the first run first).
+__device__ __forceinline__ void merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int L, int t)
+{
+    const int o = t * kMergeE;
+    const int base = o & ~(2 * L - 1);
+    const int d = o - base;
+    const uint64_t *A = src, *B = src;
+    const int a0 = base, b0 = base + L;
+    int lo = max(0, d - L), hi = min(d, L);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[padded(a0 + mid)] <= B[padded(b0 + d - 1 - mid)]) lo = mid + 1;
+        else hi = mid;
+    }
+    int i = lo, j = d - lo;
+    uint64_t a = i < L ? A[padded(a0 + i)] : 0ull, b = j < L ? B[padded(b0 + j)] : 0ull;
+#pragma unroll
+    for (int e = 0; e < kMergeE; e++) {
+        const bool ta = j >= L || (i < L && a <= b);
+        dst[padded(o + e)] = ta ? a : b;
+        i += ta;
+        j += !ta;
+        const int next = ta ? a0 + i : b0 + j;
+        const bool more = ta ? i < L : j < L;
+        const uint64_t v = more ? src[padded(next)] : 0ull;
+        a = ta ? v : a;
+        b = ta ? b : v;
+    }
+}
+
+template <bool BLOCK>
+__device__ __forceinline__ void group_sync()
+{
+    if (BLOCK) __syncthreads();
+    else __syncwarp();
+}
+
+// Sorts keys g[0, n) (n <= G * kMergeE) of a group of G threads (thread t of
+// the group) with shared buffers s0, s1 of padded(G * kMergeE) words each;
+// returns the buffer that holds the sorted keys, padded to a power of two
+// with ~0.  Ends with a group barrier.
+template <int G, bool BLOCK>
+__device__ __forceinline__ uint64_t *group_merge_sort(const uint64_t *__restrict__ g, int n, uint64_t *s0,
+                                                      uint64_t *s1, int t)
+{
+    int N = kMergeE;
+    while (N < n) N <<= 1;
+    for (int i = t; i < N; i += G) s1[padded(i)] = i < n ? g[i] : kPadKey;
+    group_sync<BLOCK>();
+    const int T = N / kMergeE;
+    if (t < T) {
+        uint64_t v[kMergeE];
+#pragma unroll
+        for (int e = 0; e < kMergeE; e++) v[e] = s1[padded(t * kMergeE + e)];
+        sort8(v);
+#pragma unroll
+        for (int e = 0; e < kMergeE; e++) s0[padded(t * kMergeE + e)] = v[e];
+    }
+    group_sync<BLOCK>();
+    uint64_t *src = s0, *dst = s1;
+    for (int L = kMergeE; L < N; L <<= 1) {
+        if (t < T) merge_pass(src, dst, L, t);
+        group_sync<BLOCK>();
+        uint64_t *x = src;
+        src = dst;
+        dst = x;
+    }
+    return src;
+}
+
+constexpr int kSortWarps = 8;                                    // warps per block of k_tile_sort_warp
+constexpr int kWarpSortMax = 32 * kMergeE;                       // longest list one warp sorts
+constexpr int kWarpBufWords = padded(kWarpSortMax);
+constexpr int kBlockSortThreads = 512;
+constexpr int kBlockSortKeys = kBlockSortThreads * kMergeE;      // longest list sorted in shared memory
+constexpr int kBlockBufWords = padded(kBlockSortKeys);
+constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
+
+// One warp per tile (grid-stride over the tiles): lists of up to 32 keys are
+// sorted in registers, up to kWarpSortMax by the warp's merge sort; longer
+// ones are queued for k_tile_sort_block.
+__global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *__restrict__ ranges, int64_t n_tiles,
+                                                                    const uint64_t *__restrict__ pair_key,
+                                                                    uint32_t *__restrict__ pair_tile,
+                                                                    uint32_t *__restrict__ pair_item,
+                                                                    uint32_t *__restrict__ long_tiles,
+                                                                    uint32_t *__restrict__ long_count)
+{
+    __shared__ uint64_t buf[kSortWarps][2][kWarpBufWords];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * kSortWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kSortWarps + w; t < n_tiles; t += warps) {
+        const int2 r = ranges[t];
+        const int n = r.y - r.x;
+        if (n == 0) continue;
+        const uint64_t *keys = pair_key + r.x;
+        if (n > kWarpSortMax) {
+            if (lane == 0) long_tiles[atomicAdd(long_count, 1u)] = (uint32_t)t;
+        } else if (n <= 32) {
+            const uint64_t a = warp_bitonic32(lane < n ? keys[lane] : kPadKey);
+            if (lane < n) write_sorted(a, r.x + lane, (uint32_t)t, pair_tile, pair_item);
+        } else {
+            const uint64_t *src = group_merge_sort<32, false>(keys, n, buf[w][0], buf[w][1], lane);
+            for (int i = lane; i < n; i += 32) write_sorted(src[padded(i)], r.x + i, (uint32_t)t, pair_tile, pair_item);
+            __syncwarp();
+        }
+    }
+}
+
+// Ascending compare-exchange of s[i] and s[l] (i < l).
+template <typename I>
+__device__ __forceinline__ void cex(uint64_t *s, I i, I l)
+{
+    const uint64_t x = s[i], y = s[l];
+    if (y < x) {
+        s[i] = y;
+        s[l] = x;
+    }
+}
+
+// Partner pairs of the bitonic network in the form whose comparators all put
+// the smaller key first: step (k, j) pairs i with i ^ (k - 1) when j = k / 2
+// (the flip) and with i + j otherwise; p enumerates the pairs' lower indices
+// (p = q j + r gives i = 2 q j + r = 2 p - r; k and j are powers of two).
+template <typename I>
+__device__ __forceinline__ void pair_of(I p, I k, I j, I &i, I &l)
+{
+    i = 2 * p - (p & (j - 1));
+    l = j == (k >> 1) ? i ^ (k - 1) : i + j;
+}
+
+// The steps of distance j_top, j_top / 2, ..., 1 of a stage whose flip
+// distance is larger (every pair is (i, i + j)), on the N0 keys (a power of
+// two) in shared memory; block-wide, ends with a barrier.
+__device__ void smem_stage_tail(uint64_t *s, int N0, int j_top)
+{
+    for (int j = j_top; j > 0; j >>= 1) {
+        for (int p = threadIdx.x; p < N0 / 2; p += blockDim.x) {
+            const int i = 2 * p - (p & (j - 1));
+            cex(s, padded(i), padded(i + j));
+        }
+        __syncthreads();
+    }
+}
+
+// Sorts the queued long lists, one block per list at a time.  A list of at
+// most kBlockSortKeys keys is merge-sorted in shared memory.  A longer one
+// (N = its length rounded up to a power of two, positions >= n read as
+// +infinity, so comparators that reach them change nothing) runs the bitonic
+// network: its chunks of kBlockSortKeys are first merge-sorted (which is what
+// the network's first stages produce), then every later stage applies its
+// steps of distance >= kBlockSortKeys in global memory and the rest chunk by
+// chunk in shared memory.
+__global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int2 *__restrict__ ranges,
+                                                                       uint64_t *__restrict__ pair_key,
+                                                                       uint32_t *__restrict__ pair_tile,
+                                                                       uint32_t *__restrict__ pair_item,
+                                                                       const uint32_t *__restrict__ long_tiles,
+                                                                       const uint32_t *__restrict__ long_count)
+{
+    extern __shared__ uint64_t smem_keys[];
+    uint64_t *s0 = smem_keys, *s1 = smem_keys + kBlockBufWords;
+    const uint32_t n_long = *long_count;
+    const int t = threadIdx.x;
+    for (uint32_t q = blockIdx.x; q < n_long; q += gridDim.x) {
+        const uint32_t tile = long_tiles[q];
+        const int2 r = ranges[tile];
+        const int64_t n = r.y - r.x;
+        uint64_t *g = pair_key + r.x;
+        if (n <= kBlockSortKeys) {
+            const uint64_t *src = group_merge_sort<kBlockSortThreads, true>(g, (int)n, s0, s1, t);
+            for (int i = t; i < n; i += kBlockSortThreads) write_sorted(src[padded(i)], r.x + i, tile, pair_tile, pair_item);
+            __syncthreads();
+            continue;
+        }
+        int64_t N = 1;
+        while (N < n) N <<= 1;
+        const int S = kBlockSortKeys;
+        for (int64_t c0 = 0; c0 < n; c0 += S) {
+            const int nc = (int)(n - c0 < S ? n - c0 : S);
+            const uint64_t *src = group_merge_sort<kBlockSortThreads, true>(g + c0, nc, s0, s1, t);
+            for (int i = t; i < nc; i += kBlockSortThreads) g[c0 + i] = src[padded(i)];
+            __syncthreads();
+        }
+        for (int64_t k = 2 * (int64_t)S; k <= N; k <<= 1) {
+            for (int64_t j = k >> 1; j >= S; j >>= 1) {
+                for (int64_t p = t; p < N / 2; p += kBlockSortThreads) {
+                    int64_t i, l;
+                    pair_of(p, k, j, i, l);
+                    if (l < n) cex(g, i, l);
+                }
+                __syncthreads();
+            }
+            for (int64_t c0 = 0; c0 < n; c0 += S) {
+                for (int i = t; i < S; i += kBlockSortThreads) s0[padded(i)] = c0 + i < n ? g[c0 + i] : kPadKey;
+                __syncthreads();
+                smem_stage_tail(s0, S, S >> 1);
+                for (int i = t; i < S && c0 + i < n; i += kBlockSortThreads) {
+                    if (k == N) write_sorted(s0[padded(i)], r.x + c0 + i, tile, pair_tile, pair_item);
+                    else g[c0 + i] = s0[padded(i)];
+                }
+                __syncthreads();
+            }
+        }
     }
 }
 
@@ -464,72 +501,48 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_group_place(const int2 *
     }
 }
 
-int ceil_log2(int64_t x)
-{
-    int b = 0;
-    while ((int64_t(1) << b) < x) b++;
-    return b;
-}
-
 }  // namespace
 
-size_t radix_sort_hist_words(int blocks) { return (size_t)kRadix * blocks + kRadix; }
+int bin_chunks(int64_t n_tiles) { return (int)std::max<int64_t>(1, (n_tiles + kTilesPerChunk - 1) / kTilesPerChunk); }
 
-int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,
-                     const SortScratch &s, cudaStream_t st)
+cudaError_t binning_setup()
 {
-    int cur = 0;
-    if (n_max <= 0) return cur;
-    // fixed grid for the largest count this call can see (graph capture), at
-    // most s.blocks; with fewer elements the trailing blocks have empty chunks
-    const int blocks = (int)std::min<int64_t>(s.blocks, (n_max + kSortTile - 1) / kSortTile);
-    for (int shift = 0; shift < bits; shift += kRadixBits) {
-        cudaMemsetAsync(s.digit_total, 0, kRadix * sizeof(uint32_t), st);
-        k_radix_upsweep<<<blocks, kSortThreads, 0, st>>>(keys[cur], d_n, shift, s.hist, s.digit_total);
-        k_radix_offsets<<<kRadix, kSortThreads, 0, st>>>(s.hist, s.digit_total, blocks);
-        k_radix_downsweep<<<blocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], d_n,
-                                                           shift, s.hist);
-        cur = 1 - cur;
-        note_launches(3);
-    }
-    return cur;
-}
-
-void gather_scan(const uint32_t *counts, const uint32_t *idx, int64_t n, int64_t *out, const ScanScratch &s,
-                 cudaStream_t st)
-{
-    k_scan_reduce<<<s.blocks, kScanThreads, 0, st>>>(counts, idx, n, s.block_sums);
-    k_scan_top<<<1, 1024, 0, st>>>(s.block_sums, s.blocks);
-    k_scan_down<<<s.blocks, kScanThreads, 0, st>>>(counts, idx, n, s.block_sums, out);
-    note_launches(3);
+    return cudaFuncSetAttribute(k_tile_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockSortSmem);
 }
 
 vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
 {
-    const int64_t n_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
     const int64_t n_tiles = (int64_t)vc * p->TX * p->TY;
-    k_set_i64<<<1, 32, 0, st>>>(p->d_n_items, n_items);
-    note_launches(1);
-    // 1. depth order of the items (stable: ties keep the item order)
-    const int a = radix_sort_pairs(p->keyA, p->valA, p->d_n_items, n_items, 32, p->sort_scratch, st);
-    // 2. pair offsets in depth order
-    gather_scan(p->touched, p->valA[a], n_items, p->offsets, p->scan_scratch, st);
-    // 3. emit pairs
-    const int grid = num_sms() * 4;
-    k_emit_pairs<<<grid, 256, 0, st>>>(p->valA[a], p->offsets, n_items, p->rect, p->geo, p->conic_c, p->cull,
-                                       p->tau, p->d_view_item_offset, vb, vc, p->TX, p->TY, p->desc.tile_w,
-                                       p->desc.tile_h, p->desc.width, p->desc.height, p->desc.pair_capacity,
-                                       p->pair_tile[0], p->pair_item[0], p->d_n_pairs, p->d_status);
-    VBM_LAUNCH("emit_pairs");
-    note_launches(1);
-    // 4. stable sort of the pairs by tile
-    p->pair_buf = radix_sort_pairs(p->pair_tile, p->pair_item, p->d_n_pairs, p->desc.pair_capacity,
-                                   ceil_log2(n_tiles), p->sort_scratch, st);
-    // 5. tile ranges
-    VBM_CUDA(cudaMemsetAsync(p->ranges, 0, sizeof(int2) * n_tiles, st));
-    k_tile_ranges<<<grid, 256, 0, st>>>(p->pair_tile[p->pair_buf], p->d_n_pairs, p->ranges);
-    VBM_LAUNCH("tile_ranges");
-    note_launches(1);
+    const BinScratch &b = p->bin_scratch;
+    const int chunks = bin_chunks(n_tiles);
+    // 1. ranges from the per-tile counts of the projection
+    k_tile_chunk_sums<<<chunks, kScanThreads, 0, st>>>(p->tile_count, n_tiles, b.chunk_sums);
+    VBM_LAUNCH("tile_chunk_sums");
+    k_tile_scan<<<chunks, kScanThreads, 0, st>>>(p->tile_count, n_tiles, b.chunk_sums, chunks,
+                                                 p->desc.pair_capacity, p->ranges, p->d_n_pairs, p->d_status,
+                                                 b.long_count);
+    VBM_LAUNCH("tile_scan");
+    note_launches(2);
+    // 2. every item's key into a slot of each listed tile
+    if (p->max_scene > 0) {
+        dim3 grid((unsigned)((p->max_scene + 255) / 256), (unsigned)vc);
+        k_place_pairs<<<grid, 256, 0, st>>>(p->d_scene_offset, p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
+                                            p->d_view_item_offset, vb, p->listed, p->rect, p->geo, p->conic_c,
+                                            p->cull, p->tau, p->depth, p->TX, p->TY, p->desc.tile_w, p->desc.tile_h,
+                                            p->desc.width, p->desc.height, p->ranges, p->tile_count, p->d_n_pairs,
+                                            p->pair_key);
+        VBM_LAUNCH("place_pairs");
+        note_launches(1);
+    }
+    // 3. each tile's list sorted by (depth, item)
+    const int sw = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 8, (n_tiles + kSortWarps - 1) / kSortWarps));
+    k_tile_sort_warp<<<sw, kSortWarps * 32, 0, st>>>(p->ranges, n_tiles, p->pair_key, p->pair_tile, p->pair_item,
+                                                     b.long_tiles, b.long_count);
+    VBM_LAUNCH("tile_sort_warp");
+    k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
+        p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);
+    VBM_LAUNCH("tile_sort_block");
+    note_launches(2);
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
         VBM_CUDA(cudaMemsetAsync(p->tile_queue, 0, kTileQueueWords * sizeof(int), st));
         const int64_t og_need = (n_tiles + kOrderThreads - 1) / kOrderThreads;

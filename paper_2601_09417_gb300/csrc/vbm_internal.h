@@ -105,65 +105,88 @@ __device__ __forceinline__ bool listed_k(const TileTest &t, int k, int tw, int t
                        W, H);
 }
 
-// Number of listed tiles of this lane's rectangle (0 when !valid).  All 32
-// lanes of the warp must call it.
-__device__ __forceinline__ uint32_t count_listed(bool valid, const TileTest &t, int tw, int th, int W, int H)
+__device__ __forceinline__ uint32_t tile_id_k(const TileTest &t, int k, uint32_t tile0, int TX)
 {
-    const int area = valid ? (t.rc.z - t.rc.x) * (t.rc.w - t.rc.y) : 0;
-    uint32_t cnt = 0;
-    if (area > 0 && area <= kSerialTiles)
-        for (int k = 0; k < area; k++) cnt += listed_k(t, k, tw, th, W, H) ? 1u : 0u;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t big = __ballot_sync(0xffffffffu, area > kSerialTiles); big; big &= big - 1) {
-        const int src = __ffs(big) - 1;
-        const TileTest b = shfl_test(t, src);
-        const int a = (b.rc.z - b.rc.x) * (b.rc.w - b.rc.y);
-        uint32_t c = 0;
-        for (int k0 = 0; k0 < a; k0 += 32) {
-            const int k = k0 + lane;
-            c += __popc(__ballot_sync(0xffffffffu, k < a && listed_k(b, k, tw, th, W, H)));
-        }
-        if (lane == src) cnt = c;
-    }
-    return cnt;
+    const int cols = t.rc.z - t.rc.x;
+    return tile0 + (uint32_t)((t.rc.y + k / cols) * TX + t.rc.x + k % cols);
 }
 
-// Write (tile0 + tile id, item) for the listed tiles of this lane's
-// rectangle, row-major, from position beg.  All 32 lanes must call it.
-__device__ __forceinline__ void emit_listed(bool valid, const TileTest &t, uint32_t tile0, uint32_t item,
-                                            int64_t beg, int TX, int tw, int th, int W, int H,
-                                            uint32_t *__restrict__ pair_tile, uint32_t *__restrict__ pair_item)
+// Listed tiles of this lane's rectangle, as one word: 0 when none (or
+// !valid); for a rectangle of at most kSerialTiles tiles, bit k set when its
+// k-th tile (row-major) is listed; for a larger one, kWideRect (its tiles are
+// tested again, by the whole warp, where they are needed).  With tile_count,
+// adds one to the counter of every listed tile (tile ids tile0 + row-major
+// index in a TX-wide grid).  All 32 lanes of the warp must call it.
+constexpr uint32_t kWideRect = 1u << 31;
+
+__device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, int tw, int th, int W, int H,
+                                                 uint32_t *__restrict__ tile_count, uint32_t tile0, int TX)
 {
     const int area = valid ? (t.rc.z - t.rc.x) * (t.rc.w - t.rc.y) : 0;
-    if (area > 0 && area <= kSerialTiles) {
-        const int cols = t.rc.z - t.rc.x;
-        int64_t o = beg;
+    uint32_t word = 0;
+    if (area > 0 && area <= kSerialTiles)
         for (int k = 0; k < area; k++)
             if (listed_k(t, k, tw, th, W, H)) {
-                pair_tile[o] = tile0 + (uint32_t)((t.rc.y + k / cols) * TX + t.rc.x + k % cols);
-                pair_item[o] = item;
-                o++;
+                word |= 1u << k;
+                atomicAdd(&tile_count[tile_id_k(t, k, tile0, TX)], 1u);
             }
-    }
     const int lane = threadIdx.x & 31;
     for (uint32_t big = __ballot_sync(0xffffffffu, area > kSerialTiles); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
         const TileTest b = shfl_test(t, src);
         const uint32_t b_tile0 = __shfl_sync(0xffffffffu, tile0, src);
-        const uint32_t b_item = __shfl_sync(0xffffffffu, item, src);
-        int64_t o = __shfl_sync(0xffffffffu, (long long)beg, src);
-        const int cols = b.rc.z - b.rc.x;
-        const int a = cols * (b.rc.w - b.rc.y);
+        const int a = (b.rc.z - b.rc.x) * (b.rc.w - b.rc.y);
+        bool any = false;
         for (int k0 = 0; k0 < a; k0 += 32) {
             const int k = k0 + lane;
             const bool ok = k < a && listed_k(b, k, tw, th, W, H);
-            const uint32_t m = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                const int64_t pos = o + __popc(m & ((1u << lane) - 1u));
-                pair_tile[pos] = b_tile0 + (uint32_t)((b.rc.y + k / cols) * TX + b.rc.x + k % cols);
-                pair_item[pos] = b_item;
+            if (ok) atomicAdd(&tile_count[tile_id_k(b, k, b_tile0, TX)], 1u);
+            any |= __any_sync(0xffffffffu, ok);
+        }
+        if (lane == src && any) word = kWideRect;
+    }
+    return word;
+}
+
+// Bucket placement: for every listed tile of this lane's rectangle (the word
+// listed_tiles returned; a wide rectangle's tiles are tested again with the
+// same code), claim a slot of that tile's range by decrementing its counter
+// (left at zero once every claim is made) and store the key there.  Order
+// within a tile is arbitrary: a sort by key follows.  A claim on a counter
+// already at zero (impossible while the counts and the claims take the same
+// decisions) stores nothing.  All 32 lanes must call it; t needs only its
+// rectangle unless the word is kWideRect.
+__device__ __forceinline__ void place_listed(uint32_t word, const TileTest &t, uint32_t tile0, uint64_t key, int TX,
+                                             int tw, int th, int W, int H, const int2 *__restrict__ ranges,
+                                             uint32_t *__restrict__ tile_count, uint64_t *__restrict__ pair_key)
+{
+    if (word && !(word & kWideRect)) {
+        // every claim is issued before the first store depends on one
+        uint32_t tid[kSerialTiles], slot[kSerialTiles];
+#pragma unroll
+        for (int k = 0; k < kSerialTiles; k++)
+            if ((word >> k) & 1u) {
+                tid[k] = tile_id_k(t, k, tile0, TX);
+                slot[k] = atomicSub(&tile_count[tid[k]], 1u);
             }
-            o += __popc(m);
+#pragma unroll
+        for (int k = 0; k < kSerialTiles; k++)
+            if (((word >> k) & 1u) && slot[k]) pair_key[(int64_t)ranges[tid[k]].x + slot[k] - 1u] = key;
+    }
+    const int lane = threadIdx.x & 31;
+    for (uint32_t big = __ballot_sync(0xffffffffu, (word & kWideRect) != 0); big; big &= big - 1) {
+        const int src = __ffs(big) - 1;
+        const TileTest b = shfl_test(t, src);
+        const uint32_t b_tile0 = __shfl_sync(0xffffffffu, tile0, src);
+        const uint64_t b_key = __shfl_sync(0xffffffffu, (unsigned long long)key, src);
+        const int a = (b.rc.z - b.rc.x) * (b.rc.w - b.rc.y);
+        for (int k0 = 0; k0 < a; k0 += 32) {
+            const int k = k0 + lane;
+            if (k < a && listed_k(b, k, tw, th, W, H)) {
+                const uint32_t id = tile_id_k(b, k, b_tile0, TX);
+                const uint32_t sl = atomicSub(&tile_count[id], 1u);
+                if (sl) pair_key[(int64_t)ranges[id].x + sl - 1u] = b_key;
+            }
         }
     }
 }
@@ -211,29 +234,21 @@ struct FilterBank {
 };
 FilterBank make_filters(int wavelet);
 
-// ---------------------------------------------------------------- sorting
-// Stable LSD radix sort of (uint32 key, uint32 value) pairs over the low
-// `bits` bits of the key; the element count is read from d_n on the device.
-// Results end in (keys[0], vals[0]) or (keys[1], vals[1]): the returned index.
+// ---------------------------------------------------------------- binning
+// Work-queue counters of the compositing kernels (2), tile-group sizes and
+// cursors of the longest-first order (32 + 32).
 constexpr int kTileQueueWords = 2 + 32 + 32;
 
-struct SortScratch {
-    uint32_t *hist = nullptr;          // radix * blocks counters
-    uint32_t *digit_total = nullptr;   // radix counters (inside the same allocation)
-    int blocks = 0;                    // largest sort grid (hist has radix x blocks counters)
+// Scratch of the binning: per-chunk sums of the tile counts and the list of
+// tiles too long for one warp's sort.
+struct BinScratch {
+    int64_t *chunk_sums = nullptr;  // [chunks]
+    int chunks = 0;                 // ceil(max tiles / tiles per chunk)
+    uint32_t *long_tiles = nullptr; // [max tiles]
+    uint32_t *long_count = nullptr; // [1]
 };
-size_t radix_sort_hist_words(int blocks);
-int radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,
-                     const SortScratch &s, cudaStream_t st);
-
-// Exclusive scan of uint32 counts gathered through an index array:
-// out[i] = sum_{j<i} counts[idx[j]], out[n] = total (int64).
-struct ScanScratch {
-    int64_t *block_sums = nullptr;  // blocks + 1
-    int blocks = 0;
-};
-void gather_scan(const uint32_t *counts, const uint32_t *idx, int64_t n, int64_t *out, const ScanScratch &s,
-                 cudaStream_t st);
+int bin_chunks(int64_t n_tiles);
+cudaError_t binning_setup();   // once per plan, before any capture: kernel attributes
 
 }  // namespace vbm
 
@@ -264,16 +279,14 @@ struct vbm_plan {
     float *depth = nullptr;
     int4 *rect = nullptr;
     int32_t *radius = nullptr;
-    uint32_t *touched = nullptr;
-    uint32_t *keyA[2] = {nullptr, nullptr};
-    uint32_t *valA[2] = {nullptr, nullptr};
-    int64_t *offsets = nullptr;             // [items + 1]
+    uint32_t *listed = nullptr;              // [items] listed-tile word of the projection (listed_tiles)
     float *g_splat = nullptr;               // [items][kGradStride]
 
     // pairs
-    uint32_t *pair_tile[2] = {nullptr, nullptr};
-    uint32_t *pair_item[2] = {nullptr, nullptr};
-    int pair_buf = 0;                        // which buffer holds the sorted pairs
+    uint64_t *pair_key = nullptr;            // [pairs] (depth bits << 32 | item), bucketed by tile
+    uint32_t *pair_tile = nullptr;           // [pairs] sorted
+    uint32_t *pair_item = nullptr;           // [pairs] sorted
+    uint32_t *tile_count = nullptr;          // [V * TX * TY] listed pairs per tile (zero between calls)
     int2 *ranges = nullptr;                  // [V * TX * TY]
     int *tile_order = nullptr;               // [V * TX * TY] longest list first (persistent mode)
     int *tile_queue = nullptr;               // [kTileQueueWords]: work-queue counters (forward, backward),
@@ -284,9 +297,7 @@ struct vbm_plan {
     int32_t *n_contrib = nullptr;
 
     // scratch + counters
-    vbm::SortScratch sort_scratch;
-    vbm::ScanScratch scan_scratch;
-    int64_t *d_n_items = nullptr;            // device copy of the call's item count
+    vbm::BinScratch bin_scratch;
     int64_t *d_n_pairs = nullptr;            // pairs of the last call
     int64_t *d_status = nullptr;             // [0] status bits, [1] max pairs needed
 

@@ -97,6 +97,38 @@ def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile):
     assert np.array_equal(st["ranges"], ranges)
 
 
+def test_binning_long_lists_bit_exact(cuda_lib):
+    """Crowded scene: one cluster of 10,000 small Gaussians (plus 500 exact copies, so
+    equal depths must fall back to the index order) projects into a few tiles, whose
+    lists exceed the 4096 keys one block sorts in shared memory; a wider cluster gives
+    lists of every shorter length class (<= 32, <= 256, <= 4096).  The pair lists must
+    equal the oracle's (tile, depth, index) sort bit for bit."""
+    from vbm_inputs.gaussians import random_gaussians
+    from vbm_inputs import orbit_cameras
+    from vbm_inputs.cameras import cameras_as_float32
+    G, W, H, tile = 32, 100, 76, (8, 8)
+    core = random_gaussians(10000, 15.7, 16.3, seed=21, scale_range=(0.1, 0.4), opacity_logit_range=(-1.0, 2.0))
+    wide = random_gaussians(3000, 8.0, 24.0, seed=22, scale_range=(0.2, 1.5), opacity_logit_range=(-2.0, 2.0))
+    P = np.concatenate([core, core[:, :500], wide], axis=1).astype(np.float32)
+    cams = orbit_cameras((G, G, G), 1, W, H)
+    plan, *_ = _forward(cuda_lib, P, cams, W, H, tile=tile)
+    st = plan_state(plan, 1)
+    TX, TY = _tiles(W, H, tile)
+    lengths = st["ranges"][:, 1] - st["ranges"][:, 0]
+    assert lengths.max() > 2 * 4096
+    for lo, hi in [(1, 32), (33, 256), (257, 4096)]:
+        assert ((lengths >= lo) & (lengths <= hi)).any(), (lo, hi)
+    rec = gpu_binning_records(st)
+    tiles, items, ranges = oraster.bin_sort(np.zeros(st["n_items"], dtype=np.int32), st["rect"],
+                                            st["depth"].astype(np.float64), TX, TY, 1, splat32=rec, tile=tile,
+                                            image=(W, H))
+    assert st["n_pairs"] == tiles.size
+    assert np.array_equal(st["pair_tile"].astype(np.int64), tiles)
+    assert np.array_equal(st["pair_item"].astype(np.int64), items.astype(np.int64))
+    assert np.array_equal(st["ranges"], ranges)
+    plan.close()
+
+
 @pytest.mark.parametrize("tile,ppt,persistent,gl", [((16, 16), 1, False, 32), ((16, 16), 2, False, 32),
                                                     ((16, 16), 4, False, 32), ((8, 8), 2, False, 32),
                                                     ((16, 8), 1, False, 32), ((16, 8), 4, False, 32),
