@@ -125,12 +125,19 @@ __device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, 
     const int area = valid ? (t.rc.z - t.rc.x) * (t.rc.w - t.rc.y) : 0;
     uint32_t word = 0;
     if (area > 0 && area <= kSerialTiles)
-        for (int k = 0; k < area; k++)
-            if (listed_k(t, k, tw, th, W, H)) {
-                word |= 1u << k;
-                atomicAdd(&tile_count[tile_id_k(t, k, tile0, TX)], 1u);
-            }
+        for (int k = 0; k < area; k++) word |= listed_k(t, k, tw, th, W, H) ? 1u << k : 0u;
+    // counts of the small rectangles: one atomic per distinct tile among the
+    // warp's lanes at each rectangle position (neighbouring items share tiles)
+    const int span = __reduce_max_sync(0xffffffffu, word ? 32 - __clz(word) : 0);
     const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < kSerialTiles; k++) {
+        if (k >= span) break;
+        const bool on = (word >> k) & 1u;
+        const uint32_t id = on ? tile_id_k(t, k, tile0, TX) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, id);
+        if (on && lane == __ffs(peers) - 1) atomicAdd(&tile_count[id], (uint32_t)__popc(peers));
+    }
     for (uint32_t big = __ballot_sync(0xffffffffu, area > kSerialTiles); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
         const TileTest b = shfl_test(t, src);
@@ -152,28 +159,39 @@ __device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, 
 // listed_tiles returned; a wide rectangle's tiles are tested again with the
 // same code), claim a slot of that tile's range by decrementing its counter
 // (left at zero once every claim is made) and store the key there.  Order
-// within a tile is arbitrary: a sort by key follows.  A claim on a counter
-// already at zero (impossible while the counts and the claims take the same
+// within a tile is arbitrary: a sort by key follows.  A claim beyond what the
+// counter holds (impossible while the counts and the claims take the same
 // decisions) stores nothing.  All 32 lanes must call it; t needs only its
 // rectangle unless the word is kWideRect.
 __device__ __forceinline__ void place_listed(uint32_t word, const TileTest &t, uint32_t tile0, uint64_t key, int TX,
                                              int tw, int th, int W, int H, const int2 *__restrict__ ranges,
                                              uint32_t *__restrict__ tile_count, uint64_t *__restrict__ pair_key)
 {
-    if (word && !(word & kWideRect)) {
-        // every claim is issued before the first store depends on one
-        uint32_t tid[kSerialTiles], slot[kSerialTiles];
-#pragma unroll
-        for (int k = 0; k < kSerialTiles; k++)
-            if ((word >> k) & 1u) {
-                tid[k] = tile_id_k(t, k, tile0, TX);
-                slot[k] = atomicSub(&tile_count[tid[k]], 1u);
-            }
-#pragma unroll
-        for (int k = 0; k < kSerialTiles; k++)
-            if (((word >> k) & 1u) && slot[k]) pair_key[(int64_t)ranges[tid[k]].x + slot[k] - 1u] = key;
-    }
+    // small rectangles: lanes claiming the same tile at the same rectangle
+    // position share one atomic (the leader takes the group's slots and each
+    // lane its rank among them); every claim is issued before the first store
+    // depends on one
+    const uint32_t small = (word & kWideRect) ? 0u : word;
+    const int span = __reduce_max_sync(0xffffffffu, small ? 32 - __clz(small) : 0);
     const int lane = threadIdx.x & 31;
+    uint32_t tid[kSerialTiles], peer[kSerialTiles], old[kSerialTiles];
+#pragma unroll
+    for (int k = 0; k < kSerialTiles; k++) {
+        old[k] = 0u;
+        if (k >= span) continue;
+        const bool on = (small >> k) & 1u;
+        tid[k] = on ? tile_id_k(t, k, tile0, TX) : 0xffffffffu;
+        peer[k] = __match_any_sync(0xffffffffu, tid[k]);
+        if (on && lane == __ffs(peer[k]) - 1) old[k] = atomicSub(&tile_count[tid[k]], (uint32_t)__popc(peer[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < kSerialTiles; k++) {
+        if (k >= span) break;
+        if (!((small >> k) & 1u)) continue;
+        const uint32_t o = __shfl_sync(peer[k], old[k], __ffs(peer[k]) - 1);
+        const int slot = (int)o - __popc(peer[k]) + __popc(peer[k] & ((1u << lane) - 1u));
+        if (slot >= 0) pair_key[(int64_t)ranges[tid[k]].x + slot] = key;
+    }
     for (uint32_t big = __ballot_sync(0xffffffffu, (word & kWideRect) != 0); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
         const TileTest b = shfl_test(t, src);
