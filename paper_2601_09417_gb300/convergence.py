@@ -12,7 +12,9 @@ rotation, opacity 0.1, colour uniform in [0, 1] (seeded).
 
 Every `every` steps the views are rendered and scored against the targets: PSNR from
 the mean squared error over all views and channels, and the mean SSIM from the
-library's own loss kernel (11 x 11 Gaussian window, sigma 1.5).
+library's own loss kernel (11 x 11 Gaussian window, sigma 1.5).  For the TF-mode
+workload (one Gaussian set per mode, Sec. 4.4) the sets are also rendered together,
+as one scene, and scored against the DVR of the sum of the modes' TFs.
 
     python -m paper_2601_09417_gb300.convergence --config c1 --steps 2000 --every 250
     python -m paper_2601_09417_gb300.convergence --variants full,isotropic,unit_weight,haar,random
@@ -42,30 +44,57 @@ def random_init(n, G, seed=0):
     return P.astype(np.float32)
 
 
-def score(ft):
-    """(PSNR in dB, mean SSIM) of the current Gaussians' renders against the targets."""
-    ft.plan.forward(ft.params, ft.cams, ft.img, bg=ft.bg)
-    loss = torch.zeros(1, dtype=torch.float64, device=ft.device)
-    dimg = torch.empty_like(ft.img)
-    n = ft.img.numel()
-    vbm.loss(ft.img, ft.targets, ft.V, ft.H, ft.W, 1.0, 1.0 / n, loss, dimg, ft.ws)   # lambda = 1: 1 - SSIM
-    torch.cuda.synchronize(ft.device)
-    img = ft.img.cpu().numpy().astype(np.float64)
-    tgt = ft.targets.cpu().numpy().astype(np.float64)
-    mse = float(np.mean((img - tgt) ** 2))
+def image_score(img, tgt, ws):
+    """(PSNR in dB, mean SSIM) of images [V][3][H][W] against targets of the same shape."""
+    V, _, H, W = img.shape
+    loss = torch.zeros(1, dtype=torch.float64, device=img.device)
+    dimg = torch.empty_like(img)
+    vbm.loss(img, tgt, V, H, W, 1.0, 1.0 / img.numel(), loss, dimg, ws)   # lambda = 1: 1 - SSIM
+    torch.cuda.synchronize(img.device)
+    a = img.cpu().numpy().astype(np.float64)
+    b = tgt.cpu().numpy().astype(np.float64)
+    mse = float(np.mean((a - b) ** 2))
     psnr = 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
     return psnr, 1.0 - float(loss.item())
 
 
-def run(ft, steps, every):
-    curve = [(0,) + score(ft)]
+def score(ft):
+    """(PSNR in dB, mean SSIM) of the current Gaussians' renders against the targets."""
+    ft.plan.forward(ft.params, ft.cams, ft.img, bg=ft.bg)
+    return image_score(ft.img, ft.targets, ft.ws)
+
+
+class ConcatScore:
+    """Renders every Gaussian set of a TF-mode batch together, as one scene, on the first
+    mode's cameras and scores it against the DVR of the modes' summed TF."""
+
+    def __init__(self, ft, w, tile):
+        self.targets = w.union_targets
+        V, _, H, W = self.targets.shape
+        n = ft.params.shape[1]
+        self.cams = vbm.cameras_to_device(w.cam_records[:V], ft.device)
+        self.plan = vbm.Plan([0, n], V, W, H, tile_w=tile[0], tile_h=tile[1],
+                             pair_capacity=vbm.default_pair_capacity(n * V))
+        self.img = torch.zeros_like(self.targets)
+        self.ft = ft
+
+    def __call__(self):
+        self.plan.forward(self.ft.params, self.cams, self.img, bg=self.ft.bg)
+        return image_score(self.img, self.targets, self.ft.ws)
+
+
+def run(ft, steps, every, extra=None):
+    """[(step, PSNR, SSIM[, concatenated PSNR, SSIM])] every `every` steps."""
+    def point(k):
+        return (k,) + score(ft) + (extra() if extra else ())
+    curve = [point(0)]
     done = 0
     while done < steps:
         k = min(every, steps - done)
         for _ in range(k):
             ft.step_graph()
         done += k
-        curve.append((done,) + score(ft))
+        curve.append(point(done))
     return curve
 
 
@@ -83,31 +112,36 @@ def main():
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     w = make_workload(args.config, device)
-    if w.scene_offset is not None:
+    if "edges" in w.cfg:
         raise SystemExit("convergence runs take a single-volume workload")
     G = w.cfg["G"]
     tile = tuple(int(x) for x in args.tile.split("x"))
     launch = dict(tile=tile, ppt=args.ppt, group_lanes=args.gl, persistent=True, extent=G)
     builds = {"full": dict(), "isotropic": dict(ablation=vbm.BANK_ISOTROPIC),
               "unit_weight": dict(ablation=vbm.BANK_UNIT_WEIGHT), "haar": dict(wavelet=1)}
-    inits = {}
+    inits = {}         # name -> (initial Gaussians, scene offsets)
     for name in args.variants.split(","):
         if name == "random":
-            inits[name] = torch.from_numpy(random_init(w.n, G)).to(device)
+            inits[name] = (torch.from_numpy(random_init(w.n, G)).to(device), w.scene_offset)
         elif name == "full":
-            inits[name] = w.params.clone()
+            inits[name] = (w.params.clone(), w.scene_offset)
         else:
-            inits[name] = make_workload(args.config, device, **builds[name]).params.clone()
-    out = {"config": args.config, "gaussians": {k: int(v.shape[1]) for k, v in inits.items()},
+            wv = make_workload(args.config, device, **builds[name])
+            inits[name] = (wv.params.clone(), wv.scene_offset)
+    out = {"config": args.config, "gaussians": {k: int(v[0].shape[1]) for k, v in inits.items()},
            "views": int(w.targets.shape[0]), "steps": args.steps, "curves": {}}
-    for name, P in inits.items():
-        ft = FineTuner(P.contiguous(), w.cam_records, w.targets, **launch)
-        curve = run(ft, args.steps, args.every)
+    for name, (P, so) in inits.items():
+        ft = FineTuner(P.contiguous(), w.cam_records, w.targets, scene_offset=so, view_scene=w.view_scene, **launch)
+        concat = ConcatScore(ft, w, tile) if w.union_targets is not None else None
+        curve = run(ft, args.steps, args.every, concat)
         ok, need, bad = ft.check()
-        out["curves"][name] = [{"step": s, "psnr": p, "ssim": q} for s, p, q in curve]
+        out["curves"][name] = [dict(zip(("step", "psnr", "ssim", "concat_psnr", "concat_ssim"), c)) for c in curve]
         out["curves"][name + "_pairs_ok"] = bool(ok)
-        for s, p, q in curve:
-            print(json.dumps({"init": name, "step": s, "psnr_db": round(p, 3), "ssim": round(q, 4)}), flush=True)
+        for c in curve:
+            rec = {"init": name, "step": c[0], "psnr_db": round(c[1], 3), "ssim": round(c[2], 4)}
+            if len(c) > 3:
+                rec.update(concat_psnr_db=round(c[3], 3), concat_ssim=round(c[4], 4))
+            print(json.dumps(rec), flush=True)
     print(json.dumps(out))
 
 

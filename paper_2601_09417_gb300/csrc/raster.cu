@@ -263,20 +263,23 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
         evaluated[k] = rg.y - rg.x;
     }
     // rounds of 32 entries, software-pipelined: while round r is composited,
-    // the lane's entry of round r + 1 and its index in round r + 2 are in flight
+    // the lane's entries of rounds r + 1 and r + 2 and its index in round r + 3
+    // are in flight
     const int lane = threadIdx.x & 31;
     const int n_rounds = (rg.y - rg.x + 31) / 32;
     Entry cur = gather_entry(load_index(pair_item, rg.x + lane, rg.y), geo, col, conic_c, cull);
-    uint32_t it_next = load_index(pair_item, rg.x + 32 + lane, rg.y);
+    Entry nxt = gather_entry(load_index(pair_item, rg.x + 32 + lane, rg.y), geo, col, conic_c, cull);
+    uint32_t it_next = load_index(pair_item, rg.x + 64 + lane, rg.y);
     for (int r = 0; r < n_rounds; r++) {
         bool all_done = true;
 #pragma unroll
         for (int k = 0; k < PPT; k++) all_done &= done[k];
         if (__all_sync(0xffffffffu, all_done)) break;
-        const uint32_t it_after = load_index(pair_item, rg.x + 32 * (r + 2) + lane, rg.y);
-        const Entry nxt = gather_entry(it_next, geo, col, conic_c, cull);
+        const uint32_t it_after = load_index(pair_item, rg.x + 32 * (r + 3) + lane, rg.y);
+        const Entry nxt2 = gather_entry(it_next, geo, col, conic_c, cull);
         uint32_t m = commit_entry<PPT, GL>(cur, 32 * r + lane + 1, wg, s, nullptr);
         cur = nxt;
+        nxt = nxt2;
         it_next = it_after;
         while (m) {                                    // no warp collectives inside
             const int j = __ffs(m) - 1;
@@ -481,20 +484,23 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     group_sum_layout<GL>(lane, vbase, vcnt);
     const uint32_t gmask = GL == 32 ? 0xffffffffu : (((1u << GL) - 1u) << (wg.g * GL));
     // rounds from the back: round r holds list positions [max(0, wmax - 32 (r + 1)), wmax - 32 r),
-    // software-pipelined as in the forward
+    // software-pipelined as in the forward (entries two rounds ahead in flight)
     const int n_rounds = (wmax + 31) / 32;
     auto round_lo = [&](int r) { return max(0, wmax - 32 * (r + 1)); };
     auto round_idx = [&](int r) { return rg.x + round_lo(r) + lane; };
     auto round_end = [&](int r) { return rg.x + wmax - 32 * r; };
     Entry cur = gather_entry(n_rounds > 0 ? load_index(pair_item, round_idx(0), round_end(0)) : kNoItem, geo, col,
                              conic_c, cull);
-    uint32_t it_next = n_rounds > 1 ? load_index(pair_item, round_idx(1), round_end(1)) : kNoItem;
+    Entry nxt = gather_entry(n_rounds > 1 ? load_index(pair_item, round_idx(1), round_end(1)) : kNoItem, geo, col,
+                             conic_c, cull);
+    uint32_t it_next = n_rounds > 2 ? load_index(pair_item, round_idx(2), round_end(2)) : kNoItem;
     for (int r = 0; r < n_rounds; r++) {
-        const uint32_t it_after = r + 2 < n_rounds ? load_index(pair_item, round_idx(r + 2), round_end(r + 2))
+        const uint32_t it_after = r + 3 < n_rounds ? load_index(pair_item, round_idx(r + 3), round_end(r + 3))
                                                    : kNoItem;
-        const Entry nxt = gather_entry(it_next, geo, col, conic_c, cull);
+        const Entry nxt2 = gather_entry(it_next, geo, col, conic_c, cull);
         uint32_t m = commit_entry<PPT, GL>(cur, round_lo(r) + lane + 1, wg, s, gmax);
         cur = nxt;
+        nxt = nxt2;
         it_next = it_after;
         const int steps = __reduce_max_sync(0xffffffffu, __popc(m));
         for (int step = 0; step < steps; step++) {   // back to front

@@ -8,7 +8,7 @@ to DVR target images by vbm_render_dvr on the GPU.
 import numpy as np
 import torch
 
-from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, config, orbit_cameras, volume_for_config
+from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, config, orbit_cameras, tf_mode, tf_modes_union, volume_for_config
 from vbm_inputs.cameras import camera_array
 
 from . import vbm
@@ -17,7 +17,8 @@ from . import vbm
 class Workload:
     """Gaussians P[14][n], packed cameras, target images [V][3][H][W] (device)."""
 
-    def __init__(self, cfg, params, n, cam_records, cams, targets, scene_offset=None, view_scene=None, volumes=None):
+    def __init__(self, cfg, params, n, cam_records, cams, targets, scene_offset=None, view_scene=None, volumes=None,
+                 union_targets=None):
         self.cfg = cfg
         self.params = params
         self.n = n
@@ -27,6 +28,9 @@ class Workload:
         self.scene_offset = scene_offset
         self.view_scene = view_scene
         self.volumes = volumes
+        # TF-mode workloads: DVR of the sum of the modes' TFs on one mode's
+        # cameras, the target of the concatenated Gaussian sets
+        self.union_targets = union_targets
 
     @property
     def views(self):
@@ -75,6 +79,27 @@ def make_workload(key, device="cuda", wavelet=0, ablation=0):
         torch.cuda.synchronize()
         return Workload(cfg, params, int(so[-1]), np.concatenate(recs_all), cams_all, torch.cat(tgts),
                         scene_offset=np.asarray(so, dtype=np.int64), view_scene=np.asarray(vs, dtype=np.int32))
+    if "modes" in cfg:                      # one Gaussian set per TF mode (Sec. 4.4)
+        F = volume_for_config(cfg)
+        Ps, so, tgts, vs = [], [0], [], []
+        cams = recs = None
+        for h in range(cfg["modes"]):
+            tf_h = vbm.make_tf(*tf_mode(h))
+            Fd, dims, P, n = _build_one(F, cfg["levels"], cfg["K_tot"], device, tf_h, wavelet, ablation)
+            cams = orbit_cameras(dims, cfg["views"], cfg["width"], cfg["height"])
+            recs, tgt = _render_targets(Fd, dims, tf_h, cams, cfg["width"], cfg["height"], device)
+            Ps.append(P)
+            so.append(so[-1] + n)
+            tgts.append(tgt)
+            vs.extend([h] * len(cams))
+        _, union = _render_targets(Fd, dims, vbm.make_tf(*tf_modes_union()), cams, cfg["width"], cfg["height"],
+                                   device)
+        params = torch.cat(Ps, dim=1).contiguous()
+        torch.cuda.synchronize()
+        H = cfg["modes"]
+        return Workload(cfg, params, int(so[-1]), np.concatenate([recs] * H), cams * H, torch.cat(tgts),
+                        scene_offset=np.asarray(so, dtype=np.int64), view_scene=np.asarray(vs, dtype=np.int32),
+                        volumes=[F], union_targets=union)
     F = volume_for_config(cfg)
     Fd, dims, params, n = _build_one(F, cfg["levels"], cfg["K_tot"], device, tf, wavelet, ablation)
     cams = orbit_cameras(dims, cfg["views"], cfg["width"], cfg["height"])

@@ -71,7 +71,7 @@ def test_bank_matches_oracle(cuda_lib, levels, wavelet):
     assert matched >= 7 * min(levels, 3)
 
 
-def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0):
+def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0, knots=None):
     dims = F.shape[::-1]
     bank = vbm.bank_build(J, wavelet)
     if ablation:
@@ -80,21 +80,29 @@ def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0):
     n = F.size
     coef = torch.zeros(4 * n, device="cuda")
     keep = torch.zeros(n, dtype=torch.uint8, device="cuda")
-    params, count = vbm.build(torch.from_numpy(F).cuda(), dims, _tf(vbm), bank, sel, capacity=n, coef=coef, keep=keep)
+    tf = _tf(vbm) if knots is None else vbm.make_tf(*knots)
+    params, count = vbm.build(torch.from_numpy(F).cuda(), dims, tf, bank, sel, capacity=n, coef=coef, keep=keep)
     torch.cuda.synchronize()
     return (params.cpu().numpy()[:, :count], count, coef.cpu().numpy().reshape(4, *F.shape),
             keep.cpu().numpy().reshape(F.shape).astype(bool), bank)
 
 
-@pytest.mark.parametrize("G,J,K_tot,seed,ablation", [(32, 2, 4096, 0, 0), (64, 3, 20000, 1, 0), (32, 2, 4096, 0, 1),
-                                                      (32, 2, 4096, 0, 2)])
-def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation):
+@pytest.mark.parametrize("G,J,K_tot,seed,ablation,mode", [(32, 2, 4096, 0, 0, None), (64, 3, 20000, 1, 0, None),
+                                                           (32, 2, 4096, 0, 1, None), (32, 2, 4096, 0, 2, None),
+                                                           (32, 2, 4096, 0, 0, 1), (64, 3, 20000, 1, 0, 3)])
+def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation, mode):
     """vbm_build against the oracle: pyramid, kept indices (bit-exact), Gaussians; also
-    with the ablated banks of Sec. 5.3 (isotropic covariance, unit weight)."""
+    with the ablated banks of Sec. 5.3 (isotropic covariance, unit weight) and with two of
+    the TF modes of Sec. 4.4 (non-zero over one value interval only)."""
+    from vbm_inputs import tf_mode
     F = blob_volume(G, 4 if G == 32 else 12, seed=seed)
-    P, count, A_gpu, keep_gpu, bank = _build(cuda_lib, F, J, K_tot, ablation=ablation)
+    knots = None if mode is None else tf_mode(mode)
+    P, count, A_gpu, keep_gpu, bank = _build(cuda_lib, F, J, K_tot, ablation=ablation, knots=knots)
     # 1. coefficient pyramid vs the FP64 oracle pipeline (TF + DWT)
-    x, rgba = _tf32()
+    if knots is None:
+        x, rgba = _tf32()
+    else:     # the library holds the knots in float32
+        x, rgba = (k.astype(np.float32).astype(np.float64) for k in knots)
     RF = apply_tf_vectorised(F.astype(np.float64), x, rgba)
     fb = filter_bank(0)
     A_ref = np.stack([dwt3d(RF[..., c], J, fb) for c in range(4)])
@@ -104,7 +112,10 @@ def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation):
     for (j, o), m in zip(subbands(J), masks):
         assert np.array_equal(keep_gpu[subband_slices(F.shape, j, o)], m), (j, o)
     assert count == sum(int(m.sum()) for m in masks)
-    assert 0.5 * K_tot < count < 1.5 * K_tot
+    if mode is None:
+        assert 0.5 * K_tot < count < 1.5 * K_tot
+    else:
+        assert count > 100
     # 3. mapping on the GPU's pyramid and masks with the library's bank
     ref = map_coefficients(A_gpu.astype(np.float64), masks, J, cuda_lib.bank_to_dicts(bank))
     assert ref.shape == P.shape

@@ -102,3 +102,29 @@ def test_pixel_subset_matches_full_image():
     sub = render_dvr(F, TF_KNOTS_X, TF_KNOTS_RGBA, cam, pixels=pix)
     for n, (i, j) in enumerate(pix):
         assert np.allclose(sub[:, n], full[:, j, i], atol=0)
+
+
+def test_tf_modes_disjoint_and_union_is_their_sum():
+    """The five TF modes (Sec. 4.4: each non-zero only over its own value interval)
+    have disjoint supports, peak at their interval's midpoint with the tabulated
+    colour, and the union TF equals their sum everywhere (checked through the
+    oracle's TF on a dense grid, against numpy's own interpolation of each mode)."""
+    from vbm_inputs import TF_MODE_EDGES, tf_mode, tf_modes_union
+    x = np.linspace(0.0, 1.0, 4001)
+    per_mode = []
+    for h in range(5):
+        kx, krgba = tf_mode(h)
+        rgba = apply_tf_vectorised(x, kx, krgba)
+        ref = np.stack([np.interp(x, kx, krgba[:, c]) for c in range(4)], axis=-1)
+        assert np.allclose(rgba, ref, atol=1e-15)
+        a, b = TF_MODE_EDGES[h], TF_MODE_EDGES[h + 1]
+        outside = (x <= a) | (x >= b)
+        assert np.all(rgba[outside] == 0.0) and np.all(rgba[~outside, 3] > 0.0)
+        mid = apply_tf_vectorised(np.array([0.5 * (a + b)]), kx, krgba)[0]
+        assert np.array_equal(mid, krgba[2])
+        per_mode.append(rgba)
+    support = np.stack([m[:, 3] > 0 for m in per_mode])
+    assert support.sum(axis=0).max() == 1
+    ux, urgba = tf_modes_union()
+    assert len(ux) <= 16 and np.all(np.diff(ux) > 0)
+    assert np.allclose(apply_tf_vectorised(x, ux, urgba), sum(per_mode), atol=1e-15)

@@ -1,4 +1,4 @@
-"""Workload table: the five synthetic workloads the tests and benchmark use.
+"""Workload table: the synthetic workloads the tests and benchmark use.
 
 Each entry names the volume recipe, wavelet levels J, global coefficient
 budget K_tot, number of views and image size.  K_tot is the budget handed to
@@ -36,6 +36,12 @@ CONFIGS = {
     "c4": dict(key="c4", workload="512^3 supernova-like shells, J=5, ~3M Gaussians, 8 views 1024x1024",
                volume="supernova", G=512, seed=4, levels=5, K_tot=3000000,
                views=8, width=1024, height=1024, fwd_only=(1920, 1080), recompute=True),
+    # Sec. 4.4's TF modes: the c1 volume under five transfer functions with
+    # disjoint value intervals, one Gaussian set (scene) per mode, each
+    # fine-tuned against its own DVR targets, all in one batch
+    "c5": dict(key="c5", workload="c1 volume under 5 TF modes, one Gaussian set per mode, 8 views 512x512 per mode",
+               volume="blobs+bandnoise", G=128, blobs=32, seed=1, levels=3, K_tot=250000,
+               views=8, width=512, height=512, modes=5),
 }
 
 
