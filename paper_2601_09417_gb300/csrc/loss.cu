@@ -27,6 +27,7 @@ constexpr int kHalf = 5;
 constexpr int kTW = 32, kTH = 32;                  // output tile
 constexpr int kSW = kTW + 2 * kHalf, kSH = kTH + 2 * kHalf;
 constexpr int kSWP = kSW + 2;                      // padded row of the staged tile (zero-filled)
+constexpr int kHP = kTW + 1;                       // padded row of the horizontal sums
 constexpr int kSeg = 11, kSegs = 3;                // horizontal: 3 segments of <= 11 outputs per row
 constexpr int kVRows = 8;                          // vertical: 8 outputs per column segment
 constexpr int kLossThreads = 128;
@@ -97,9 +98,12 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
                                                           float *__restrict__ g3, double *__restrict__ partial)
 {
     __shared__ __align__(16) float2 sxy[kSH][kSWP];
-    __shared__ __align__(16) float2 hm[kSH][kTW];   // horizontal sums of (x, y)
-    __shared__ __align__(16) float2 hq[kSH][kTW];   // of (x^2, y^2)
-    __shared__ float hp[kSH][kTW];                   // of x y
+    // horizontal sums of (x, y), (x^2, y^2) and x y; rows padded by one
+    // element so the horizontal pass's lanes (11 rows at the same column)
+    // write to different banks
+    __shared__ __align__(16) float2 hm[kSH][kHP];
+    __shared__ __align__(16) float2 hq[kSH][kHP];
+    __shared__ float hp[kSH][kHP];
     __shared__ float red[2][kLossThreads / 32];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kTW, oy = blockIdx.y * kTH;
@@ -203,8 +207,8 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
 {
     __shared__ __align__(16) float2 s12[kSH][kSWP];   // (g1, g2) with halo
     __shared__ float s3[kSH][kSWP];                   // g3 with halo
-    __shared__ __align__(16) float2 h12[kSH][kTW];
-    __shared__ float h3[kSH][kTW];
+    __shared__ __align__(16) float2 h12[kSH][kHP];
+    __shared__ float h3[kSH][kHP];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kTW, oy = blockIdx.y * kTH;
     const int64_t base = (int64_t)plane * H * W;

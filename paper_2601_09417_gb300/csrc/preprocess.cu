@@ -8,7 +8,11 @@
 // item to the pair count of each listed tile.  The
 // backward recomputes the forward state from the parameters (cheaper than
 // storing it) and sums the per-view contributions of a Gaussian in
-// registers, so the parameter gradient is written once, without atomics.
+// registers, so the parameter gradient is written once, without atomics: the
+// view-independent state (rotation, 3D covariance, opacity) is built once per
+// Gaussian, and since the scale and rotation gradients are linear in
+// dL/dSigma, that is summed over the views and taken through the
+// covariance's factorisation once.
 //
 // Sec. 4.4 fine-tunes "as in" 3D Gaussian Splatting; the constants are that
 // method's (vbm_internal.h), except that the splat radius is the extent of the
@@ -30,14 +34,9 @@ struct ProjState {
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
-__device__ __forceinline__ int floordiv_i(int a, int b)
-{
-    int q = a / b;
-    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
-}
-
-__device__ void project_state(const float *__restrict__ P, int64_t stride, int64_t g, const vbm_camera &cam,
-                              ProjState &st)
+// The view-independent part: mean, scales, normalised quaternion, rotation,
+// 3D covariance and opacity.
+__device__ __forceinline__ void project_base(const float *__restrict__ P, int64_t stride, int64_t g, ProjState &st)
 {
 #pragma unroll
     for (int k = 0; k < 3; k++) st.mu[k] = P[k * stride + g];
@@ -61,11 +60,17 @@ __device__ void project_state(const float *__restrict__ P, int64_t stride, int64
         for (int b = 0; b < 3; b++)
             st.Sig[a][b] = st.R[a][0] * s2[0] * st.R[b][0] + st.R[a][1] * s2[1] * st.R[b][1] +
                            st.R[a][2] * s2[2] * st.R[b][2];
+    st.opac = 1.0f / (1.0f + expf(-P[10 * stride + g]));
+}
+
+// The view-dependent part, from the base state: camera-space mean, culling,
+// frustum clamp, the Jacobian rows T0, T1 (J W) and the 2D covariance.
+__device__ __forceinline__ void project_view(const vbm_camera &cam, ProjState &st)
+{
     const float *Wm = cam.R;
 #pragma unroll
     for (int r = 0; r < 3; r++)
         st.t[r] = Wm[3 * r] * st.mu[0] + Wm[3 * r + 1] * st.mu[1] + Wm[3 * r + 2] * st.mu[2] + cam.t[r];
-    st.opac = 1.0f / (1.0f + expf(-P[10 * stride + g]));
     st.culled = !(st.t[2] > cam.znear);
     st.clampx = st.clampy = false;
     if (st.culled) return;
@@ -96,6 +101,13 @@ __device__ void project_state(const float *__restrict__ P, int64_t stride, int64
     st.c = st.T1[0] * ST1[0] + st.T1[1] * ST1[1] + st.T1[2] * ST1[2] + kDilation;
     st.det = st.a * st.c - st.b * st.b;
     if (!(st.det > 0.f)) st.culled = true;
+}
+
+__device__ __forceinline__ void project_state(const float *__restrict__ P, int64_t stride, int64_t g,
+                                              const vbm_camera &cam, ProjState &st)
+{
+    project_base(P, stride, g, st);
+    project_view(cam, st);
 }
 
 __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
@@ -156,10 +168,12 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
             r_int = (int)r;
             int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
             int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
-            rc.x = min(max(floordiv_i(fu - r_int, tw), 0), TX);
-            rc.z = min(max(floordiv_i(fu + r_int, tw) + 1, 0), TX);
-            rc.y = min(max(floordiv_i(fv - r_int, th), 0), TY);
-            rc.w = min(max(floordiv_i(fv + r_int, th) + 1, 0), TY);
+            // floor division by the tile size, a power of two: arithmetic shifts
+            const int lw = __ffs(tw) - 1, lh = __ffs(th) - 1;
+            rc.x = min(max((fu - r_int) >> lw, 0), TX);
+            rc.z = min(max(((fu + r_int) >> lw) + 1, 0), TX);
+            rc.y = min(max((fv - r_int) >> lh, 0), TY);
+            rc.w = min(max(((fv + r_int) >> lh) + 1, 0), TY);
             tt = TileTest{u, vv, A, B, C, bc, ba, tau, rc};
             has_tiles = true;
         } else {
@@ -202,6 +216,15 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
     float acc[14];
 #pragma unroll
     for (int k = 0; k < 14; k++) acc[k] = 0.f;
+    // dL/dSigma + its transpose, summed over the views: the scale and rotation
+    // gradients are linear in it, so they are formed once after the loop
+    float GS2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) GS2[i][j] = 0.f;
+    ProjState st;
+    project_base(P, stride, g, st);
     bool seen = false;
     for (int e = scene_view_ptr[scene]; e < scene_view_ptr[scene + 1]; e++) {
         const int v = scene_views[e];
@@ -212,8 +235,7 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
 #pragma unroll
         for (int k = 0; k < 9; k++) g9[k] = gs[item * kGradStride + k];
         const vbm_camera cam = cams[v];
-        ProjState st;
-        project_state(P, stride, g, cam, st);
+        project_view(cam, st);
         acc[10] += g9[5] * st.opac * (1.f - st.opac);
         acc[11] += g9[6];
         acc[12] += g9[7];
@@ -254,13 +276,16 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
                     dJ12 * (fy * st.yzc * itz2 - fy * itz * dyc_dtz);
 #pragma unroll
         for (int k = 0; k < 3; k++) acc[k] += Wm[k] * dt0 + Wm[3 + k] * dt1 + Wm[6 + k] * dt2;
-        // dL/dSigma over all nine entries, then Sigma = M M^T with M = R diag(s)
-        float GS[3][3];
+        // dL/dSigma = dLa T0 T0^T + dLb T0 T1^T + dLc T1 T1^T; add it and its transpose
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
-                GS[i][j] = dLa * st.T0[i] * st.T0[j] + dLb * st.T0[i] * st.T1[j] + dLc * st.T1[i] * st.T1[j];
+                GS2[i][j] += 2.f * dLa * st.T0[i] * st.T0[j] + dLb * (st.T0[i] * st.T1[j] + st.T1[i] * st.T0[j]) +
+                             2.f * dLc * st.T1[i] * st.T1[j];
+    }
+    if (seen) {
+        // Sigma = M M^T with M = R diag(s): dL/dM = (G + G^T) M
         float dR[3][3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -269,7 +294,7 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
             for (int i = 0; i < 3; i++) {
                 float dM = 0.f;
 #pragma unroll
-                for (int j = 0; j < 3; j++) dM += (GS[i][j] + GS[j][i]) * st.R[j][k] * st.s[k];
+                for (int j = 0; j < 3; j++) dM += GS2[i][j] * st.R[j][k] * st.s[k];
                 ds += dM * st.R[i][k];
                 dR[i][k] = dM * st.s[k];
             }

@@ -5,9 +5,9 @@
 // index".  The projection counts, per tile, the items whose exact tile test
 // lists it; an exclusive scan of those counts gives every tile its range of
 // the pair array.  Each item then claims one slot per listed tile with an
-// atomic decrement of the tile's counter (which leaves every counter at zero
-// for the next call) and stores its 64-bit key (depth bits << 32 | item)
-// there.  The slots of a tile are filled in arbitrary order, so each tile's
+// atomic decrement of the tile's counter (which the scan set to the range's
+// end, and the tile sort clears for the next call) and stores its 64-bit key
+// (depth bits << 32 | item) there.  The slots of a tile are filled in arbitrary order, so each tile's
 // list is sorted by that key: depth > 0 for every listed item, so the float
 // bits order like the depths, and the low word breaks ties by item index.
 // The result is unique, so it equals the oracle's (tile, depth, index) sort
@@ -61,10 +61,12 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_chunk_sums(const uint32_t
 }
 
 // Exclusive scan of the tile counts into ranges [begin, end) ((0, 0) for an
-// empty tile).  Each block adds up the sums of the chunks before its own and
-// of all chunks.  If the total exceeds the capacity every range is empty, the
-// pair count is 0, the counters are cleared and the status records the size
-// needed.  Also resets the long-list queue of the sort.
+// empty tile); each non-empty tile's counter becomes its range's end, the
+// cursor the placement claims slots from.  Each block adds up the sums of the
+// chunks before its own and of all chunks.  If the total exceeds the capacity
+// every range is empty, the pair count is 0, the counters are cleared and the
+// status records the size needed.  Also resets the long-list queue of the
+// sort.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict__ tile_count, int64_t n_tiles,
                                                             const int64_t *__restrict__ chunk_sums, int chunks,
                                                             int64_t capacity, int2 *__restrict__ ranges,
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict
             tile_count[t] = 0u;
         } else {
             ranges[t] = c[it] ? make_int2((int)run, (int)(run + c[it])) : make_int2(0, 0);
+            if (c[it]) tile_count[t] = (uint32_t)(run + c[it]);   // claim cursor: the range's end
         }
         run += c[it];
     }
@@ -149,11 +152,11 @@ __global__ void k_place_pairs(const int64_t *__restrict__ scene_offset, const in
                               const int4 *__restrict__ rect, const float4 *__restrict__ geo,
                               const float *__restrict__ conic_c, const float4 *__restrict__ cull,
                               const float *__restrict__ tau, const float *__restrict__ depth, int TX, int TY, int tw,
-                              int th, int W, int H, const int2 *__restrict__ ranges,
-                              uint32_t *__restrict__ tile_count, const int64_t *__restrict__ n_pairs,
-                              uint64_t *__restrict__ pair_key)
+                              int th, int W, int H, uint32_t *__restrict__ tile_count,
+                              const int64_t *__restrict__ n_pairs, uint64_t *__restrict__ pair_key)
 {
-    if (*n_pairs == 0) return;
+    const int64_t n_total = *n_pairs;
+    if (n_total == 0) return;
     const int v = vb + blockIdx.y;
     const int scene = view_scene ? view_scene[v] : 0;
     const int64_t ns = scene_offset[scene + 1] - scene_offset[scene];
@@ -173,7 +176,7 @@ __global__ void k_place_pairs(const int64_t *__restrict__ scene_offset, const in
             t = TileTest{g.x, g.y, g.z, g.w, conic_c[item], cu.z, cu.w, tau[item], t.rc};
         }
     }
-    place_listed(word, t, (uint32_t)blockIdx.y * (uint32_t)(TX * TY), key, TX, tw, th, W, H, ranges, tile_count,
+    place_listed(word, t, (uint32_t)blockIdx.y * (uint32_t)(TX * TY), key, TX, tw, th, W, H, n_total, tile_count,
                  pair_key);
 }
 
@@ -311,11 +314,13 @@ constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
 
 // One warp per tile (grid-stride over the tiles): lists of up to 32 keys are
 // sorted in registers, up to kWarpSortMax by the warp's merge sort; longer
-// ones are queued for k_tile_sort_block.
+// ones are queued for k_tile_sort_block.  Also clears every tile's counter
+// for the next call.
 __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *__restrict__ ranges, int64_t n_tiles,
                                                                     const uint64_t *__restrict__ pair_key,
                                                                     uint32_t *__restrict__ pair_tile,
                                                                     uint32_t *__restrict__ pair_item,
+                                                                    uint32_t *__restrict__ tile_count,
                                                                     uint32_t *__restrict__ long_tiles,
                                                                     uint32_t *__restrict__ long_count)
 {
@@ -325,6 +330,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *
     for (int64_t t = (int64_t)blockIdx.x * kSortWarps + w; t < n_tiles; t += warps) {
         const int2 r = ranges[t];
         const int n = r.y - r.x;
+        if (lane == 0) tile_count[t] = 0u;
         if (n == 0) continue;
         const uint64_t *keys = pair_key + r.x;
         if (n > kWarpSortMax) {
@@ -529,15 +535,14 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
         k_place_pairs<<<grid, 256, 0, st>>>(p->d_scene_offset, p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
                                             p->d_view_item_offset, vb, p->listed, p->rect, p->geo, p->conic_c,
                                             p->cull, p->tau, p->depth, p->TX, p->TY, p->desc.tile_w, p->desc.tile_h,
-                                            p->desc.width, p->desc.height, p->ranges, p->tile_count, p->d_n_pairs,
-                                            p->pair_key);
+                                            p->desc.width, p->desc.height, p->tile_count, p->d_n_pairs, p->pair_key);
         VBM_LAUNCH("place_pairs");
         note_launches(1);
     }
     // 3. each tile's list sorted by (depth, item)
     const int sw = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 8, (n_tiles + kSortWarps - 1) / kSortWarps));
     k_tile_sort_warp<<<sw, kSortWarps * 32, 0, st>>>(p->ranges, n_tiles, p->pair_key, p->pair_tile, p->pair_item,
-                                                     b.long_tiles, b.long_count);
+                                                     p->tile_count, b.long_tiles, b.long_count);
     VBM_LAUNCH("tile_sort_warp");
     k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
         p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);

@@ -98,17 +98,23 @@ __device__ __forceinline__ TileTest shfl_test(const TileTest &t, int src)
     return r;
 }
 
-__device__ __forceinline__ bool listed_k(const TileTest &t, int k, int tw, int th, int W, int H)
+__device__ __forceinline__ bool listed_at(const TileTest &t, int col, int row, int tw, int th, int W, int H)
 {
-    const int cols = t.rc.z - t.rc.x;
-    return tile_listed(t.u, t.v, t.A, t.B, t.C, t.bc, t.ba, t.tau, t.rc.x + k % cols, t.rc.y + k / cols, tw, th,
-                       W, H);
+    return tile_listed(t.u, t.v, t.A, t.B, t.C, t.bc, t.ba, t.tau, t.rc.x + col, t.rc.y + row, tw, th, W, H);
 }
 
-__device__ __forceinline__ uint32_t tile_id_k(const TileTest &t, int k, uint32_t tile0, int TX)
+__device__ __forceinline__ uint32_t tile_id_at(const TileTest &t, int col, int row, uint32_t tile0, int TX)
 {
-    const int cols = t.rc.z - t.rc.x;
-    return tile0 + (uint32_t)((t.rc.y + k / cols) * TX + t.rc.x + k % cols);
+    return tile0 + (uint32_t)((t.rc.y + row) * TX + t.rc.x + col);
+}
+
+// Row-major position k of a rectangle with `cols` columns as (column, row).
+// Below 2^21 positions by a float reciprocal: (k + 1/2) / cols lies at least
+// 1 / (2 cols) from an integer, far more than the product's rounding error.
+__device__ __forceinline__ int2 rect_pos(int k, int cols, float inv_cols, int area)
+{
+    const int row = area < (1 << 21) ? (int)(((float)k + 0.5f) * inv_cols) : k / cols;
+    return make_int2(k - row * cols, row);
 }
 
 // Listed tiles of this lane's rectangle, as one word: 0 when none (or
@@ -122,32 +128,44 @@ constexpr uint32_t kWideRect = 1u << 31;
 __device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, int tw, int th, int W, int H,
                                                  uint32_t *__restrict__ tile_count, uint32_t tile0, int TX)
 {
-    const int area = valid ? (t.rc.z - t.rc.x) * (t.rc.w - t.rc.y) : 0;
+    const int cols = t.rc.z - t.rc.x;
+    const int area = valid ? cols * (t.rc.w - t.rc.y) : 0;
     uint32_t word = 0;
-    if (area > 0 && area <= kSerialTiles)
-        for (int k = 0; k < area; k++) word |= listed_k(t, k, tw, th, W, H) ? 1u << k : 0u;
+    if (area > 0 && area <= kSerialTiles) {
+        int k = 0;
+        for (int row = 0; row < t.rc.w - t.rc.y; row++)
+            for (int col = 0; col < cols; col++, k++) word |= listed_at(t, col, row, tw, th, W, H) ? 1u << k : 0u;
+    }
     // counts of the small rectangles: one atomic per distinct tile among the
     // warp's lanes at each rectangle position (neighbouring items share tiles)
     const int span = __reduce_max_sync(0xffffffffu, word ? 32 - __clz(word) : 0);
     const int lane = threadIdx.x & 31;
+    int col = 0, row = 0;
 #pragma unroll
     for (int k = 0; k < kSerialTiles; k++) {
         if (k >= span) break;
         const bool on = (word >> k) & 1u;
-        const uint32_t id = on ? tile_id_k(t, k, tile0, TX) : 0xffffffffu;
+        const uint32_t id = on ? tile_id_at(t, col, row, tile0, TX) : 0xffffffffu;
         const uint32_t peers = __match_any_sync(0xffffffffu, id);
         if (on && lane == __ffs(peers) - 1) atomicAdd(&tile_count[id], (uint32_t)__popc(peers));
+        if (++col == cols) {
+            col = 0;
+            row++;
+        }
     }
     for (uint32_t big = __ballot_sync(0xffffffffu, area > kSerialTiles); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
         const TileTest b = shfl_test(t, src);
         const uint32_t b_tile0 = __shfl_sync(0xffffffffu, tile0, src);
-        const int a = (b.rc.z - b.rc.x) * (b.rc.w - b.rc.y);
+        const int b_cols = b.rc.z - b.rc.x;
+        const int a = b_cols * (b.rc.w - b.rc.y);
+        const float inv_cols = 1.0f / (float)b_cols;
         bool any = false;
         for (int k0 = 0; k0 < a; k0 += 32) {
             const int k = k0 + lane;
-            const bool ok = k < a && listed_k(b, k, tw, th, W, H);
-            if (ok) atomicAdd(&tile_count[tile_id_k(b, k, b_tile0, TX)], 1u);
+            const int2 pos = rect_pos(k, b_cols, inv_cols, a);
+            const bool ok = k < a && listed_at(b, pos.x, pos.y, tw, th, W, H);
+            if (ok) atomicAdd(&tile_count[tile_id_at(b, pos.x, pos.y, b_tile0, TX)], 1u);
             any |= __any_sync(0xffffffffu, ok);
         }
         if (lane == src && any) word = kWideRect;
@@ -157,14 +175,15 @@ __device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, 
 
 // Bucket placement: for every listed tile of this lane's rectangle (the word
 // listed_tiles returned; a wide rectangle's tiles are tested again with the
-// same code), claim a slot of that tile's range by decrementing its counter
-// (left at zero once every claim is made) and store the key there.  Order
-// within a tile is arbitrary: a sort by key follows.  A claim beyond what the
-// counter holds (impossible while the counts and the claims take the same
-// decisions) stores nothing.  All 32 lanes must call it; t needs only its
-// rectangle unless the word is kWideRect.
+// same code), claim a slot of that tile's range and store the key there.  The
+// tile's counter holds the end of its unclaimed part of the pair array (the
+// scan sets it to the range's end), so a claim is one atomic decrement that
+// returns the slot directly.  Order within a tile is arbitrary: a sort by key
+// follows.  A slot outside [0, n_total) (impossible while the counts and the
+// claims take the same decisions) stores nothing.  All 32 lanes must call it;
+// t needs only its rectangle unless the word is kWideRect.
 __device__ __forceinline__ void place_listed(uint32_t word, const TileTest &t, uint32_t tile0, uint64_t key, int TX,
-                                             int tw, int th, int W, int H, const int2 *__restrict__ ranges,
+                                             int tw, int th, int W, int H, int64_t n_total,
                                              uint32_t *__restrict__ tile_count, uint64_t *__restrict__ pair_key)
 {
     // small rectangles: lanes claiming the same tile at the same rectangle
@@ -174,36 +193,45 @@ __device__ __forceinline__ void place_listed(uint32_t word, const TileTest &t, u
     const uint32_t small = (word & kWideRect) ? 0u : word;
     const int span = __reduce_max_sync(0xffffffffu, small ? 32 - __clz(small) : 0);
     const int lane = threadIdx.x & 31;
+    const int cols = t.rc.z - t.rc.x;
     uint32_t tid[kSerialTiles], peer[kSerialTiles], old[kSerialTiles];
+    int col = 0, row = 0;
 #pragma unroll
     for (int k = 0; k < kSerialTiles; k++) {
         old[k] = 0u;
         if (k >= span) continue;
         const bool on = (small >> k) & 1u;
-        tid[k] = on ? tile_id_k(t, k, tile0, TX) : 0xffffffffu;
+        tid[k] = on ? tile_id_at(t, col, row, tile0, TX) : 0xffffffffu;
         peer[k] = __match_any_sync(0xffffffffu, tid[k]);
         if (on && lane == __ffs(peer[k]) - 1) old[k] = atomicSub(&tile_count[tid[k]], (uint32_t)__popc(peer[k]));
+        if (++col == cols) {
+            col = 0;
+            row++;
+        }
     }
 #pragma unroll
     for (int k = 0; k < kSerialTiles; k++) {
         if (k >= span) break;
         if (!((small >> k) & 1u)) continue;
         const uint32_t o = __shfl_sync(peer[k], old[k], __ffs(peer[k]) - 1);
-        const int slot = (int)o - __popc(peer[k]) + __popc(peer[k] & ((1u << lane) - 1u));
-        if (slot >= 0) pair_key[(int64_t)ranges[tid[k]].x + slot] = key;
+        const int64_t slot = (int64_t)o - __popc(peer[k]) + __popc(peer[k] & ((1u << lane) - 1u));
+        if (slot >= 0 && slot < n_total) pair_key[slot] = key;
     }
     for (uint32_t big = __ballot_sync(0xffffffffu, (word & kWideRect) != 0); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
         const TileTest b = shfl_test(t, src);
         const uint32_t b_tile0 = __shfl_sync(0xffffffffu, tile0, src);
         const uint64_t b_key = __shfl_sync(0xffffffffu, (unsigned long long)key, src);
-        const int a = (b.rc.z - b.rc.x) * (b.rc.w - b.rc.y);
+        const int b_cols = b.rc.z - b.rc.x;
+        const int a = b_cols * (b.rc.w - b.rc.y);
+        const float inv_cols = 1.0f / (float)b_cols;
         for (int k0 = 0; k0 < a; k0 += 32) {
             const int k = k0 + lane;
-            if (k < a && listed_k(b, k, tw, th, W, H)) {
-                const uint32_t id = tile_id_k(b, k, b_tile0, TX);
-                const uint32_t sl = atomicSub(&tile_count[id], 1u);
-                if (sl) pair_key[(int64_t)ranges[id].x + sl - 1u] = b_key;
+            const int2 pos = rect_pos(k, b_cols, inv_cols, a);
+            if (k < a && listed_at(b, pos.x, pos.y, tw, th, W, H)) {
+                const uint32_t id = tile_id_at(b, pos.x, pos.y, b_tile0, TX);
+                const int64_t slot = (int64_t)atomicSub(&tile_count[id], 1u) - 1;
+                if (slot >= 0 && slot < n_total) pair_key[slot] = b_key;
             }
         }
     }
@@ -304,7 +332,8 @@ struct vbm_plan {
     uint64_t *pair_key = nullptr;            // [pairs] (depth bits << 32 | item), bucketed by tile
     uint32_t *pair_tile = nullptr;           // [pairs] sorted
     uint32_t *pair_item = nullptr;           // [pairs] sorted
-    uint32_t *tile_count = nullptr;          // [V * TX * TY] listed pairs per tile (zero between calls)
+    uint32_t *tile_count = nullptr;          // [V * TX * TY] listed pairs per tile, then the placement's
+                                             // claim cursor (zero between calls)
     int2 *ranges = nullptr;                  // [V * TX * TY]
     int *tile_order = nullptr;               // [V * TX * TY] longest list first (persistent mode)
     int *tile_queue = nullptr;               // [kTileQueueWords]: work-queue counters (forward, backward),
