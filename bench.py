@@ -72,6 +72,9 @@ def workload_extent(cfg):
     return max(cfg["edges"]) if "edges" in cfg else cfg["G"]
 
 
+# Fine-tuning steps run (with a fixed launch configuration) before the autotuner times its candidates.
+TUNE_WARM_STEPS = 30
+
 # Oracle timing window for workloads whose full view would take minutes on one core.
 CPU_CROP = {"c4": 256}
 
@@ -273,8 +276,17 @@ def main():
         tune_table = []
     else:
         from paper_2601_09417_gb300.autotune import autotune
-        (tile, ppt, gl, pers), tune_table = autotune(params, recs, V, W, H, scene_offset=w.scene_offset,
+        # tune on the Gaussians as they are a few dozen steps into fine-tuning:
+        # the first steps shrink the initial footprints, and the timed steps run
+        # in that regime
+        ftw = FineTuner(params.clone(), recs, targets, **batch, tile=(16, 16), ppt=1, group_lanes=16,
+                        persistent=True)
+        for _ in range(TUNE_WARM_STEPS):
+            ftw.step_batched()
+        torch.cuda.synchronize()
+        (tile, ppt, gl, pers), tune_table = autotune(ftw.params, recs, V, W, H, scene_offset=w.scene_offset,
                                                       view_scene=w.view_scene)
+        del ftw
     launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl)
     if args.profile_only:
         ftp = FineTuner(params, recs, targets, **batch, **launch)
@@ -440,7 +452,9 @@ def main():
             "autotune": {"candidates": len(tune_table),
                          "fastest": [{"tile": "%dx%d" % tuple(r["tile"]), "ppt": r["ppt"],
                                       "group_lanes": r["group_lanes"], "persistent": r["persistent"],
-                                      "ms_fwd_bwd": r["ms"]} for r in sorted(tune_table, key=lambda r: r["ms"])[:6]]},
+                                      "ms_fwd_bwd": r["ms"], "ms_fwd_bwd_retimed": r.get("ms_final")}
+                                     for r in sorted(tune_table, key=lambda r: r.get("ms_final", r["ms"]))[:6]],
+                         "tuned_after_steps": TUNE_WARM_STEPS if tune_table else 0},
             "batched_over_plain": plain_ms / ms_per_step,
             "step_ms_percentiles": {"p10": float(np.percentile(step_ms, 10)),
                                     "p50": float(np.percentile(step_ms, 50)),

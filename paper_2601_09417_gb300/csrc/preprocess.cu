@@ -26,7 +26,7 @@ namespace {
 
 struct ProjState {
     float mu[3], s[3], qn[4], qnorm, R[3][3], Sig[3][3];
-    float t[3], xzc, yzc;
+    float t[3], itz, xz, yz, xzc, yzc;
     bool clampx, clampy, culled;
     float T0[3], T1[3];
     float a, b, c, det, opac;
@@ -74,17 +74,21 @@ __device__ __forceinline__ void project_view(const vbm_camera &cam, ProjState &s
     st.culled = !(st.t[2] > cam.znear);
     st.clampx = st.clampy = false;
     if (st.culled) return;
-    float tz = st.t[2];
-    float xz = st.t[0] / tz, yz = st.t[1] / tz;
+    // one reciprocal of the depth and of each focal length instead of ten
+    // divisions (their results differ by an ulp or so)
+    const float itz = 1.0f / st.t[2], ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy;
+    st.itz = itz;
+    st.xz = st.t[0] * itz;
+    st.yz = st.t[1] * itz;
     float Wi = (float)cam.width, Hi = (float)cam.height;
-    float xlo = (-kFrustumGuard * Wi - cam.cx) / cam.fx, xhi = ((1.f + kFrustumGuard) * Wi - cam.cx) / cam.fx;
-    float ylo = (-kFrustumGuard * Hi - cam.cy) / cam.fy, yhi = ((1.f + kFrustumGuard) * Hi - cam.cy) / cam.fy;
-    st.xzc = clampf(xz, xlo, xhi);
-    st.yzc = clampf(yz, ylo, yhi);
-    st.clampx = st.xzc != xz;
-    st.clampy = st.yzc != yz;
-    float J00 = cam.fx / tz, J02 = -cam.fx * st.xzc / tz;
-    float J11 = cam.fy / tz, J12 = -cam.fy * st.yzc / tz;
+    float xlo = (-kFrustumGuard * Wi - cam.cx) * ifx, xhi = ((1.f + kFrustumGuard) * Wi - cam.cx) * ifx;
+    float ylo = (-kFrustumGuard * Hi - cam.cy) * ify, yhi = ((1.f + kFrustumGuard) * Hi - cam.cy) * ify;
+    st.xzc = clampf(st.xz, xlo, xhi);
+    st.yzc = clampf(st.yz, ylo, yhi);
+    st.clampx = st.xzc != st.xz;
+    st.clampy = st.yzc != st.yz;
+    float J00 = cam.fx * itz, J02 = -cam.fx * st.xzc * itz;
+    float J11 = cam.fy * itz, J12 = -cam.fy * st.yzc * itz;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         st.T0[k] = J00 * Wm[k] + J02 * Wm[6 + k];
@@ -152,8 +156,8 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
             // Bounded so the integer rectangle arithmetic cannot overflow; any
             // radius above 2^24 already spans every image narrower than 6.7M px.
             float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
-            float u = cam.fx * (st.t[0] / st.t[2]) + cam.cx;
-            float vv = cam.fy * (st.t[1] / st.t[2]) + cam.cy;
+            float u = cam.fx * st.xz + cam.cx;
+            float vv = cam.fy * st.yz + cam.cy;
             geo[item] = make_float4(u, vv, A, B);
             conic_c[item] = C;
             // For the tile test and the compositing kernels' culling: tau =
@@ -265,7 +269,7 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
         float dJ11 = dT1[0] * Wm[3] + dT1[1] * Wm[4] + dT1[2] * Wm[5];
         float dJ12 = dT1[0] * Wm[6] + dT1[1] * Wm[7] + dT1[2] * Wm[8];
         float tx = st.t[0], ty = st.t[1], tz = st.t[2];
-        float itz = 1.0f / tz, itz2 = itz * itz;
+        float itz = st.itz, itz2 = itz * itz;
         float dxc_dtx = st.clampx ? 0.f : itz, dxc_dtz = st.clampx ? 0.f : -tx * itz2;
         float dyc_dty = st.clampy ? 0.f : itz, dyc_dtz = st.clampy ? 0.f : -ty * itz2;
         float fx = cam.fx, fy = cam.fy;

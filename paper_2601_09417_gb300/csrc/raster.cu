@@ -147,8 +147,43 @@ struct WarpSlots {
     uint32_t item[32];
 };
 
+// Rounds of list entries the backward keeps in flight: their per-item data
+// is copied asynchronously (cp.async) into shared memory while earlier
+// rounds are processed, so the prefetch depth costs no registers.  Lane l
+// copies, and later reads, entry l of a round.
+constexpr int kStages = 3;
+
+struct RawStages {
+    float4 geo[kStages][32];
+    float4 col[kStages][32];
+    float4 cull[kStages][32];
+    float cc[kStages][32];
+    uint32_t it[kStages][32];
+};
+
 // One list entry's per-item data as loaded by a lane (it = kNoItem: none).
 constexpr uint32_t kNoItem = 0xffffffffu;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's copy groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 struct Entry {
     uint32_t it;
@@ -174,6 +209,41 @@ __device__ __forceinline__ Entry gather_entry(uint32_t it, const float4 *__restr
         e.cc = conic_c[it];
         e.c = col[it];
         e.cu = cull[it];
+    } else {
+        e.g = e.c = e.cu = make_float4(0.f, 0.f, 0.f, 0.f);
+        e.cc = 0.f;
+    }
+    return e;
+}
+
+// Start copying the lane's entry `it` of a round into stage st; one copy
+// group per round, empty when there is no entry.
+__device__ __forceinline__ void stage_entry(RawStages &rs, int st, uint32_t it, const float4 *__restrict__ geo,
+                                            const float4 *__restrict__ col, const float *__restrict__ conic_c,
+                                            const float4 *__restrict__ cull)
+{
+    const int lane = threadIdx.x & 31;
+    rs.it[st][lane] = it;
+    if (it != kNoItem) {
+        cp_async16(&rs.geo[st][lane], geo + it);
+        cp_async16(&rs.col[st][lane], col + it);
+        cp_async16(&rs.cull[st][lane], cull + it);
+        cp_async4(&rs.cc[st][lane], conic_c + it);
+    }
+    cp_async_commit();
+}
+
+// The lane's staged entry of stage st (its copies must have completed).
+__device__ __forceinline__ Entry read_entry(const RawStages &rs, int st)
+{
+    const int lane = threadIdx.x & 31;
+    Entry e;
+    e.it = rs.it[st][lane];
+    if (e.it != kNoItem) {
+        e.g = rs.geo[st][lane];
+        e.c = rs.col[st][lane];
+        e.cu = rs.cull[st][lane];
+        e.cc = rs.cc[st][lane];
     } else {
         e.g = e.c = e.cu = make_float4(0.f, 0.f, 0.f, 0.f);
         e.cc = 0.f;
@@ -235,6 +305,8 @@ struct PixState {
 // state (final transmittance and last contributor), with exactly the
 // decisions of the full forward: the backward uses it when the state is not
 // stored.
+// The entries are prefetched in registers, or, with rs (the backward's replay),
+// through its asynchronous shared-memory stages.
 template <int PPT, int GL, bool COLOR = true>
 __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__restrict__ ranges,
                                            const uint32_t *__restrict__ pair_item, const float4 *__restrict__ geo,
@@ -243,7 +315,7 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
                                            float bg1, float bg2, float *__restrict__ img,
                                            float *__restrict__ alpha_out, float *__restrict__ T_final,
                                            int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval,
-                                           WarpSlots &s, PixState<PPT> *state = nullptr)
+                                           WarpSlots &s, PixState<PPT> *state = nullptr, RawStages *rs = nullptr)
 {
     static_assert(PPT == 1 || PPT % 2 == 0, "pixels per thread: 1 or even");
     constexpr int STEP = PPT == 1 ? 1 : 2;
@@ -262,25 +334,43 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
         last[k] = 0;
         evaluated[k] = rg.y - rg.x;
     }
-    // rounds of 32 entries, software-pipelined: while round r is composited,
-    // the lane's entries of rounds r + 1 and r + 2 and its index in round r + 3
-    // are in flight
+    // rounds of 32 entries, software-pipelined in registers: while round r is
+    // composited, the lane's entries of rounds r + 1 and r + 2 and its index in
+    // round r + 3 are in flight
     const int lane = threadIdx.x & 31;
     const int n_rounds = (rg.y - rg.x + 31) / 32;
-    Entry cur = gather_entry(load_index(pair_item, rg.x + lane, rg.y), geo, col, conic_c, cull);
-    Entry nxt = gather_entry(load_index(pair_item, rg.x + 32 + lane, rg.y), geo, col, conic_c, cull);
-    uint32_t it_next = load_index(pair_item, rg.x + 64 + lane, rg.y);
+    constexpr bool kAsync = !COLOR;
+    Entry cur, nxt;
+    uint32_t it_next;
+    if constexpr (kAsync) {
+#pragma unroll
+        for (int d = 0; d < kStages - 1; d++)
+            stage_entry(*rs, d, load_index(pair_item, rg.x + 32 * d + lane, rg.y), geo, col, conic_c, cull);
+        it_next = load_index(pair_item, rg.x + 32 * (kStages - 1) + lane, rg.y);
+    } else {
+        cur = gather_entry(load_index(pair_item, rg.x + lane, rg.y), geo, col, conic_c, cull);
+        nxt = gather_entry(load_index(pair_item, rg.x + 32 + lane, rg.y), geo, col, conic_c, cull);
+        it_next = load_index(pair_item, rg.x + 64 + lane, rg.y);
+    }
     for (int r = 0; r < n_rounds; r++) {
         bool all_done = true;
 #pragma unroll
         for (int k = 0; k < PPT; k++) all_done &= done[k];
         if (__all_sync(0xffffffffu, all_done)) break;
-        const uint32_t it_after = load_index(pair_item, rg.x + 32 * (r + 3) + lane, rg.y);
-        const Entry nxt2 = gather_entry(it_next, geo, col, conic_c, cull);
-        uint32_t m = commit_entry<PPT, GL>(cur, 32 * r + lane + 1, wg, s, nullptr);
-        cur = nxt;
-        nxt = nxt2;
-        it_next = it_after;
+        uint32_t m;
+        if constexpr (kAsync) {
+            stage_entry(*rs, (r + kStages - 1) % kStages, it_next, geo, col, conic_c, cull);
+            it_next = load_index(pair_item, rg.x + 32 * (r + kStages) + lane, rg.y);
+            cp_async_wait<kStages - 1>();
+            m = commit_entry<PPT, GL>(read_entry(*rs, r % kStages), 32 * r + lane + 1, wg, s, nullptr);
+        } else {
+            const uint32_t it_after = load_index(pair_item, rg.x + 32 * (r + 3) + lane, rg.y);
+            const Entry nxt2 = gather_entry(it_next, geo, col, conic_c, cull);
+            m = commit_entry<PPT, GL>(cur, 32 * r + lane + 1, wg, s, nullptr);
+            cur = nxt;
+            nxt = nxt2;
+            it_next = it_after;
+        }
         while (m) {                                    // no warp collectives inside
             const int j = __ffs(m) - 1;
             m &= m - 1;
@@ -335,6 +425,7 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
         }
         __syncwarp();                                  // slots are rewritten next round
     }
+    if constexpr (kAsync) cp_async_wait<0>();          // no copy in flight into the next user's stages
     if (state) {
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
@@ -435,7 +526,7 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
                                            float bg1, float bg2, const float *__restrict__ dimg,
                                            const float *__restrict__ dalpha, const float *__restrict__ T_final,
                                            const int32_t *__restrict__ n_contrib, float *__restrict__ gs,
-                                           WarpSlots &s, float (&acc_s)[32][kNV])
+                                           WarpSlots &s, RawStages &rs, float (&acc_s)[32][kNV])
 {
     using Gp = Groups<GL>;
     const int2 rg = ranges[wg.tile];
@@ -448,7 +539,7 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     PixState<PPT> rec;
     if (!T_final)   // recompute mode: replay the forward decisions of this region
         fwd_region<PPT, GL, false>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, nullptr,
-                                   nullptr, nullptr, nullptr, nullptr, s, &rec);
+                                   nullptr, nullptr, nullptr, nullptr, s, &rec, &rs);
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         const int py = wg.py0 + k;
@@ -484,24 +575,21 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     group_sum_layout<GL>(lane, vbase, vcnt);
     const uint32_t gmask = GL == 32 ? 0xffffffffu : (((1u << GL) - 1u) << (wg.g * GL));
     // rounds from the back: round r holds list positions [max(0, wmax - 32 (r + 1)), wmax - 32 r),
-    // software-pipelined as in the forward (entries two rounds ahead in flight)
+    // software-pipelined as in the forward
     const int n_rounds = (wmax + 31) / 32;
     auto round_lo = [&](int r) { return max(0, wmax - 32 * (r + 1)); };
     auto round_idx = [&](int r) { return rg.x + round_lo(r) + lane; };
     auto round_end = [&](int r) { return rg.x + wmax - 32 * r; };
-    Entry cur = gather_entry(n_rounds > 0 ? load_index(pair_item, round_idx(0), round_end(0)) : kNoItem, geo, col,
-                             conic_c, cull);
-    Entry nxt = gather_entry(n_rounds > 1 ? load_index(pair_item, round_idx(1), round_end(1)) : kNoItem, geo, col,
-                             conic_c, cull);
-    uint32_t it_next = n_rounds > 2 ? load_index(pair_item, round_idx(2), round_end(2)) : kNoItem;
+    auto round_item = [&](int r) { return r < n_rounds ? load_index(pair_item, round_idx(r), round_end(r)) : kNoItem; };
+#pragma unroll
+    for (int d = 0; d < kStages - 1; d++) stage_entry(rs, d, round_item(d), geo, col, conic_c, cull);
+    uint32_t it_next = round_item(kStages - 1);
     for (int r = 0; r < n_rounds; r++) {
-        const uint32_t it_after = r + 3 < n_rounds ? load_index(pair_item, round_idx(r + 3), round_end(r + 3))
-                                                   : kNoItem;
-        const Entry nxt2 = gather_entry(it_next, geo, col, conic_c, cull);
+        stage_entry(rs, (r + kStages - 1) % kStages, it_next, geo, col, conic_c, cull);
+        it_next = round_item(r + kStages);
+        cp_async_wait<kStages - 1>();
+        const Entry cur = read_entry(rs, r % kStages);
         uint32_t m = commit_entry<PPT, GL>(cur, round_lo(r) + lane + 1, wg, s, gmax);
-        cur = nxt;
-        nxt = nxt2;
-        it_next = it_after;
         const int steps = __reduce_max_sync(0xffffffffu, __popc(m));
         for (int step = 0; step < steps; step++) {   // back to front
             int j = 0;
@@ -580,6 +668,7 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
         }
         __syncwarp();
     }
+    cp_async_wait<0>();
 }
 
 // Work item of a warp: the global warp index once, or items from the queue
@@ -629,6 +718,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                  const float *__restrict__ T_final, const int32_t *__restrict__ n_contrib, float *__restrict__ gs)
 {
     __shared__ WarpSlots slots[kWarps];
+    __shared__ RawStages raw[kWarps];
     __shared__ float acc_s[kWarps][32][kNV];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSlots &s = slots[w];
@@ -642,7 +732,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         const WarpGeom wg = warp_geom<PPT, GL>(tile, q % n_regions, tw, th, TX, TY, W, H);
         if (wg.x0 > wg.x1 || wg.y0 > wg.y1) continue;
         bwd_region<PPT, GL>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, dimg, dalpha,
-                            T_final, n_contrib, gs, s, acc_s[w]);
+                            T_final, n_contrib, gs, s, raw[w], acc_s[w]);
     }
 }
 
