@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread with --tile")
     ap.add_argument("--persistent", action="store_true", help="persistent compositing kernels with --tile")
     ap.add_argument("--gl", type=int, default=32, help="lanes per compositing group with --tile (8, 16, 32)")
+    ap.add_argument("--seg", type=int, default=0,
+                    help="list segment length of the persistent backward (0 = library default, -1 = never split)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps of the batched step without timing (for ncu captures)")
     return ap.parse_args()
@@ -287,7 +289,7 @@ def main():
         (tile, ppt, gl, pers), tune_table = autotune(ftw.params, recs, V, W, H, scene_offset=w.scene_offset,
                                                       view_scene=w.view_scene)
         del ftw
-    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl)
+    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=args.seg)
     if args.profile_only:
         ftp = FineTuner(params, recs, targets, **batch, **launch)
         for _ in range(args.warmup + args.steps):

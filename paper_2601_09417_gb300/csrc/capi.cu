@@ -108,6 +108,8 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     VBM_ARG(d->pixels_per_thread == 0 || d->pixels_per_thread == 1 || d->pixels_per_thread == 2 ||
                 d->pixels_per_thread == 4,
             "pixels_per_thread must be 0, 1, 2 or 4");
+    VBM_ARG(d->segment_len == -1 || (d->segment_len >= 0 && d->segment_len <= 65536 && d->segment_len % 32 == 0),
+            "segment_len must be -1, 0 or a positive multiple of 32 up to 65536");
     VBM_ARG(d->scene_offset[0] == 0, "scene_offset[0] must be 0");
     for (int s = 0; s < d->n_scenes; s++)
         VBM_ARG(d->scene_offset[s + 1] >= d->scene_offset[s], "scene_offset must be non-decreasing");
@@ -173,6 +175,15 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->ranges, tiles);
     ALLOC(p->tile_order, tiles);
     ALLOC(p->tile_queue, kTileQueueWords);
+    if ((d->flags & VBM_PLAN_PERSISTENT) && !(d->flags & VBM_PLAN_RECOMPUTE) && d->segment_len >= 0) {
+        p->seg_len = d->segment_len ? d->segment_len : kDefaultSegmentLen;
+        const int64_t tile_px = (int64_t)d->tile_w * d->tile_h;
+        p->ckpt_cap = std::max<int64_t>(1, std::min((pairs + p->seg_len - 1) / p->seg_len,
+                                                    kCheckpointBytes / (tile_px * (int64_t)sizeof(float4))));
+        ALLOC(p->ckpt, p->ckpt_cap * tile_px);
+        ALLOC(p->ckpt_base, tiles);
+        ALLOC(p->seg_units, 2 * p->ckpt_cap);
+    }
     if (!(d->flags & VBM_PLAN_RECOMPUTE)) {
         ALLOC(p->T_final, pixels);
         ALLOC(p->n_contrib, pixels);

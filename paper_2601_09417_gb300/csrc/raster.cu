@@ -101,6 +101,7 @@ struct Groups {
 // Geometry of a work item (tile, region) for this lane.
 struct WarpGeom {
     int tile, vrel, px, py0;
+    int pit0;                   // index of the lane's first pixel inside the tile (row-major, tile_w wide)
     float pxc;
     float x0, x1, y0, y1;       // pixel-centre rectangle of the region (clipped to the image)
     float gx0[4], gy0[4];       // first pixel centre of each group's block
@@ -132,6 +133,7 @@ __device__ __forceinline__ WarpGeom warp_geom(int tile, int region, int tw, int 
     t.px = ox + (t.g % Gp::PER_ROW) * Gp::GW + k % Gp::GW;
     t.py0 = oy + ((t.g / Gp::PER_ROW) * Gp::GR + k / Gp::GW) * PPT;
     t.pxc = t.px + 0.5f;
+    t.pit0 = (t.py0 - ty * th) * tw + (t.px - tx * tw);
     t.x0 = ox + 0.5f;
     t.x1 = min(ox + kRegionCols, W) - 0.5f;
     t.y0 = oy + 0.5f;
@@ -315,7 +317,8 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
                                            float bg1, float bg2, float *__restrict__ img,
                                            float *__restrict__ alpha_out, float *__restrict__ T_final,
                                            int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval,
-                                           WarpSlots &s, PixState<PPT> *state = nullptr, RawStages *rs = nullptr)
+                                           WarpSlots &s, PixState<PPT> *state = nullptr, RawStages *rs = nullptr,
+                                           float4 *ck = nullptr, int seg_len = 0, int tw = 0, int tile_px = 0)
 {
     static_assert(PPT == 1 || PPT % 2 == 0, "pixels per thread: 1 or even");
     constexpr int STEP = PPT == 1 ? 1 : 2;
@@ -357,6 +360,15 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
 #pragma unroll
         for (int k = 0; k < PPT; k++) all_done &= done[k];
         if (__all_sync(0xffffffffu, all_done)) break;
+        if (COLOR && ck && r > 0 && (32 * r) % seg_len == 0) {
+            // segment boundary 32 r: state after the entries before it, for
+            // the pixels still compositing (the others' backward starts from
+            // their final state)
+            float4 *slot = ck + (int64_t)((32 * r) / seg_len - 1) * tile_px;
+#pragma unroll
+            for (int k = 0; k < PPT; k++)
+                if (!done[k]) slot[wg.pit0 + k * tw] = make_float4(T[k], C0[k], C1[k], C2[k]);
+        }
         uint32_t m;
         if constexpr (kAsync) {
             stage_entry(*rs, (r + kStages - 1) % kStages, it_next, geo, col, conic_c, cull);
@@ -439,6 +451,15 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         if (!inside[k]) continue;
+        if (ck) {
+            // checkpoints written for this pixel (boundaries before its last
+            // contributor): colour so far -> colour still to come
+            for (int b = seg_len; b < last[k]; b += seg_len) {
+                float4 *a = ck + (int64_t)(b / seg_len - 1) * tile_px + wg.pit0 + k * tw;
+                const float4 c = *a;
+                *a = make_float4(c.x, C0[k] - c.y, C1[k] - c.z, C2[k] - c.w);
+            }
+        }
         const int64_t pix = (int64_t)(wg.py0 + k) * W + wg.px;
         img[(v * 3 + 0) * HW + pix] = C0[k] + T[k] * bg0;
         img[(v * 3 + 1) * HW + pix] = C1[k] + T[k] * bg1;
@@ -526,10 +547,17 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
                                            float bg1, float bg2, const float *__restrict__ dimg,
                                            const float *__restrict__ dalpha, const float *__restrict__ T_final,
                                            const int32_t *__restrict__ n_contrib, float *__restrict__ gs,
-                                           WarpSlots &s, RawStages &rs, float (&acc_s)[32][kNV])
+                                           WarpSlots &s, RawStages &rs, float (&acc_s)[32][kNV], int seg = -1,
+                                           const float4 *__restrict__ ck = nullptr, int seg_len = 0, int tw = 0,
+                                           int tile_px = 0)
 {
     using Gp = Groups<GL>;
     const int2 rg = ranges[wg.tile];
+    // list positions [pa, pb) of this work unit: a segment, or the whole list
+    const int len = rg.y - rg.x;
+    const int pa = seg >= 0 ? seg * seg_len : 0;
+    const int pb = seg >= 0 ? min(pa + seg_len, len) : len;
+    const float4 *ck_end = seg >= 0 && pb < len ? ck + (int64_t)seg * tile_px : nullptr;   // boundary pb
     const int64_t HW = (int64_t)H * W;
     const int64_t v = vb + wg.vrel;
     const int lane = threadIdx.x & 31;
@@ -561,6 +589,13 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
         // plus the background and alpha-output terms: dL/dalpha_k =
         // (c_k . dL/dC) T_k - Q / (1 - alpha_k)
         Q[k] = T[k] * (bg0 * dC0[k] + bg1 * dC1[k] + bg2 * dC2[k]) - dA * T[k];
+        if (ck_end && pb < nc[k]) {
+            // the pixel still composited at pb: start from the transmittance
+            // there, with the colour still to come in Q
+            const float4 c = ck_end[wg.pit0 + k * tw];
+            T[k] = c.x;
+            Q[k] += c.y * dC0[k] + c.z * dC1[k] + c.w * dC2[k];
+        }
         my_max = max(my_max, nc[k]);
     }
     // largest contributor count of each group and of the warp
@@ -570,16 +605,16 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     int gmax[Gp::NG];
 #pragma unroll
     for (int gi = 0; gi < Gp::NG; gi++) gmax[gi] = __shfl_sync(0xffffffffu, gm, gi * GL);
-    const int wmax = __reduce_max_sync(0xffffffffu, gm);
+    const int wtop = min(pb, __reduce_max_sync(0xffffffffu, gm));   // walk positions [pa, wtop)
     int vbase, vcnt;
     group_sum_layout<GL>(lane, vbase, vcnt);
     const uint32_t gmask = GL == 32 ? 0xffffffffu : (((1u << GL) - 1u) << (wg.g * GL));
-    // rounds from the back: round r holds list positions [max(0, wmax - 32 (r + 1)), wmax - 32 r),
+    // rounds from the back: round r holds list positions [max(pa, wtop - 32 (r + 1)), wtop - 32 r),
     // software-pipelined as in the forward
-    const int n_rounds = (wmax + 31) / 32;
-    auto round_lo = [&](int r) { return max(0, wmax - 32 * (r + 1)); };
+    const int n_rounds = wtop > pa ? (wtop - pa + 31) / 32 : 0;
+    auto round_lo = [&](int r) { return max(pa, wtop - 32 * (r + 1)); };
     auto round_idx = [&](int r) { return rg.x + round_lo(r) + lane; };
-    auto round_end = [&](int r) { return rg.x + wmax - 32 * r; };
+    auto round_end = [&](int r) { return rg.x + wtop - 32 * r; };
     auto round_item = [&](int r) { return r < n_rounds ? load_index(pair_item, round_idx(r), round_end(r)) : kNoItem; };
 #pragma unroll
     for (int d = 0; d < kStages - 1; d++) stage_entry(rs, d, round_item(d), geo, col, conic_c, cull);
@@ -693,18 +728,22 @@ __global__ void __launch_bounds__(kWarps * 32)
                  const float4 *__restrict__ geo, const float4 *__restrict__ col, const float *__restrict__ conic_c,
                  const float4 *__restrict__ cull, int W, int H, int tw, int th, int TX, int TY, int vb, float bg0,
                  float bg1, float bg2, float *__restrict__ img, float *__restrict__ alpha_out,
-                 float *__restrict__ T_final, int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval)
+                 float *__restrict__ T_final, int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval,
+                 float4 *__restrict__ ckpt, const int *__restrict__ ckpt_base, int seg_len)
 {
     __shared__ WarpSlots slots[kWarps];
     WarpSlots &s = slots[threadIdx.x >> 5];
     const int w_global = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int tile_px = tw * th;
     int q;
     for (bool first = true; next_item<PERSIST>(q, w_global, n_items_w, queue, first); first = false) {
         const int tile = PERSIST ? order[q / n_regions] : q / n_regions;
         const WarpGeom wg = warp_geom<PPT, GL>(tile, q % n_regions, tw, th, TX, TY, W, H);
         if (wg.x0 > wg.x1 || wg.y0 > wg.y1) continue;            // region outside the image
+        const int cb = ckpt_base ? ckpt_base[tile] : -1;
         fwd_region<PPT, GL>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, img, alpha_out,
-                            T_final, n_contrib, n_eval, s);
+                            T_final, n_contrib, n_eval, s, nullptr, nullptr,
+                            cb >= 0 ? ckpt + (int64_t)cb * tile_px : nullptr, seg_len, tw, tile_px);
     }
 }
 
@@ -715,7 +754,9 @@ __global__ void __launch_bounds__(kWarps * 32)
                  const float4 *__restrict__ geo, const float4 *__restrict__ col, const float *__restrict__ conic_c,
                  const float4 *__restrict__ cull, int W, int H, int tw, int th, int TX, int TY, int vb, float bg0,
                  float bg1, float bg2, const float *__restrict__ dimg, const float *__restrict__ dalpha,
-                 const float *__restrict__ T_final, const int32_t *__restrict__ n_contrib, float *__restrict__ gs)
+                 const float *__restrict__ T_final, const int32_t *__restrict__ n_contrib, float *__restrict__ gs,
+                 const int *__restrict__ seg_count, const int2 *__restrict__ seg_units,
+                 const float4 *__restrict__ ckpt, const int *__restrict__ ckpt_base, int seg_len)
 {
     __shared__ WarpSlots slots[kWarps];
     __shared__ RawStages raw[kWarps];
@@ -726,13 +767,31 @@ __global__ void __launch_bounds__(kWarps * 32)
     for (int q = 0; q < kNV; q++) acc_s[w][lane][q] = 0.f;
     __syncwarp();
     const int w_global = blockIdx.x * kWarps + w;
+    const int tile_px = tw * th;
+    // work units: the segments of the segmented tiles (placed first in the
+    // order), then every other tile whole in the order's sequence
+    int n_units = 0, n_seg_tiles = 0;
+    if (seg_units) {
+        n_units = seg_count[kQSegUnits];
+        n_seg_tiles = seg_count[kQSegTiles];
+        n_items_w += (n_units - n_seg_tiles) * n_regions;
+    }
     int q;
     for (bool first = true; next_item<PERSIST>(q, w_global, n_items_w, queue, first); first = false) {
-        const int tile = PERSIST ? order[q / n_regions] : q / n_regions;
-        const WarpGeom wg = warp_geom<PPT, GL>(tile, q % n_regions, tw, th, TX, TY, W, H);
+        const int u = q / n_regions;
+        int tile, seg = -1;
+        if (u < n_units) {
+            const int2 su = seg_units[u];
+            tile = su.x;
+            seg = su.y;
+        } else {
+            tile = PERSIST ? order[u - n_units + n_seg_tiles] : u;
+        }
+        const WarpGeom wg = warp_geom<PPT, GL>(tile, q - u * n_regions, tw, th, TX, TY, W, H);
         if (wg.x0 > wg.x1 || wg.y0 > wg.y1) continue;
         bwd_region<PPT, GL>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, dimg, dalpha,
-                            T_final, n_contrib, gs, s, raw[w], acc_s[w]);
+                            T_final, n_contrib, gs, s, raw[w], acc_s[w], seg,
+                            seg >= 0 ? ckpt + (int64_t)ckpt_base[tile] * tile_px : nullptr, seg_len, tw, tile_px);
     }
 }
 
@@ -773,12 +832,13 @@ vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
             p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col,
             p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
             bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib,
-            p->prof_n_eval);
+            p->prof_n_eval, p->ckpt, p->seg_len ? p->ckpt_base : nullptr, p->seg_len);
     } else {
         k_raster_fwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
             nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col, p->conic_c,
             p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
-            bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib, p->prof_n_eval);
+            bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib, p->prof_n_eval, nullptr,
+            nullptr, 0);
     }
     VBM_LAUNCH("raster_fwd");
     record_event(p->prof_ev[1], st);
@@ -799,12 +859,13 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
         k_raster_bwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
             p->tile_order, p->tile_queue + 1, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col,
             p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
-            bg[0], bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat);
+            bg[0], bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat, p->tile_queue,
+            p->seg_len ? p->seg_units : nullptr, p->ckpt, p->ckpt_base, p->seg_len);
     } else {
         k_raster_bwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
             nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col, p->conic_c,
             p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
-            bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat);
+            bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat, nullptr, nullptr, nullptr, nullptr, 0);
     }
     VBM_LAUNCH("raster_bwd");
     record_event(p->prof_ev[3], st);

@@ -450,7 +450,17 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
 // Two grid-stride kernels over the tiles: group sizes, then placement.  Lanes
 // of a warp with the same group share one atomic.  The scratch q holds the two
 // work-queue counters (q[0], q[1]), the group sizes (q[2 + g]) and the group
-// cursors (q[34 + g]); it is zeroed before the first kernel.
+// cursors (q[34 + g]), then the list-segment counters; it is zeroed before the
+// first kernel.
+//
+// With list segments of length L (seg_len > 0), the counting kernel also
+// gives each tile whose list is longer than L ceil(len / L) - 1 checkpoint
+// slots (one per segment boundary) and ceil(len / L) backward work units
+// (tile, segment), and records the tile's first slot in ckpt_base (-1 for
+// every other tile, and for a long tile that finds no free slot, which is
+// then walked whole).  Segmented tiles are placed first in the order.  Each
+// segmented tile has at least two segments, so the units claimed never exceed
+// twice the slots claimed: seg_units holds 2 ckpt_cap entries.
 constexpr int kOrderThreads = 256;
 
 __device__ __forceinline__ int tile_group(const int2 *__restrict__ ranges, int t, int n_tiles, int lane)
@@ -460,8 +470,33 @@ __device__ __forceinline__ int tile_group(const int2 *__restrict__ ranges, int t
     return __clz(r.y - r.x + 1);                        // 31 = length 0; smaller = longer
 }
 
+// Checkpoint slots and backward units of tile t (t < n_tiles).  Returns true
+// if the tile is segmented.
+__device__ __forceinline__ bool claim_segments(const int2 *__restrict__ ranges, int t, int seg_len,
+                                               int64_t ckpt_cap, int *__restrict__ q, int *__restrict__ ckpt_base,
+                                               int2 *__restrict__ seg_units)
+{
+    const int2 r = ranges[t];
+    const int len = r.y - r.x;
+    int base = -1;
+    if (seg_len > 0 && len > seg_len) {
+        const int nseg = (len + seg_len - 1) / seg_len;
+        const int b = atomicAdd(&q[kQSegSlots], nseg - 1);
+        if ((int64_t)b + nseg - 1 <= ckpt_cap) {
+            base = b;
+            const int u = atomicAdd(&q[kQSegUnits], nseg);
+            for (int k = 0; k < nseg; k++) seg_units[u + k] = make_int2(t, k);
+            atomicAdd(&q[kQSegTiles], 1);
+        }
+    }
+    ckpt_base[t] = base;
+    return base >= 0;
+}
+
 __global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *__restrict__ ranges, int n_tiles,
-                                                                    int *__restrict__ q)
+                                                                    int *__restrict__ q, int seg_len,
+                                                                    int64_t ckpt_cap, int *__restrict__ ckpt_base,
+                                                                    int2 *__restrict__ seg_units)
 {
     __shared__ int hist[32];
     if (threadIdx.x < 32) hist[threadIdx.x] = 0;
@@ -469,7 +504,10 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * kOrderThreads;
     for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {   // uniform per block
-        const int g = tile_group(ranges, t0 + (int)threadIdx.x, n_tiles, lane);
+        const int t = t0 + (int)threadIdx.x;
+        int g = tile_group(ranges, t, n_tiles, lane);
+        if (ckpt_base && t < n_tiles && claim_segments(ranges, t, seg_len, ckpt_cap, q, ckpt_base, seg_units))
+            g = 32 + lane;                              // placed ahead of the groups
         const uint32_t peers = __match_any_sync(0xffffffffu, g);
         if (g < 32 && lane == __ffs(peers) - 1) atomicAdd(&hist[g], __popc(peers));
     }
@@ -478,7 +516,8 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *
 }
 
 __global__ void __launch_bounds__(kOrderThreads) k_tile_group_place(const int2 *__restrict__ ranges, int n_tiles,
-                                                                    int *__restrict__ q, int *__restrict__ order)
+                                                                    int *__restrict__ q, int *__restrict__ order,
+                                                                    const int *__restrict__ ckpt_base)
 {
     __shared__ int base[32];
     if (threadIdx.x < 32) {
@@ -489,7 +528,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_group_place(const int2 *
             const int y = __shfl_up_sync(0xffffffffu, incl, off);
             if ((int)threadIdx.x >= off) incl += y;
         }
-        base[threadIdx.x] = incl - c;
+        base[threadIdx.x] = incl - c + (ckpt_base ? q[kQSegTiles] : 0);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -497,7 +536,11 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_group_place(const int2 *
     const int stride = gridDim.x * kOrderThreads;
     for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {
         const int t = t0 + (int)threadIdx.x;
-        const int g = tile_group(ranges, t, n_tiles, lane);
+        int g = tile_group(ranges, t, n_tiles, lane);
+        if (ckpt_base && t < n_tiles && ckpt_base[t] >= 0) {
+            order[atomicAdd(&q[kQSegCursor], 1)] = t;
+            g = 32 + lane;
+        }
         const uint32_t peers = __match_any_sync(0xffffffffu, g);
         const int leader = __ffs(peers) - 1;
         int first = 0;
@@ -552,9 +595,11 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
         VBM_CUDA(cudaMemsetAsync(p->tile_queue, 0, kTileQueueWords * sizeof(int), st));
         const int64_t og_need = (n_tiles + kOrderThreads - 1) / kOrderThreads;
         const int og = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 2, og_need));
-        k_tile_group_count<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue);
+        k_tile_group_count<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->seg_len,
+                                                         p->ckpt_cap, p->ckpt_base, p->seg_units);
         VBM_LAUNCH("tile_group_count");
-        k_tile_group_place<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->tile_order);
+        k_tile_group_place<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->tile_order,
+                                                         p->ckpt_base);
         VBM_LAUNCH("tile_group_place");
         note_launches(2);
     }

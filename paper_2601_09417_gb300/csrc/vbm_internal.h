@@ -282,8 +282,21 @@ FilterBank make_filters(int wavelet);
 
 // ---------------------------------------------------------------- binning
 // Work-queue counters of the compositing kernels (2), tile-group sizes and
-// cursors of the longest-first order (32 + 32).
-constexpr int kTileQueueWords = 2 + 32 + 32;
+// cursors of the longest-first order (32 + 32), then the list-segment
+// counters: backward segment units, segmented tiles, claimed checkpoint
+// slots, and the placement cursor of the segmented tiles.
+constexpr int kTileQueueWords = 2 + 32 + 32 + 4;
+constexpr int kQSegUnits = 66, kQSegTiles = 67, kQSegSlots = 68, kQSegCursor = 69;
+
+// List segments (persistent plans that store the per-pixel state): a tile
+// whose list is longer than the segment length L is walked by the backward
+// as ceil(len / L) independent work units of L entries.  The forward stores,
+// per pixel of such a tile, the transmittance and the colour still to come
+// at each segment boundary (one float4 checkpoint slot of tile_w x tile_h
+// records per boundary).  Checkpoint memory is bounded; tiles that find no
+// free slot are walked whole.
+constexpr int kDefaultSegmentLen = 256;
+constexpr int64_t kCheckpointBytes = 64ll << 20;
 
 // Scratch of the binning: per-chunk sums of the tile counts and the list of
 // tiles too long for one warp's sort.
@@ -338,6 +351,11 @@ struct vbm_plan {
     int *tile_order = nullptr;               // [V * TX * TY] longest list first (persistent mode)
     int *tile_queue = nullptr;               // [kTileQueueWords]: work-queue counters (forward, backward),
                                              // then tile-group sizes and cursors of the ordering
+    int seg_len = 0;                         // list segment length L (0: lists are never split)
+    int64_t ckpt_cap = 0;                    // checkpoint slots
+    float4 *ckpt = nullptr;                  // [ckpt_cap][tile_w * tile_h] (T, colour to come) at boundaries
+    int *ckpt_base = nullptr;                // [V * TX * TY] first slot of a segmented tile, else -1
+    int2 *seg_units = nullptr;               // [2 * ckpt_cap] (tile, segment) backward work units
 
     // per pixel
     float *T_final = nullptr;

@@ -21,12 +21,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0),
-             ppt=0, persistent=False, gl=0):
+             ppt=0, persistent=False, gl=0, seg=0):
     params, cams_dev = to_device(P, cams)
     V = len(cams)
     so = [0, P.shape[1]] if scene_offset is None else scene_offset
     plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap,
-                    pixels_per_thread=ppt, flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=gl)
+                    pixels_per_thread=ppt, flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=gl,
+                    segment_len=seg)
     img = torch.zeros((V, 3, H, W), device="cuda")
     alpha = torch.zeros((V, H, W), device="cuda")
     plan.forward(params, cams_dev, img, alpha, bg=bg)
@@ -186,15 +187,22 @@ def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
     assert err.max() <= 1e-4, err.max()
 
 
-@pytest.mark.parametrize("ppt,persistent,gl", [(1, False, 32), (2, False, 32), (4, False, 32), (1, True, 32),
-                                               (1, False, 8), (1, True, 16), (2, False, 8), (4, True, 16)])
-def test_backward_matches_oracle(cuda_lib, ppt, persistent, gl):
+@pytest.mark.parametrize("ppt,persistent,gl,seg", [(1, False, 32, 0), (2, False, 32, 0), (4, False, 32, 0),
+                                                   (1, True, 32, 0), (1, False, 8, 0), (1, True, 16, 0),
+                                                   (2, False, 8, 0), (4, True, 16, 0), (1, True, 16, 32),
+                                                   (2, True, 8, 64), (4, True, 32, 32), (1, True, 32, -1)])
+def test_backward_matches_oracle(cuda_lib, ppt, persistent, gl, seg):
+    """seg > 0: tile lists longer than seg entries are walked by the backward as
+    segments starting from the forward's checkpoints; -1: never split."""
     W, H, V = 100, 76, 2
     P, cams, cams32 = scene(seed=5, n=2000, V=V, W=W, H=H)
     n = P.shape[1]
     bg = (0.05, 0.1, 0.2)
     plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, bg=bg, ppt=ppt, persistent=persistent,
-                                              gl=gl)
+                                              gl=gl, seg=seg)
+    if seg > 0:   # the split is exercised: pixels still composite past a segment boundary
+        st0 = plan_state(plan, V)
+        assert (st0["n_contrib"] > seg).any()
     st = plan_state(plan, V)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -346,3 +354,63 @@ def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl):
     assert np.array_equal(out[0][0], out[1][0])
     nrm, elt = rel_group_error(out[1][1], out[0][1])
     assert nrm < 1e-5 and elt < 1e-4, (nrm, elt)
+
+
+@pytest.mark.parametrize("ppt,gl", [(1, 16), (2, 8), (1, 32)])
+def test_segmented_backward_equals_whole_walk(cuda_lib, ppt, gl):
+    """A cluster of faint splats gives 8x8 tiles lists of several hundred entries along
+    which the pixels keep compositing.  Walking such lists as segments of 32 or 64
+    entries, each started from the forward's checkpoint (transmittance, colour still to
+    come), must leave the image unchanged bit for bit and give the gradients of the whole
+    walk up to FP32 rounding, and the oracle's (on the GPU's splats) within the bars."""
+    from vbm_inputs.gaussians import random_gaussians
+    from vbm_inputs import orbit_cameras
+    from vbm_inputs.cameras import cameras_as_float32
+    G, W, H, V, tile = 32, 96, 72, 2, (8, 8)
+    P = random_gaussians(3000, 12.0, 20.0, seed=31, scale_range=(0.3, 1.2),
+                         opacity_logit_range=(-4.5, -2.5)).astype(np.float32)
+    cams = orbit_cameras((G, G, G), V, W, H)
+    bg = (0.1, 0.05, 0.2)
+    rng = np.random.default_rng(4)
+    w = torch.from_numpy(rng.standard_normal((V, 3, H, W)).astype(np.float32)).cuda()
+    wa = torch.from_numpy(rng.standard_normal((V, H, W)).astype(np.float32)).cuda()
+    out = {}
+    for seg in (-1, 32, 64):
+        plan, params, cams_dev, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt,
+                                                      persistent=True, gl=gl, seg=seg)
+        grad = torch.zeros_like(params)
+        plan.backward(params, cams_dev, w, grad, dalpha=wa, bg=bg)
+        torch.cuda.synchronize()
+        out[seg] = (img, alpha, grad.cpu().numpy(), plan_state(plan, V))
+    st = out[32][3]
+    lengths = st["ranges"][:, 1] - st["ranges"][:, 0]
+    assert lengths.max() > 8 * 32, lengths.max()
+    assert (st["n_contrib"] > 4 * 32).any()         # pixels composite across several boundaries
+    for seg in (32, 64):
+        assert np.array_equal(out[seg][0], out[-1][0]) and np.array_equal(out[seg][1], out[-1][1])
+        for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+            nrm, elt = rel_group_error(out[seg][2][lo:hi], out[-1][2][lo:hi])
+            assert nrm < 1e-4 and elt < 1e-4, (seg, lo, nrm, elt)
+    # segmented walk against the FP64 oracle on the GPU's own splats
+    splat, color = gpu_splats_as_oracle(st)
+    ref = oraster.render(V, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32), splat, color,
+                         np.array(bg))
+    keep = ref["margin"] > 1e-5
+    wk = w.cpu().numpy().astype(np.float64) * keep[:, None]
+    wak = wa.cpu().numpy().astype(np.float64) * keep
+    plan, params, cams_dev, _, _ = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt, persistent=True,
+                                            gl=gl, seg=32)
+    grad = torch.zeros_like(params)
+    plan.backward(params, cams_dev, torch.from_numpy(wk.astype(np.float32)).cuda(), grad,
+                  dalpha=torch.from_numpy(wak.astype(np.float32)).cuda(), bg=bg)
+    torch.cuda.synchronize()
+    st = plan_state(plan, V)
+    g_ref, c_ref = oraster.render_bwd(V, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32),
+                                      splat, color, np.array(bg), wk, wak)
+    gs = st["g_splat"]
+    for k in range(6):
+        nrm, elt = rel_group_error(gs[k], g_ref[:, k])
+        assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
+    for k in range(3):
+        nrm, elt = rel_group_error(gs[6 + k], c_ref[:, k])
+        assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
