@@ -229,15 +229,16 @@ typedef struct {
     int32_t flags;
     int32_t pixels_per_thread;     /* 0 = default (2); 1, 2 or 4 */
     int32_t group_lanes;           /* 0 = default (32); 8, 16 or 32 lanes per compositing group */
-    int32_t segment_len;           /* persistent plans that store the per-pixel state: the backward
-                                      walks a tile list longer than this many entries as segments
-                                      that different warps take at once (the forward stores each
-                                      pixel's transmittance and colour still to come at every
-                                      segment boundary; at most 64 MiB of such checkpoints, tiles
-                                      beyond that are walked whole).  0 = default (256); a positive
-                                      multiple of 32 up to 65536; -1 = never split.  Ignored by
-                                      other plans.  Results equal the unsplit walk's up to FP32
-                                      rounding of the transmittance and of the colour sums. */
+    int32_t segment_len;           /* persistent plans: the backward walks a tile list longer than
+                                      this many entries as segments that different warps take at
+                                      once (the forward stores each pixel's transmittance and
+                                      colour still to come at every segment boundary, and with
+                                      VBM_PLAN_RECOMPUTE the tile's final per-pixel state; at most
+                                      64 MiB of such checkpoints, tiles beyond that are walked
+                                      whole).  0 = default (256); a positive multiple of 32 up to
+                                      65536; -1 = never split.  Ignored by other plans.  Results
+                                      equal the unsplit walk's up to FP32 rounding of the
+                                      transmittance and of the colour sums. */
 } vbm_plan_desc;
 
 /* Create a plan (allocates device memory, synchronous). */

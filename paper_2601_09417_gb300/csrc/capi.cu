@@ -175,10 +175,10 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->ranges, tiles);
     ALLOC(p->tile_order, tiles);
     ALLOC(p->tile_queue, kTileQueueWords);
-    if ((d->flags & VBM_PLAN_PERSISTENT) && !(d->flags & VBM_PLAN_RECOMPUTE) && d->segment_len >= 0) {
+    if ((d->flags & VBM_PLAN_PERSISTENT) && d->segment_len >= 0) {
         p->seg_len = d->segment_len ? d->segment_len : kDefaultSegmentLen;
         const int64_t tile_px = (int64_t)d->tile_w * d->tile_h;
-        p->ckpt_cap = std::max<int64_t>(1, std::min((pairs + p->seg_len - 1) / p->seg_len,
+        p->ckpt_cap = std::max<int64_t>(1, std::min((pairs + p->seg_len - 1) / p->seg_len * (d->flags & VBM_PLAN_RECOMPUTE ? 2 : 1),
                                                     kCheckpointBytes / (tile_px * (int64_t)sizeof(float4))));
         ALLOC(p->ckpt, p->ckpt_cap * tile_px);
         ALLOC(p->ckpt_base, tiles);

@@ -459,6 +459,11 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
                 const float4 c = *a;
                 *a = make_float4(c.x, C0[k] - c.y, C1[k] - c.z, C2[k] - c.w);
             }
+            if (!T_final) {   // no per-pixel state kept: the tile's final state after its boundaries
+                const int nseg = (rg.y - rg.x + seg_len - 1) / seg_len;
+                ck[(int64_t)(nseg - 1) * tile_px + wg.pit0 + k * tw] =
+                    make_float4(T[k], __int_as_float(last[k]), 0.f, 0.f);
+            }
         }
         const int64_t pix = (int64_t)(wg.py0 + k) * W + wg.px;
         img[(v * 3 + 0) * HW + pix] = C0[k] + T[k] * bg0;
@@ -565,7 +570,7 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     int nc[PPT];
     int my_max = 0;
     PixState<PPT> rec;
-    if (!T_final)   // recompute mode: replay the forward decisions of this region
+    if (!T_final && seg < 0)   // recompute mode, whole list: replay the forward decisions of this region
         fwd_region<PPT, GL, false>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, nullptr,
                                    nullptr, nullptr, nullptr, nullptr, s, &rec, &rs);
 #pragma unroll
@@ -578,8 +583,17 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
         float dA = 0.f;
         if (wg.px < W && py < H) {
             const int64_t pix = (int64_t)py * W + wg.px;
-            T[k] = T_final ? T_final[v * HW + pix] : rec.T[k];
-            nc[k] = T_final ? n_contrib[v * HW + pix] : rec.last[k];
+            if (T_final) {
+                T[k] = T_final[v * HW + pix];
+                nc[k] = n_contrib[v * HW + pix];
+            } else if (seg >= 0) {   // recompute mode, segmented tile: the state the forward kept for it
+                const float4 f = ck[(int64_t)((len + seg_len - 1) / seg_len - 1) * tile_px + wg.pit0 + k * tw];
+                T[k] = f.x;
+                nc[k] = __float_as_int(f.y);
+            } else {
+                T[k] = rec.T[k];
+                nc[k] = rec.last[k];
+            }
             dC0[k] = dimg[(v * 3 + 0) * HW + pix];
             dC1[k] = dimg[(v * 3 + 1) * HW + pix];
             dC2[k] = dimg[(v * 3 + 2) * HW + pix];

@@ -455,7 +455,8 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
 //
 // With list segments of length L (seg_len > 0), the counting kernel also
 // gives each tile whose list is longer than L ceil(len / L) - 1 checkpoint
-// slots (one per segment boundary) and ceil(len / L) backward work units
+// slots (one per segment boundary), plus one for its final per-pixel state
+// when the plan stores none (final_slot), and ceil(len / L) backward work units
 // (tile, segment), and records the tile's first slot in ckpt_base (-1 for
 // every other tile, and for a long tile that finds no free slot, which is
 // then walked whole).  Segmented tiles are placed first in the order.  Each
@@ -472,7 +473,7 @@ __device__ __forceinline__ int tile_group(const int2 *__restrict__ ranges, int t
 
 // Checkpoint slots and backward units of tile t (t < n_tiles).  Returns true
 // if the tile is segmented.
-__device__ __forceinline__ bool claim_segments(const int2 *__restrict__ ranges, int t, int seg_len,
+__device__ __forceinline__ bool claim_segments(const int2 *__restrict__ ranges, int t, int seg_len, int final_slot,
                                                int64_t ckpt_cap, int *__restrict__ q, int *__restrict__ ckpt_base,
                                                int2 *__restrict__ seg_units)
 {
@@ -481,8 +482,9 @@ __device__ __forceinline__ bool claim_segments(const int2 *__restrict__ ranges, 
     int base = -1;
     if (seg_len > 0 && len > seg_len) {
         const int nseg = (len + seg_len - 1) / seg_len;
-        const int b = atomicAdd(&q[kQSegSlots], nseg - 1);
-        if ((int64_t)b + nseg - 1 <= ckpt_cap) {
+        const int need = nseg - 1 + final_slot;
+        const int b = atomicAdd(&q[kQSegSlots], need);
+        if ((int64_t)b + need <= ckpt_cap) {
             base = b;
             const int u = atomicAdd(&q[kQSegUnits], nseg);
             for (int k = 0; k < nseg; k++) seg_units[u + k] = make_int2(t, k);
@@ -495,7 +497,8 @@ __device__ __forceinline__ bool claim_segments(const int2 *__restrict__ ranges, 
 
 __global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *__restrict__ ranges, int n_tiles,
                                                                     int *__restrict__ q, int seg_len,
-                                                                    int64_t ckpt_cap, int *__restrict__ ckpt_base,
+                                                                    int final_slot, int64_t ckpt_cap,
+                                                                    int *__restrict__ ckpt_base,
                                                                     int2 *__restrict__ seg_units)
 {
     __shared__ int hist[32];
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *
     for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {   // uniform per block
         const int t = t0 + (int)threadIdx.x;
         int g = tile_group(ranges, t, n_tiles, lane);
-        if (ckpt_base && t < n_tiles && claim_segments(ranges, t, seg_len, ckpt_cap, q, ckpt_base, seg_units))
+        if (ckpt_base && t < n_tiles && claim_segments(ranges, t, seg_len, final_slot, ckpt_cap, q, ckpt_base, seg_units))
             g = 32 + lane;                              // placed ahead of the groups
         const uint32_t peers = __match_any_sync(0xffffffffu, g);
         if (g < 32 && lane == __ffs(peers) - 1) atomicAdd(&hist[g], __popc(peers));
@@ -596,7 +599,8 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
         const int64_t og_need = (n_tiles + kOrderThreads - 1) / kOrderThreads;
         const int og = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 2, og_need));
         k_tile_group_count<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->seg_len,
-                                                         p->ckpt_cap, p->ckpt_base, p->seg_units);
+                                                         p->T_final ? 0 : 1, p->ckpt_cap, p->ckpt_base,
+                                                         p->seg_units);
         VBM_LAUNCH("tile_group_count");
         k_tile_group_place<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->tile_order,
                                                          p->ckpt_base);

@@ -288,12 +288,14 @@ FilterBank make_filters(int wavelet);
 constexpr int kTileQueueWords = 2 + 32 + 32 + 4;
 constexpr int kQSegUnits = 66, kQSegTiles = 67, kQSegSlots = 68, kQSegCursor = 69;
 
-// List segments (persistent plans that store the per-pixel state): a tile
-// whose list is longer than the segment length L is walked by the backward
-// as ceil(len / L) independent work units of L entries.  The forward stores,
-// per pixel of such a tile, the transmittance and the colour still to come
-// at each segment boundary (one float4 checkpoint slot of tile_w x tile_h
-// records per boundary).  Checkpoint memory is bounded; tiles that find no
+// List segments (persistent plans): a tile whose list is longer than the
+// segment length L is walked by the backward as ceil(len / L) independent
+// work units of L entries.  The forward stores, per pixel of such a tile, the
+// transmittance and the colour still to come at each segment boundary (one
+// float4 checkpoint slot of tile_w x tile_h records per boundary); plans that
+// keep no per-pixel state (recompute) also store the tile's final state
+// (transmittance, last contributor) in one more slot, so the backward replays
+// only the short lists.  Checkpoint memory is bounded; tiles that find no
 // free slot are walked whole.
 constexpr int kDefaultSegmentLen = 256;
 constexpr int64_t kCheckpointBytes = 64ll << 20;
@@ -353,7 +355,8 @@ struct vbm_plan {
                                              // then tile-group sizes and cursors of the ordering
     int seg_len = 0;                         // list segment length L (0: lists are never split)
     int64_t ckpt_cap = 0;                    // checkpoint slots
-    float4 *ckpt = nullptr;                  // [ckpt_cap][tile_w * tile_h] (T, colour to come) at boundaries
+    float4 *ckpt = nullptr;                  // [ckpt_cap][tile_w * tile_h] (T, colour to come) at boundaries,
+                                             // then (recompute plans) (T_final, last contributor bits, 0, 0)
     int *ckpt_base = nullptr;                // [V * TX * TY] first slot of a segmented tile, else -1
     int2 *seg_units = nullptr;               // [2 * ckpt_cap] (tile, segment) backward work units
 

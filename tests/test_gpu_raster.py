@@ -329,10 +329,13 @@ def test_empty_and_culled_scenes(cuda_lib):
     assert alpha.max() == 0 and np.allclose(img[0, 2], 0.75)
 
 
-@pytest.mark.parametrize("persistent,gl", [(False, 32), (True, 32), (True, 8)])
-def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl):
+@pytest.mark.parametrize("persistent,gl,seg", [(False, 32, 0), (True, 32, 0), (True, 8, 0), (True, 16, 32),
+                                              (True, 32, 64)])
+def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl, seg):
     """VBM_PLAN_RECOMPUTE keeps no per-pixel state; the backward replays the forward's
-    decisions, so images are bit-identical and gradients equal up to atomic order."""
+    decisions (for lists split into segments of seg entries, it reads the final state the
+    forward kept for those tiles only), so images are bit-identical and gradients equal
+    up to atomic order and FP32 rounding."""
     vbm = cuda_lib
     W, H, V = 96, 80, 3
     P, cams, cams32 = scene(seed=12, n=2000, V=V, W=W, H=H)
@@ -342,9 +345,12 @@ def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl):
     for flags in (0, vbm.PLAN_RECOMPUTE):
         fl = flags | (vbm.PLAN_PERSISTENT if persistent else 0)
         plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 22, flags=fl, tile_w=8, tile_h=8,
-                        pixels_per_thread=1, group_lanes=gl)
+                        pixels_per_thread=1, group_lanes=gl, segment_len=seg)
         img = torch.zeros((V, 3, H, W), device="cuda")
         plan.forward(params, cams_dev, img)
+        if seg > 0 and not flags:   # the split is exercised
+            st = plan_state(plan, V)
+            assert (st["n_contrib"] > seg).any()
         grad = torch.zeros_like(params)
         plan.backward(params, cams_dev, w, grad)
         torch.cuda.synchronize()
