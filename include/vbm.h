@@ -213,7 +213,8 @@ typedef struct vbm_plan vbm_plan;
  * ranges [scene_offset[s], scene_offset[s+1]) of one parameter array; view v
  * renders scene view_scene[v] (NULL means all views render scene 0).  Every
  * view has the same width x height.  Tiles are tile_w x tile_h pixels
- * (tile_w 8 or 16, tile_w * tile_h in {64, 128, 256}); each compositing
+ * (tile_w 8 or 16, tile_h a multiple of 4, tile_w * tile_h in {32, 64, 128,
+ * 256}); each compositing
  * thread handles pixels_per_thread pixels of one tile column (at least 32
  * threads per tile), and the threads of a warp form groups of group_lanes
  * lanes that each walk the list entries reaching their own pixel block.

@@ -27,12 +27,13 @@ import torch
 from . import vbm
 
 CANDIDATES = [(tile, ppt, gl, pers)
-              for tile in ((16, 16), (16, 8), (8, 8))
+              for tile in ((16, 16), (16, 8), (8, 8), (16, 4), (8, 4))
               for ppt in (1, 2)
               for gl in (8, 16, 32)
-              for pers in (False, True)]
+              for pers in (False, True)
+              if tile[1] % (4 * ppt) == 0]   # a warp region is 4 thread rows of ppt pixels
 DEFAULT = ((16, 16), 2, 32, False)
-CACHE_FORMAT = "v3"
+CACHE_FORMAT = "v4"
 
 
 def _cache_path():

@@ -100,8 +100,9 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     VBM_ARG(d->n_scenes == 1 || d->view_scene != nullptr, "view_scene is required with several scenes");
     VBM_ARG(d->width > 0 && d->height > 0, "image size must be positive");
     const int tp = d->tile_w * d->tile_h;
-    VBM_ARG((d->tile_w == 8 || d->tile_w == 16) && d->tile_h > 0 && (tp == 64 || tp == 128 || tp == 256),
-            "tile_w must be 8 or 16 and tile_w * tile_h 64, 128 or 256");
+    VBM_ARG((d->tile_w == 8 || d->tile_w == 16) && d->tile_h > 0 && d->tile_h % 4 == 0 &&
+                (tp == 32 || tp == 64 || tp == 128 || tp == 256),
+            "tile_w must be 8 or 16, tile_h a multiple of 4 and tile_w * tile_h 32, 64, 128 or 256");
     VBM_ARG(d->group_lanes == 0 || d->group_lanes == 8 || d->group_lanes == 16 || d->group_lanes == 32,
             "group_lanes must be 0, 8, 16 or 32");
     VBM_ARG(d->pair_capacity > 0 && d->pair_capacity < ((int64_t)1 << 31), "pair_capacity out of range");

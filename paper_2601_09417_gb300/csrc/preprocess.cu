@@ -358,7 +358,11 @@ vbm_status preprocess_bwd(vbm_plan *p, const float *params, int64_t stride, cons
     }
     if (g_end <= g_begin) return VBM_OK;
     int64_t n = g_end - g_begin;
-    k_preprocess_bwd<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+    // one-warp blocks: a thread's work (its Gaussian's views) is long and the
+    // blocks are few, so the finest granularity keeps the SMs evenly loaded
+    // (with 128-thread blocks the 8 x 512^2 workload left a second wave of 19
+    // blocks running on 19 SMs)
+    k_preprocess_bwd<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(
         params, stride, cams, p->d_scene_offset, p->desc.n_scenes, p->d_scene_view_ptr, p->d_scene_views,
         p->d_view_item_offset, vb, vc, p->last_items, p->g_splat, grad, accumulate, g_begin, g_end);
     VBM_LAUNCH("preprocess_bwd");

@@ -586,7 +586,14 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
         note_launches(1);
     }
     // 3. each tile's list sorted by (depth, item)
-    const int sw = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 8, (n_tiles + kSortWarps - 1) / kSortWarps));
+    // one wave of blocks (more would leave a partial second wave on a few SMs)
+    static int sort_per_sm = 0;
+    if (sort_per_sm == 0) {
+        VBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sort_per_sm, k_tile_sort_warp, kSortWarps * 32, 0));
+        sort_per_sm = std::max(sort_per_sm, 1);
+    }
+    const int sw = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * sort_per_sm,
+                                                               (n_tiles + kSortWarps - 1) / kSortWarps));
     k_tile_sort_warp<<<sw, kSortWarps * 32, 0, st>>>(p->ranges, n_tiles, p->pair_key, p->pair_tile, p->pair_item,
                                                      p->tile_count, b.long_tiles, b.long_count);
     VBM_LAUNCH("tile_sort_warp");

@@ -70,7 +70,7 @@ def test_preprocess_matches_oracle(cuda_lib):
     assert flagged < 0.01 * 3 * n
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (8, 4)])
 def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile):
     """Pair lists, order and ranges equal, bit for bit, the oracle's (tile, depth, index)
     sort of the GPU's rectangles and depths, with the oracle's float32 tile test on the
@@ -136,7 +136,9 @@ def test_binning_long_lists_bit_exact(cuda_lib):
                                                     ((16, 16), 1, True, 32), ((8, 8), 1, True, 32),
                                                     ((8, 8), 1, True, 8), ((8, 8), 1, False, 16),
                                                     ((16, 16), 1, False, 8), ((16, 16), 2, True, 16),
-                                                    ((16, 8), 4, False, 8), ((8, 8), 2, False, 8)])
+                                                    ((16, 8), 4, False, 8), ((8, 8), 2, False, 8),
+                                                    ((8, 4), 1, True, 16), ((8, 4), 1, False, 32),
+                                                    ((16, 4), 1, True, 8)])
 def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt, persistent, gl):
     W, H = 100, 76
     P, cams, cams32 = scene(seed=3, n=2500, V=2, W=W, H=H)
@@ -362,9 +364,9 @@ def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl, seg):
     assert nrm < 1e-5 and elt < 1e-4, (nrm, elt)
 
 
-@pytest.mark.parametrize("ppt,gl", [(1, 16), (2, 8), (1, 32)])
-def test_segmented_backward_equals_whole_walk(cuda_lib, ppt, gl):
-    """A cluster of faint splats gives 8x8 tiles lists of several hundred entries along
+@pytest.mark.parametrize("tile,ppt,gl", [((8, 8), 1, 16), ((8, 8), 2, 8), ((8, 8), 1, 32), ((8, 4), 1, 16)])
+def test_segmented_backward_equals_whole_walk(cuda_lib, tile, ppt, gl):
+    """A cluster of faint splats gives tiles lists of several hundred entries along
     which the pixels keep compositing.  Walking such lists as segments of 32 or 64
     entries, each started from the forward's checkpoint (transmittance, colour still to
     come), must leave the image unchanged bit for bit and give the gradients of the whole
@@ -372,7 +374,7 @@ def test_segmented_backward_equals_whole_walk(cuda_lib, ppt, gl):
     from vbm_inputs.gaussians import random_gaussians
     from vbm_inputs import orbit_cameras
     from vbm_inputs.cameras import cameras_as_float32
-    G, W, H, V, tile = 32, 96, 72, 2, (8, 8)
+    G, W, H, V = 32, 96, 72, 2
     P = random_gaussians(3000, 12.0, 20.0, seed=31, scale_range=(0.3, 1.2),
                          opacity_logit_range=(-4.5, -2.5)).astype(np.float32)
     cams = orbit_cameras((G, G, G), V, W, H)
