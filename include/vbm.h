@@ -234,9 +234,9 @@ typedef struct {
                                       this many entries as segments that different warps take at
                                       once (the forward stores each pixel's transmittance and
                                       colour still to come at every segment boundary, and with
-                                      VBM_PLAN_RECOMPUTE the tile's final per-pixel state; at most
-                                      64 MiB of such checkpoints, tiles beyond that are walked
-                                      whole).  0 = default (256); a positive multiple of 32 up to
+                                      VBM_PLAN_RECOMPUTE the tile's final per-pixel state; the
+                                      plan holds checkpoints for about 2 pairs per (view, Gaussian)
+                                      item, at most 1 GiB; tiles beyond that are walked whole).  0 = default (256); a positive multiple of 32 up to
                                       65536; -1 = never split.  Ignored by other plans.  Results
                                       equal the unsplit walk's up to FP32 rounding of the
                                       transmittance and of the colour sums. */

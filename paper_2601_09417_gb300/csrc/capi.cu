@@ -179,8 +179,15 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     if ((d->flags & VBM_PLAN_PERSISTENT) && d->segment_len >= 0) {
         p->seg_len = d->segment_len ? d->segment_len : kDefaultSegmentLen;
         const int64_t tile_px = (int64_t)d->tile_w * d->tile_h;
-        p->ckpt_cap = std::max<int64_t>(1, std::min((pairs + p->seg_len - 1) / p->seg_len * (d->flags & VBM_PLAN_RECOMPUTE ? 2 : 1),
-                                                    kCheckpointBytes / (tile_px * (int64_t)sizeof(float4))));
+        // boundary slots for about kCheckpointPairsPerItem pairs per item (the
+        // workloads list about two per item before fine-tuning shrinks the
+        // splats, fewer after), one final-state slot per tile in recompute
+        // plans; never more than the pair capacity can use or kCheckpointBytes
+        const bool rc = (d->flags & VBM_PLAN_RECOMPUTE) != 0;
+        const int64_t want = (kCheckpointPairsPerItem * items + p->seg_len - 1) / p->seg_len + (rc ? tiles : 0);
+        const int64_t usable = (pairs + p->seg_len - 1) / p->seg_len * (rc ? 2 : 1);
+        p->ckpt_cap = std::max<int64_t>(1, std::min({want, usable,
+                                                     kCheckpointBytes / (tile_px * (int64_t)sizeof(float4))}));
         ALLOC(p->ckpt, p->ckpt_cap * tile_px);
         ALLOC(p->ckpt_base, tiles);
         ALLOC(p->seg_units, 2 * p->ckpt_cap);

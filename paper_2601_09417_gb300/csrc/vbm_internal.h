@@ -298,7 +298,8 @@ constexpr int kQSegUnits = 66, kQSegTiles = 67, kQSegSlots = 68, kQSegCursor = 6
 // only the short lists.  Checkpoint memory is bounded; tiles that find no
 // free slot are walked whole.
 constexpr int kDefaultSegmentLen = 256;
-constexpr int64_t kCheckpointBytes = 64ll << 20;
+constexpr int64_t kCheckpointPairsPerItem = 2;
+constexpr int64_t kCheckpointBytes = 1ll << 30;
 
 // Scratch of the binning: per-chunk sums of the tile counts and the list of
 // tiles too long for one warp's sort.

@@ -29,9 +29,14 @@ def _take(vbm, ptr, shape, dtype, index):
     return t[torch.from_numpy(index).cuda()].cpu().numpy()
 
 
-def _sample_tiles(ranges, n, rng):
-    nonempty = np.nonzero(ranges[:, 1] > ranges[:, 0])[0]
-    return np.sort(rng.choice(nonempty, size=min(n, nonempty.size), replace=False))
+def _sample_tiles(ranges, n, rng, longest=4):
+    """A random sample of the non-empty tiles plus the `longest` tiles with the longest
+    lists (walked as segments by the backward of persistent plans)."""
+    lengths = ranges[:, 1] - ranges[:, 0]
+    nonempty = np.nonzero(lengths > 0)[0]
+    pick = rng.choice(nonempty, size=min(n, nonempty.size), replace=False)
+    top = np.argsort(lengths, kind="stable")[::-1][:longest]
+    return np.unique(np.concatenate([pick, top[lengths[top] > 0]]))
 
 
 @pytest.mark.parametrize("key,tile,ppt,gl,recompute", [("c2", (16, 8), 1, 16, False),
@@ -77,6 +82,8 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
     # --- sampled tiles: compact lists and the splats they reference
     rng = np.random.default_rng(7)
     sel = _sample_tiles(ranges, 48, rng)
+    if recompute:   # the sample holds lists the backward splits into segments (default 256 entries)
+        assert (ranges[sel, 1] - ranges[sel, 0]).max() > 256
     lists = [pair_item[ranges[t, 0]:ranges[t, 1]].cpu().numpy().astype(np.int64) for t in sel]
     used = np.unique(np.concatenate(lists))
     remap = {int(it): i for i, it in enumerate(used)}
