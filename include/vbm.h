@@ -301,6 +301,11 @@ typedef struct {
     const float *g_splat;     /* [n_items][12] after a backward: du dv dA dB dC dopac dr dg db, 3 unused */
     const float *cull;        /* [n_items][4]: half-widths of the alpha >= 1/255 box, B / C, B / A  */
     const float *tau;         /* [n_items]: 2 (ln(255 o) + 1e-3), bound of the binning tile test  */
+    const int32_t *seg_count; /* persistent plans, device [4]: backward units of the segmented tiles,
+                                 segmented tiles, checkpoint slots requested (may exceed
+                                 checkpoint_slots: the tiles that found none were walked whole), -;
+                                 NULL when lists are never split */
+    int64_t checkpoint_slots; /* checkpoint slots the plan holds (0 when lists are never split) */
 } vbm_plan_buffers;
 
 VBM_API vbm_status vbm_plan_get_buffers(vbm_plan *plan, vbm_plan_buffers *out);

@@ -315,6 +315,8 @@ vbm_status vbm_plan_get_buffers(vbm_plan *p, vbm_plan_buffers *o)
     o->g_splat = p->g_splat;
     o->cull = (const float *)p->cull;
     o->tau = p->tau;
+    o->seg_count = p->seg_len ? p->tile_queue + kQSegUnits : nullptr;
+    o->checkpoint_slots = p->seg_len ? p->ckpt_cap : 0;
     return VBM_OK;
 }
 

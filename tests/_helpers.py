@@ -50,6 +50,8 @@ def plan_state(plan, n_views):
     st["g_splat"] = np.ascontiguousarray(read_device(b.g_splat, (n, 12), np.float32)[:, :9].T)
     st["cull"] = read_device(b.cull, (n, 4), np.float32)
     st["tau"] = read_device(b.tau, (n,), np.float32)
+    st["seg_count"] = read_device(b.seg_count, (4,), np.int32) if b.seg_count else None
+    st["checkpoint_slots"] = int(b.checkpoint_slots)
     return st
 
 

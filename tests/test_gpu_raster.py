@@ -394,6 +394,19 @@ def test_segmented_backward_equals_whole_walk(cuda_lib, tile, ppt, gl):
     lengths = st["ranges"][:, 1] - st["ranges"][:, 0]
     assert lengths.max() > 8 * 32, lengths.max()
     assert (st["n_contrib"] > 4 * 32).any()         # pixels composite across several boundaries
+    # every list longer than 32 entries is split while the checkpoint pool (about two pairs
+    # per item) lasts; with 8x4 tiles it runs out and the remaining long tiles are walked
+    # whole: both kinds must agree with the whole walk
+    units, seg_tiles, slots_asked, _ = st["seg_count"]
+    n_long = int((lengths > 32).sum())
+    assert seg_tiles > 0 and units >= 2 * seg_tiles
+    if slots_asked > st["checkpoint_slots"]:
+        assert seg_tiles < n_long, (seg_tiles, n_long)
+    else:
+        assert seg_tiles == n_long, (seg_tiles, n_long)
+    if tile == (8, 4):
+        assert slots_asked > st["checkpoint_slots"], (slots_asked, st["checkpoint_slots"])
+    assert out[-1][3]["seg_count"] is None and out[-1][3]["checkpoint_slots"] == 0
     for seg in (32, 64):
         assert np.array_equal(out[seg][0], out[-1][0]) and np.array_equal(out[seg][1], out[-1][1])
         for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
