@@ -275,6 +275,7 @@ def main():
                  recompute=bool(cfg.get("recompute", False)))
     if args.tile:
         tile, ppt, gl, pers = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.gl, args.persistent
+        seg = args.seg
         tune_table = []
     else:
         from paper_2601_09417_gb300.autotune import autotune
@@ -286,10 +287,12 @@ def main():
         for _ in range(TUNE_WARM_STEPS):
             ftw.step_batched()
         torch.cuda.synchronize()
-        (tile, ppt, gl, pers), tune_table = autotune(ftw.params, recs, V, W, H, scene_offset=w.scene_offset,
-                                                      view_scene=w.view_scene)
+        (tile, ppt, gl, pers, seg), tune_table = autotune(ftw.params, recs, V, W, H, scene_offset=w.scene_offset,
+                                                           view_scene=w.view_scene, recompute=batch["recompute"])
         del ftw
-    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=args.seg)
+    if args.seg:
+        seg = args.seg
+    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=seg)
     if args.profile_only:
         ftp = FineTuner(params, recs, targets, **batch, **launch)
         for _ in range(args.warmup + args.steps):
@@ -444,6 +447,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
                        "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "group_lanes": gl, "persistent": pers,
+                       "segment_len": (seg if seg else 256) if pers else None,
                        "compositing_state": "recomputed in the backward" if batch["recompute"] else "stored",
                        "pairs_mean": n_pairs,
                        "form": "batched, CUDA graph, autotuned",
@@ -455,7 +459,10 @@ def main():
                          "fastest": [{"tile": "%dx%d" % tuple(r["tile"]), "ppt": r["ppt"],
                                       "group_lanes": r["group_lanes"], "persistent": r["persistent"],
                                       "ms_fwd_bwd": r["ms"], "ms_fwd_bwd_retimed": r.get("ms_final")}
-                                     for r in sorted(tune_table, key=lambda r: r.get("ms_final", r["ms"]))[:6]],
+                                     for r in sorted((r for r in tune_table if r.get("stage") != "segment"),
+                                                     key=lambda r: r.get("ms_final", r["ms"]))[:6]],
+                         "segment_len": [{"segment_len": r["segment_len"], "ms_fwd_bwd": r["ms"]}
+                                         for r in tune_table if r.get("stage") == "segment"],
                          "tuned_after_steps": TUNE_WARM_STEPS if tune_table else 0},
             "batched_over_plain": plain_ms / ms_per_step,
             "step_ms_percentiles": {"p10": float(np.percentile(step_ms, 10)),

@@ -9,7 +9,9 @@ memory per round; lanes per group sets the pixel block whose own entry list a
 lane group walks (smaller groups: fewer idle lanes, more reductions per
 pixel in the backward); persistent runs the compositing kernels as one grid
 of resident blocks taking tiles longest-list-first from a work queue instead
-of one block per tile.
+of one block per tile.  For a persistent winner a second stage times the
+per-warp list length: the number of list entries beyond which the backward
+walks a tile's list as separate segments (SEGMENT_LENGTHS; -1 never splits).
 Each candidate runs the batch's forward and backward calls on the caller's
 own Gaussians and cameras (median of a few timed repetitions, CUDA events on
 the current stream); the fastest few are then timed again, in turns, with
@@ -32,8 +34,9 @@ CANDIDATES = [(tile, ppt, gl, pers)
               for gl in (8, 16, 32)
               for pers in (False, True)
               if tile[1] % (4 * ppt) == 0]   # a warp region is 4 thread rows of ppt pixels
-DEFAULT = ((16, 16), 2, 32, False)
-CACHE_FORMAT = "v4"
+SEGMENT_LENGTHS = (64, 128, 256, 512, -1)
+DEFAULT = ((16, 16), 2, 32, False, 0)
+CACHE_FORMAT = "v5"
 
 
 def _cache_path():
@@ -55,11 +58,13 @@ class _Trial:
     """A plan and buffers for one candidate; times forward + backward calls of the batch."""
 
     def __init__(self, params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent,
-                 pair_capacity):
+                 pair_capacity, segment_len=0, recompute=False):
         self.params, self.cams = params, cams_dev
         self.plan = vbm.Plan(scene_offset, n_views, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1],
                              pair_capacity=pair_capacity, pixels_per_thread=ppt,
-                             flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=gl)
+                             flags=(vbm.PLAN_PERSISTENT if persistent else 0) |
+                             (vbm.PLAN_RECOMPUTE if recompute else 0), group_lanes=gl,
+                             segment_len=segment_len)
         self.img = torch.zeros((n_views, 3, H, W), device=params.device)
         self.dimg = torch.full_like(self.img, 1e-6)
         self.grad = torch.zeros_like(params)
@@ -83,18 +88,22 @@ class _Trial:
 
 
 def time_config(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent, pair_capacity,
-                iters=5):
+                iters=5, recompute=False):
     """Median ms of one forward + backward call of the whole batch with this configuration."""
-    t = _Trial(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent, pair_capacity)
+    t = _Trial(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent, pair_capacity,
+               recompute=recompute)
     times = t.run(iters + 2)[2:]
     ok, need = t.close()
     return (float(np.median(times)) if ok else float("inf")), need
 
 
-def retime(params, cams_dev, n_views, W, H, scene_offset, view_scene, configs, pair_capacity, rounds=8, iters=3):
-    """Median ms of each configuration, timed in turns (rounds x iters calls each) so that
-    clock or thermal drift affects them alike."""
-    trials = [_Trial(params, cams_dev, n_views, W, H, scene_offset, view_scene, *c, pair_capacity) for c in configs]
+def retime(params, cams_dev, n_views, W, H, scene_offset, view_scene, configs, pair_capacity, rounds=8, iters=3,
+           recompute=False):
+    """Median ms of each configuration (tile, ppt, group lanes, persistent[, segment length]),
+    timed in turns (rounds x iters calls each) so that clock or thermal drift affects them
+    alike."""
+    trials = [_Trial(params, cams_dev, n_views, W, H, scene_offset, view_scene, *c[:4], pair_capacity, *c[4:],
+                     recompute=recompute) for c in configs]
     for t in trials:
         t.run(2)
     times = [[] for _ in trials]
@@ -109,13 +118,15 @@ def retime(params, cams_dev, n_views, W, H, scene_offset, view_scene, configs, p
 
 
 def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=None, pair_capacity=None,
-             candidates=None, use_cache=True):
-    """Best ((tile_w, tile_h), ppt, group_lanes, persistent) for this workload, plus the table of timings."""
+             candidates=None, use_cache=True, recompute=False):
+    """Best ((tile_w, tile_h), ppt, group_lanes, persistent, segment_len) for this workload, plus the
+    table of timings (segment_len 0: the library's default; only persistent plans split lists).
+    recompute: time plans that keep no per-pixel state (VBM_PLAN_RECOMPUTE), as the caller will run."""
     n = int(params.shape[1] if scene_offset is None else scene_offset[-1])
     so = [0, n] if scene_offset is None else list(scene_offset)
     raw = np.ascontiguousarray(cam_records).view(np.uint8).tobytes()
     dev = torch.cuda.get_device_name(params.device)
-    key = "%s|%s|%s" % (CACHE_FORMAT, dev, _signature(params, n, raw, W, H, so, view_scene))
+    key = "%s|%s|%s|%d" % (CACHE_FORMAT, dev, _signature(params, n, raw, W, H, so, view_scene), int(recompute))
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -126,27 +137,38 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
             cache = {}
     if use_cache and key in cache:
         ent = cache[key]
-        return (tuple(ent["tile"]), ent["ppt"], ent["group_lanes"], ent["persistent"]), ent["table"]
+        return (tuple(ent["tile"]), ent["ppt"], ent["group_lanes"], ent["persistent"], ent["segment_len"]), \
+            ent["table"]
     cams_dev = vbm.cameras_to_device(cam_records, params.device)
     cap = pair_capacity if pair_capacity is not None else vbm.default_pair_capacity(
         vbm.batch_items(so, n_views, view_scene))
     cap = min(cap, vbm.MAX_PAIR_CAPACITY)
     table = []
     for tile, ppt, gl, persistent in (candidates or CANDIDATES):
-        ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, gl, persistent, cap)
+        ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, gl, persistent, cap,
+                               recompute=recompute)
         table.append({"tile": list(tile), "ppt": ppt, "group_lanes": gl, "persistent": persistent, "ms": ms,
                       "pairs_needed": need})
     # the fastest few again, in turns and with more repetitions
     top = sorted(range(len(table)), key=lambda k: table[k]["ms"])[:4]
     finals = retime(params, cams_dev, n_views, W, H, so, view_scene,
                     [(tuple(table[k]["tile"]), table[k]["ppt"], table[k]["group_lanes"], table[k]["persistent"])
-                     for k in top], cap)
+                     for k in top], cap, recompute=recompute)
     for k, ms in zip(top, finals):
         table[k]["ms_final"] = ms
     best = table[top[int(np.argmin(finals))]]
+    seg = 0
+    if best["persistent"]:
+        segs = retime(params, cams_dev, n_views, W, H, so, view_scene,
+                      [(tuple(best["tile"]), best["ppt"], best["group_lanes"], True, s) for s in SEGMENT_LENGTHS], cap,
+                      recompute=recompute)
+        for s_len, ms in zip(SEGMENT_LENGTHS, segs):
+            table.append({"tile": best["tile"], "ppt": best["ppt"], "group_lanes": best["group_lanes"],
+                          "persistent": True, "segment_len": s_len, "ms": ms, "ms_final": ms, "stage": "segment"})
+        seg = SEGMENT_LENGTHS[int(np.argmin(segs))]
     if use_cache:
         cache[key] = {"tile": best["tile"], "ppt": best["ppt"], "group_lanes": best["group_lanes"],
-                      "persistent": best["persistent"], "table": table}
+                      "persistent": best["persistent"], "segment_len": seg, "table": table}
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             tmp = path + ".%d.tmp" % os.getpid()
@@ -155,4 +177,4 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
             os.replace(tmp, path)
         except OSError:
             pass
-    return (tuple(best["tile"]), best["ppt"], best["group_lanes"], best["persistent"]), table
+    return (tuple(best["tile"]), best["ppt"], best["group_lanes"], best["persistent"], seg), table

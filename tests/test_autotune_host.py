@@ -1,0 +1,36 @@
+"""Host logic of the autotuner, without a GPU: the candidate list and the configuration
+tuples handed to the timing trials (segment length last, pair capacity in its place)."""
+
+import pytest
+
+pytest.importorskip("torch")
+
+from paper_2601_09417_gb300 import autotune as at
+
+
+def test_candidates_respect_region_rows():
+    assert len(at.CANDIDATES) == len(set(at.CANDIDATES))
+    for tile, ppt, gl, pers in at.CANDIDATES:
+        assert tile[1] % (4 * ppt) == 0 and gl in (8, 16, 32)
+    assert -1 in at.SEGMENT_LENGTHS and all(s == -1 or s % 32 == 0 for s in at.SEGMENT_LENGTHS)
+
+
+def test_retime_passes_segment_length_and_capacity(monkeypatch):
+    made = []
+
+    class Trial:
+        def __init__(self, params, cams, n_views, W, H, so, vs, tile, ppt, gl, persistent, cap, segment_len=0,
+                     recompute=False):
+            made.append((tile, ppt, gl, persistent, cap, segment_len, recompute))
+
+        def run(self, iters):
+            return [1.0 + len(made)] * iters
+
+        def close(self):
+            return True, 0
+
+    monkeypatch.setattr(at, "_Trial", Trial)
+    out = at.retime(None, None, 2, 8, 8, [0, 1], None,
+                    [((8, 8), 1, 16, True), ((16, 8), 2, 8, True, 128)], 12345, rounds=2, iters=1, recompute=True)
+    assert made == [((8, 8), 1, 16, True, 12345, 0, True), ((16, 8), 2, 8, True, 12345, 128, True)]
+    assert len(out) == 2
