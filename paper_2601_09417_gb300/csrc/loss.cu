@@ -13,8 +13,9 @@
 // or a column segment (vertical) held in registers, so each staged value is
 // read from shared memory once per pass; the moment pairs (x, y), (x^2, y^2)
 // and the map pair (g1, g2) are accumulated with packed FP32x2 FMAs.
-// A final one-block kernel adds the per-block sums in double in a fixed order,
-// so the loss value is deterministic.
+// The first block of pass 2 adds pass 1's per-block sums in double in a fixed
+// order (they are complete when pass 2 starts), so the loss value is
+// deterministic and needs no launch of its own.
 #include <cmath>
 
 #include "vbm_internal.h"
@@ -200,11 +201,43 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
     }
 }
 
+// L = scale ((1 - lambda) sum |x - y| + lambda (n_elem - sum SSIM)) from the
+// per-block sums of pass 1, in a fixed order; one block, all threads.
+__device__ __forceinline__ void loss_total(const double *__restrict__ partial, int64_t blocks, double n_elem,
+                                           double lambda, double scale, double *__restrict__ loss, int accumulate)
+{
+    __shared__ double red[2][kLossThreads];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < blocks; i += kLossThreads) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int off = kLossThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < (unsigned)off) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + off];
+            red[1][threadIdx.x] += red[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double L = scale * ((1.0 - lambda) * red[0][0] + lambda * (n_elem - red[1][0]));
+        *loss = accumulate ? *loss + L : L;
+    }
+}
+
 __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y,
                                                           int H, int W, const float2 *__restrict__ g12,
                                                           const float *__restrict__ g3, float lambda, float scale,
-                                                          float *__restrict__ dx)
+                                                          float *__restrict__ dx, const double *__restrict__ partial,
+                                                          double n_elem, double scale_d, double *__restrict__ loss,
+                                                          int accumulate)
 {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)   // block-uniform
+        loss_total(partial, (int64_t)gridDim.x * gridDim.y * gridDim.z, n_elem, (double)lambda, scale_d, loss,
+                   accumulate);
     __shared__ __align__(16) float2 s12[kSH][kSWP];   // (g1, g2) with halo
     __shared__ float s3[kSH][kSWP];                   // g3 with halo
     __shared__ __align__(16) float2 h12[kSH][kHP];
@@ -283,31 +316,6 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
     }
 }
 
-__global__ void k_loss_final(const double *__restrict__ partial, int64_t blocks, double n_elem, double lambda,
-                             double scale, double *__restrict__ loss, int accumulate)
-{
-    __shared__ double red[2][256];
-    double a = 0.0, b = 0.0;
-    for (int64_t i = threadIdx.x; i < blocks; i += blockDim.x) {
-        a += partial[2 * i];
-        b += partial[2 * i + 1];
-    }
-    red[0][threadIdx.x] = a;
-    red[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < (unsigned)off) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + off];
-            red[1][threadIdx.x] += red[1][threadIdx.x + off];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double L = scale * ((1.0 - lambda) * red[0][0] + lambda * (n_elem - red[1][0]));
-        *loss = accumulate ? *loss + L : L;
-    }
-}
-
 bool g_win_ready = false;
 
 vbm_status ensure_window()
@@ -355,12 +363,10 @@ vbm_status loss_fwd_bwd(const float *img, const float *target, int n_images, int
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, n_images * 3);
     k_ssim_fwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g12, g3, partial);
     VBM_LAUNCH("ssim_fwd");
-    k_ssim_bwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g12, g3, lambda, (float)scale, dimg);
+    k_ssim_bwd<<<grid, kLossThreads, 0, st>>>(img, target, H, W, g12, g3, lambda, (float)scale, dimg, partial,
+                                              (double)n, scale, loss, accumulate);
     VBM_LAUNCH("ssim_bwd");
-    k_loss_final<<<1, 256, 0, st>>>(partial, (int64_t)grid.x * grid.y * grid.z, (double)n, (double)lambda, scale,
-                                    loss, accumulate);
-    VBM_LAUNCH("loss_final");
-    note_launches(3);
+    note_launches(2);
     return VBM_OK;
 }
 

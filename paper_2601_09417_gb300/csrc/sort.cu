@@ -35,12 +35,66 @@ constexpr int kScanItems = 16;                        // tiles per thread of a s
 constexpr int kTilesPerChunk = kScanThreads * kScanItems;
 constexpr uint64_t kPadKey = ~0ull;
 
+// Longest-list-first order of the tiles for the persistent compositing
+// kernels: tiles are grouped by floor(log2(length + 1)), longest group first
+// (order within a group is arbitrary; each tile is processed independently).
+// The scan that produces the ranges also counts the groups, and the warp sort
+// places each tile into the order before it sorts; lanes of a warp with the
+// same group share one atomic.  The words q hold the two work-queue counters
+// (q[0], q[1]), the group sizes (q[2 + g]) and the group cursors (q[34 + g]),
+// then the list-segment counters; the first scan kernel zeroes them.
+//
+// With list segments of length L (seg_len > 0), the scan also gives each tile
+// whose list is longer than L ceil(len / L) - 1 checkpoint slots (one per
+// segment boundary), plus one for its final per-pixel state when the plan
+// stores none (final_slot), and ceil(len / L) backward work units (tile,
+// segment), and records the tile's first slot in ckpt_base (-1 for every other
+// tile, and for a long tile that finds no free slot, which is then walked
+// whole).  Segmented tiles are placed first in the order.  Each segmented tile
+// has at least two segments, so the units claimed never exceed twice the slots
+// claimed: seg_units holds 2 ckpt_cap entries.
+struct TileOrder {
+    int *q;              // queue words (NULL: no ordering, non-persistent plans)
+    int *order;          // [tiles]
+    int seg_len;         // 0: lists are never split
+    int final_slot;      // 1 in plans that keep no per-pixel state
+    int64_t ckpt_cap;
+    int *ckpt_base;      // [tiles] (NULL when seg_len is 0)
+    int2 *seg_units;     // [2 ckpt_cap]
+};
+
+__device__ __forceinline__ int length_group(int len) { return __clz(len + 1); }   // 31 = length 0; smaller = longer
+
+// Checkpoint slots and backward units of tile t with a list of len entries.
+// Returns true if the tile is segmented.
+__device__ __forceinline__ bool claim_segments(int len, int t, const TileOrder &o)
+{
+    int base = -1;
+    if (o.seg_len > 0 && len > o.seg_len) {
+        const int nseg = (len + o.seg_len - 1) / o.seg_len;
+        const int need = nseg - 1 + o.final_slot;
+        const int b = atomicAdd(&o.q[kQSegSlots], need);
+        if ((int64_t)b + need <= o.ckpt_cap) {
+            base = b;
+            const int u = atomicAdd(&o.q[kQSegUnits], nseg);
+            for (int k = 0; k < nseg; k++) o.seg_units[u + k] = make_int2(t, k);
+            atomicAdd(&o.q[kQSegTiles], 1);
+        }
+    }
+    o.ckpt_base[t] = base;
+    return base >= 0;
+}
+
 // ------------------------------------------------------------ tile ranges
 
 // Sum of the tile counts of each chunk of kTilesPerChunk tiles.
+// Also zeroes the queue words of the tile order (q, if not NULL).
 __global__ void __launch_bounds__(kScanThreads) k_tile_chunk_sums(const uint32_t *__restrict__ tile_count,
-                                                                  int64_t n_tiles, int64_t *__restrict__ chunk_sums)
+                                                                  int64_t n_tiles, int64_t *__restrict__ chunk_sums,
+                                                                  int *__restrict__ q)
 {
+    if (q && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < kTileQueueWords; i += kScanThreads) q[i] = 0;
     __shared__ int64_t warp_sums[kScanThreads / 32];
     const int64_t beg = (int64_t)blockIdx.x * kTilesPerChunk;
     int64_t s = 0;
@@ -66,17 +120,20 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_chunk_sums(const uint32_t
 // chunks before its own and of all chunks.  If the total exceeds the capacity
 // every range is empty, the pair count is 0, the counters are cleared and the
 // status records the size needed.  Also resets the long-list queue of the
-// sort.
+// sort and, with an ordering (o.q), counts the tiles of each length group and
+// claims the list segments.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict__ tile_count, int64_t n_tiles,
                                                             const int64_t *__restrict__ chunk_sums, int chunks,
                                                             int64_t capacity, int2 *__restrict__ ranges,
                                                             int64_t *__restrict__ n_pairs,
                                                             int64_t *__restrict__ status,
-                                                            uint32_t *__restrict__ long_count)
+                                                            uint32_t *__restrict__ long_count, TileOrder o)
 {
     __shared__ int64_t red[2][kScanThreads / 32];
     __shared__ int64_t warp_off[kScanThreads / 32];
+    __shared__ int hist[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
     int64_t before = 0, total = 0;
     for (int c = threadIdx.x; c < chunks; c += kScanThreads) {
         const int64_t v = chunk_sums[c];
@@ -139,6 +196,23 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict
         }
         run += c[it];
     }
+    if (!o.q) return;                                          // block-uniform
+    // length groups of this thread's tiles (segmented tiles are placed ahead
+    // of the groups), one shared atomic per group among a warp's lanes
+#pragma unroll
+    for (int it = 0; it < kScanItems; it++) {
+        const int64_t t = t0 + it;
+        const int len = overflow ? 0 : (int)c[it];
+        int g = 32 + lane;                                      // no group: unique per lane
+        if (t < n_tiles) {
+            g = length_group(len);
+            if (o.ckpt_base && claim_segments(len, (int)t, o)) g = 32 + lane;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, g);
+        if (g < 32 && lane == __ffs(peers) - 1) atomicAdd(&hist[g], __popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&o.q[2 + threadIdx.x], hist[threadIdx.x]);
 }
 
 // ---------------------------------------------------------- placement
@@ -315,17 +389,52 @@ constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
 // One warp per tile (grid-stride over the tiles): lists of up to 32 keys are
 // sorted in registers, up to kWarpSortMax by the warp's merge sort; longer
 // ones are queued for k_tile_sort_block.  Also clears every tile's counter
-// for the next call.
+// for the next call and, with an ordering (o.q), first places every tile into
+// the longest-first order (the scan has counted the groups).
 __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *__restrict__ ranges, int64_t n_tiles,
                                                                     const uint64_t *__restrict__ pair_key,
                                                                     uint32_t *__restrict__ pair_tile,
                                                                     uint32_t *__restrict__ pair_item,
                                                                     uint32_t *__restrict__ tile_count,
                                                                     uint32_t *__restrict__ long_tiles,
-                                                                    uint32_t *__restrict__ long_count)
+                                                                    uint32_t *__restrict__ long_count, TileOrder o)
 {
     __shared__ uint64_t buf[kSortWarps][2][kWarpBufWords];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (o.q) {                                                  // grid-uniform
+        __shared__ int base[32];
+        if (threadIdx.x < 32) {
+            const int cnt = o.q[2 + threadIdx.x];
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if ((int)threadIdx.x >= off) incl += y;
+            }
+            base[threadIdx.x] = incl - cnt + (o.ckpt_base ? o.q[kQSegTiles] : 0);
+        }
+        __syncthreads();
+        const uint32_t lt_mask = (1u << lane) - 1u;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n_tiles; t0 += stride) {   // uniform per block
+            const int64_t t = t0 + threadIdx.x;
+            int g = 32 + lane;
+            if (t < n_tiles) {
+                const int2 r = ranges[t];
+                g = length_group(r.y - r.x);
+                if (o.ckpt_base && o.ckpt_base[t] >= 0) {
+                    o.order[atomicAdd(&o.q[kQSegCursor], 1)] = (int)t;
+                    g = 32 + lane;
+                }
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, g);
+            const int leader = __ffs(peers) - 1;
+            int first = 0;
+            if (g < 32 && lane == leader) first = atomicAdd(&o.q[34 + g], __popc(peers));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            if (g < 32) o.order[base[g] + first + __popc(peers & lt_mask)] = (int)t;
+        }
+    }
     const int64_t warps = (int64_t)gridDim.x * kSortWarps;
     for (int64_t t = (int64_t)blockIdx.x * kSortWarps + w; t < n_tiles; t += warps) {
         const int2 r = ranges[t];
@@ -444,115 +553,6 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
     }
 }
 
-// Longest-list-first order of the tiles for the persistent compositing
-// kernels: tiles are grouped by floor(log2(length + 1)), longest group first
-// (order within a group is arbitrary; each tile is processed independently).
-// Two grid-stride kernels over the tiles: group sizes, then placement.  Lanes
-// of a warp with the same group share one atomic.  The scratch q holds the two
-// work-queue counters (q[0], q[1]), the group sizes (q[2 + g]) and the group
-// cursors (q[34 + g]), then the list-segment counters; it is zeroed before the
-// first kernel.
-//
-// With list segments of length L (seg_len > 0), the counting kernel also
-// gives each tile whose list is longer than L ceil(len / L) - 1 checkpoint
-// slots (one per segment boundary), plus one for its final per-pixel state
-// when the plan stores none (final_slot), and ceil(len / L) backward work units
-// (tile, segment), and records the tile's first slot in ckpt_base (-1 for
-// every other tile, and for a long tile that finds no free slot, which is
-// then walked whole).  Segmented tiles are placed first in the order.  Each
-// segmented tile has at least two segments, so the units claimed never exceed
-// twice the slots claimed: seg_units holds 2 ckpt_cap entries.
-constexpr int kOrderThreads = 256;
-
-__device__ __forceinline__ int tile_group(const int2 *__restrict__ ranges, int t, int n_tiles, int lane)
-{
-    if (t >= n_tiles) return 32 + lane;                 // no group: unique per lane
-    const int2 r = ranges[t];
-    return __clz(r.y - r.x + 1);                        // 31 = length 0; smaller = longer
-}
-
-// Checkpoint slots and backward units of tile t (t < n_tiles).  Returns true
-// if the tile is segmented.
-__device__ __forceinline__ bool claim_segments(const int2 *__restrict__ ranges, int t, int seg_len, int final_slot,
-                                               int64_t ckpt_cap, int *__restrict__ q, int *__restrict__ ckpt_base,
-                                               int2 *__restrict__ seg_units)
-{
-    const int2 r = ranges[t];
-    const int len = r.y - r.x;
-    int base = -1;
-    if (seg_len > 0 && len > seg_len) {
-        const int nseg = (len + seg_len - 1) / seg_len;
-        const int need = nseg - 1 + final_slot;
-        const int b = atomicAdd(&q[kQSegSlots], need);
-        if ((int64_t)b + need <= ckpt_cap) {
-            base = b;
-            const int u = atomicAdd(&q[kQSegUnits], nseg);
-            for (int k = 0; k < nseg; k++) seg_units[u + k] = make_int2(t, k);
-            atomicAdd(&q[kQSegTiles], 1);
-        }
-    }
-    ckpt_base[t] = base;
-    return base >= 0;
-}
-
-__global__ void __launch_bounds__(kOrderThreads) k_tile_group_count(const int2 *__restrict__ ranges, int n_tiles,
-                                                                    int *__restrict__ q, int seg_len,
-                                                                    int final_slot, int64_t ckpt_cap,
-                                                                    int *__restrict__ ckpt_base,
-                                                                    int2 *__restrict__ seg_units)
-{
-    __shared__ int hist[32];
-    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * kOrderThreads;
-    for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {   // uniform per block
-        const int t = t0 + (int)threadIdx.x;
-        int g = tile_group(ranges, t, n_tiles, lane);
-        if (ckpt_base && t < n_tiles && claim_segments(ranges, t, seg_len, final_slot, ckpt_cap, q, ckpt_base, seg_units))
-            g = 32 + lane;                              // placed ahead of the groups
-        const uint32_t peers = __match_any_sync(0xffffffffu, g);
-        if (g < 32 && lane == __ffs(peers) - 1) atomicAdd(&hist[g], __popc(peers));
-    }
-    __syncthreads();
-    if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&q[2 + threadIdx.x], hist[threadIdx.x]);
-}
-
-__global__ void __launch_bounds__(kOrderThreads) k_tile_group_place(const int2 *__restrict__ ranges, int n_tiles,
-                                                                    int *__restrict__ q, int *__restrict__ order,
-                                                                    const int *__restrict__ ckpt_base)
-{
-    __shared__ int base[32];
-    if (threadIdx.x < 32) {
-        const int c = q[2 + threadIdx.x];
-        int incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if ((int)threadIdx.x >= off) incl += y;
-        }
-        base[threadIdx.x] = incl - c + (ckpt_base ? q[kQSegTiles] : 0);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const int stride = gridDim.x * kOrderThreads;
-    for (int t0 = blockIdx.x * kOrderThreads; t0 < n_tiles; t0 += stride) {
-        const int t = t0 + (int)threadIdx.x;
-        int g = tile_group(ranges, t, n_tiles, lane);
-        if (ckpt_base && t < n_tiles && ckpt_base[t] >= 0) {
-            order[atomicAdd(&q[kQSegCursor], 1)] = t;
-            g = 32 + lane;
-        }
-        const uint32_t peers = __match_any_sync(0xffffffffu, g);
-        const int leader = __ffs(peers) - 1;
-        int first = 0;
-        if (g < 32 && lane == leader) first = atomicAdd(&q[34 + g], __popc(peers));
-        first = __shfl_sync(0xffffffffu, first, leader);
-        if (g < 32) order[base[g] + first + __popc(peers & lt_mask)] = t;
-    }
-}
-
 }  // namespace
 
 int bin_chunks(int64_t n_tiles) { return (int)std::max<int64_t>(1, (n_tiles + kTilesPerChunk - 1) / kTilesPerChunk); }
@@ -568,11 +568,21 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     const BinScratch &b = p->bin_scratch;
     const int chunks = bin_chunks(n_tiles);
     // 1. ranges from the per-tile counts of the projection
-    k_tile_chunk_sums<<<chunks, kScanThreads, 0, st>>>(p->tile_count, n_tiles, b.chunk_sums);
+    TileOrder o{};
+    if (p->desc.flags & VBM_PLAN_PERSISTENT) {
+        o.q = p->tile_queue;
+        o.order = p->tile_order;
+        o.seg_len = p->seg_len;
+        o.final_slot = p->T_final ? 0 : 1;
+        o.ckpt_cap = p->ckpt_cap;
+        o.ckpt_base = p->seg_len ? p->ckpt_base : nullptr;
+        o.seg_units = p->seg_units;
+    }
+    k_tile_chunk_sums<<<chunks, kScanThreads, 0, st>>>(p->tile_count, n_tiles, b.chunk_sums, o.q);
     VBM_LAUNCH("tile_chunk_sums");
     k_tile_scan<<<chunks, kScanThreads, 0, st>>>(p->tile_count, n_tiles, b.chunk_sums, chunks,
                                                  p->desc.pair_capacity, p->ranges, p->d_n_pairs, p->d_status,
-                                                 b.long_count);
+                                                 b.long_count, o);
     VBM_LAUNCH("tile_scan");
     note_launches(2);
     // 2. every item's key into a slot of each listed tile
@@ -595,25 +605,12 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     const int sw = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * sort_per_sm,
                                                                (n_tiles + kSortWarps - 1) / kSortWarps));
     k_tile_sort_warp<<<sw, kSortWarps * 32, 0, st>>>(p->ranges, n_tiles, p->pair_key, p->pair_tile, p->pair_item,
-                                                     p->tile_count, b.long_tiles, b.long_count);
+                                                     p->tile_count, b.long_tiles, b.long_count, o);
     VBM_LAUNCH("tile_sort_warp");
     k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
         p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);
     VBM_LAUNCH("tile_sort_block");
     note_launches(2);
-    if (p->desc.flags & VBM_PLAN_PERSISTENT) {
-        VBM_CUDA(cudaMemsetAsync(p->tile_queue, 0, kTileQueueWords * sizeof(int), st));
-        const int64_t og_need = (n_tiles + kOrderThreads - 1) / kOrderThreads;
-        const int og = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 2, og_need));
-        k_tile_group_count<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->seg_len,
-                                                         p->T_final ? 0 : 1, p->ckpt_cap, p->ckpt_base,
-                                                         p->seg_units);
-        VBM_LAUNCH("tile_group_count");
-        k_tile_group_place<<<og, kOrderThreads, 0, st>>>(p->ranges, (int)n_tiles, p->tile_queue, p->tile_order,
-                                                         p->ckpt_base);
-        VBM_LAUNCH("tile_group_place");
-        note_launches(2);
-    }
     return VBM_OK;
 }
 
