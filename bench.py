@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread with --tile")
     ap.add_argument("--persistent", action="store_true", help="persistent compositing kernels with --tile")
     ap.add_argument("--gl", type=int, default=32, help="lanes per compositing group with --tile (8, 16, 32)")
+    ap.add_argument("--radix", action="store_true",
+                    help="order the pairs by device radix sorts (items by depth, pairs by tile)")
     ap.add_argument("--seg", type=int, default=0,
                     help="list segment length of the persistent backward (0 = library default, -1 = never split)")
     ap.add_argument("--profile-only", action="store_true",
@@ -292,7 +294,7 @@ def main():
         del ftw
     if args.seg:
         seg = args.seg
-    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=seg)
+    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=seg, radix_sort=args.radix)
     if args.profile_only:
         ftp = FineTuner(params, recs, targets, **batch, **launch)
         for _ in range(args.warmup + args.steps):
@@ -448,6 +450,7 @@ def main():
             "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
                        "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "group_lanes": gl, "persistent": pers,
                        "segment_len": (seg if seg else 256) if pers else None,
+                       "pair_order": "device radix sorts" if args.radix else "bucketed per-tile sort",
                        "compositing_state": "recomputed in the backward" if batch["recompute"] else "stored",
                        "pairs_mean": n_pairs,
                        "form": "batched, CUDA graph, autotuned",

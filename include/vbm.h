@@ -208,6 +208,12 @@ typedef struct vbm_plan vbm_plan;
 #define VBM_PLAN_RECOMPUTE 1   /* keep no per-pixel state; backward recomputes it */
 #define VBM_PLAN_PERSISTENT 2  /* compositing kernels run as one persistent grid pulling tiles,
                                   longest list first, from a work queue */
+#define VBM_PLAN_RADIX_SORT 4  /* order the pairs with device radix sorts instead of the bucketed
+                                  per-tile sort: the items are sorted by depth (stable LSD radix
+                                  sort on the 32 depth bits), their pairs emitted in that order and
+                                  sorted stably by tile (LSD radix sort on ceil(log2 tiles) bits),
+                                  which is the sort on (tile | depth) keys with ties in item order;
+                                  the lists are identical bit for bit */
 
 /* Batch description.  Scenes are independent Gaussian sets stored as column
  * ranges [scene_offset[s], scene_offset[s+1]) of one parameter array; view v

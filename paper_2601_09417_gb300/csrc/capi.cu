@@ -192,6 +192,20 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
         ALLOC(p->ckpt_base, tiles);
         ALLOC(p->seg_units, 2 * p->ckpt_cap);
     }
+    if (d->flags & VBM_PLAN_RADIX_SORT) {
+        p->radix_blocks = radix_blocks();
+        p->scan_blocks = scan_blocks();
+        ALLOC(p->touched, items);
+        for (int k = 0; k < 2; k++) {
+            ALLOC(p->item_key[k], items);
+            ALLOC(p->item_val[k], items);
+        }
+        ALLOC(p->item_offset, items + 1);
+        ALLOC(p->d_n_items, 1);
+        ALLOC(p->radix_hist, radix_hist_words(p->radix_blocks));
+        ALLOC(p->radix_total, 256);
+        ALLOC(p->scan_sums, p->scan_blocks + 1);
+    }
     if (!(d->flags & VBM_PLAN_RECOMPUTE)) {
         ALLOC(p->T_final, pixels);
         ALLOC(p->n_contrib, pixels);

@@ -120,7 +120,8 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                                  int W, int H, float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
                                  float4 *__restrict__ cull, float *__restrict__ tau_out, float *__restrict__ depth,
                                  int4 *__restrict__ rect, int32_t *__restrict__ radius,
-                                 uint32_t *__restrict__ listed, uint32_t *__restrict__ tile_count)
+                                 uint32_t *__restrict__ listed, uint32_t *__restrict__ tile_count,
+                                 uint32_t *__restrict__ touched)
 {
     const int v = vb + blockIdx.y;
     const int scene = view_scene ? view_scene[v] : 0;
@@ -192,10 +193,12 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     // tiles of the rectangle that pass the exact tile test (the image size is
     // the plan's, as in the pair placement, so both take the same decisions),
     // counted per tile and recorded per item for the placement
+    uint32_t n_listed = 0;
     const uint32_t word = listed_tiles(has_tiles, tt, tw, th, W, H, tile_count,
-                                       (uint32_t)(v - vb) * (uint32_t)(TX * TY), TX);
+                                       (uint32_t)(v - vb) * (uint32_t)(TX * TY), TX, &n_listed);
     if (!valid) return;
     listed[item] = word;
+    if (touched) touched[item] = n_listed;   // pairs of the item (radix-sort ordering)
 }
 
 // Chain rule from the per-item splat gradient (du, dv, dA, dB, dC, dopacity,
@@ -339,7 +342,7 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
                                               p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
                                               p->desc.tile_h, p->desc.width, p->desc.height, p->geo, p->col,
                                               p->conic_c, p->cull, p->tau, p->depth, p->rect, p->radius,
-                                              p->listed, p->tile_count);
+                                              p->listed, p->tile_count, p->touched);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);
     return VBM_OK;

@@ -390,14 +390,16 @@ constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
 // sorted in registers, up to kWarpSortMax by the warp's merge sort; longer
 // ones are queued for k_tile_sort_block.  Also clears every tile's counter
 // for the next call and, with an ordering (o.q), first places every tile into
-// the longest-first order (the scan has counted the groups).
+// the longest-first order (the scan has counted the groups).  With sort = 0
+// (radix-sort ordering) it only clears the counters and places the tiles.
 __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *__restrict__ ranges, int64_t n_tiles,
                                                                     const uint64_t *__restrict__ pair_key,
                                                                     uint32_t *__restrict__ pair_tile,
                                                                     uint32_t *__restrict__ pair_item,
                                                                     uint32_t *__restrict__ tile_count,
                                                                     uint32_t *__restrict__ long_tiles,
-                                                                    uint32_t *__restrict__ long_count, TileOrder o)
+                                                                    uint32_t *__restrict__ long_count, TileOrder o,
+                                                                    int sort)
 {
     __shared__ uint64_t buf[kSortWarps][2][kWarpBufWords];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *
         const int2 r = ranges[t];
         const int n = r.y - r.x;
         if (lane == 0) tile_count[t] = 0u;
-        if (n == 0) continue;
+        if (n == 0 || !sort) continue;                          // radix ordering: counters only
         const uint64_t *keys = pair_key + r.x;
         if (n > kWarpSortMax) {
             if (lane == 0) long_tiles[atomicAdd(long_count, 1u)] = (uint32_t)t;
@@ -553,9 +555,463 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
     }
 }
 
+// ------------------------------------------------- radix-sort ordering
+//
+// VBM_PLAN_RADIX_SORT orders the pairs the way 3D Gaussian Splatting does,
+// by a device-wide sort on (tile | depth) keys, split into two stable LSD
+// radix sorts on 32-bit keys: the items by their depth bits (ties keep the
+// item order), then the pairs, emitted in that depth order, by their tile id
+// (ceil(log2 tiles) bits).  Stability carries the (depth, item) order into
+// every tile's list, so the lists equal the bucketed per-tile sort's bit for
+// bit.  Each radix pass is reduce-then-scan on a fixed grid (per-block digit
+// histograms, one block per digit for the offsets, a stable scatter), reading
+// the element count from device memory; no block waits on another.
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixItems = 8;                       // elements per thread per tile
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+
+__device__ __forceinline__ int64_t radix_chunk(int64_t n, int blocks)
+{
+    const int64_t c = (n + blocks - 1) / blocks;
+    return (c + kRadixTile - 1) / kRadixTile * kRadixTile;
+}
+
+// Per-block digit histogram of the block's chunk: hist[d * blocks + b], and
+// the per-digit totals over all blocks (digit_total, zeroed before).  Equal
+// digits within a warp share one shared-memory atomic.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                                 const int64_t *__restrict__ d_n, int shift,
+                                                                 uint32_t *__restrict__ hist,
+                                                                 uint32_t *__restrict__ digit_total)
+{
+    __shared__ uint32_t h[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t n = *d_n;
+    const int64_t chunk = radix_chunk(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = beg; b < end; b += kRadixTile) {       // uniform trip count across the block
+        uint32_t d[kRadixItems];
+#pragma unroll
+        for (int it = 0; it < kRadixItems; it++) {
+            const int64_t i = b + it * kRadixThreads + threadIdx.x;
+            d[it] = i < end ? (keys[i] >> shift) & (kRadix - 1) : (uint32_t)(kRadix + lane);
+        }
+#pragma unroll
+        for (int it = 0; it < kRadixItems; it++) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
+            if (d[it] < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d[it]], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+        hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+        if (h[d]) atomicAdd(&digit_total[d], h[d]);
+    }
+}
+
+// Exclusive scan of one value per thread over the block; the total goes to
+// *total if not NULL.  Ends with a barrier.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sums, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        if (lane < nw) warp_sums[lane] = wi - w;
+        if (lane == 31 && total) *total = wi;
+    }
+    __syncthreads();
+    const uint32_t r = warp_sums[warp] + incl - x;
+    __syncthreads();
+    return r;
+}
+
+// Digit-major exclusive offsets, one block per digit d: base(d) = the totals
+// of the smaller digits, then a scan of digit d's per-block counts.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(uint32_t *__restrict__ hist,
+                                                                 const uint32_t *__restrict__ digit_total,
+                                                                 int blocks)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t s_base, chunk_total;
+    const int d = blockIdx.x;
+    uint32_t lower = 0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) lower += digit_total[i];
+    (void)block_exclusive_scan(lower, warp_sums, &s_base);
+    uint32_t carry = s_base;
+    __syncthreads();
+    uint32_t *h = hist + (int64_t)d * blocks;
+    for (int b0 = 0; b0 < blocks; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t x = b < blocks ? h[b] : 0u;
+        const uint32_t ex = block_exclusive_scan(x, warp_sums, &chunk_total);
+        if (b < blocks) h[b] = carry + ex;
+        __syncthreads();
+        carry += chunk_total;
+        __syncthreads();
+    }
+}
+
+// Stable scatter of the block's chunk, one tile of kRadixTile elements at a
+// time: within a tile each warp ranks its elements among equal digits
+// (earlier iterations of the warp + earlier lanes, from __match_any_sync), the
+// tile is exchanged through shared memory into digit order, and written out
+// with consecutive threads on consecutive elements of each digit's run.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
+                                                                   const uint32_t *__restrict__ vals_in,
+                                                                   uint32_t *__restrict__ keys_out,
+                                                                   uint32_t *__restrict__ vals_out,
+                                                                   const int64_t *__restrict__ d_n, int shift,
+                                                                   const uint32_t *__restrict__ hist)
+{
+    static_assert(kRadixThreads == kRadix, "one thread per digit in the per-tile digit scans");
+    __shared__ uint32_t run[kRadix];        // global position of the next element of each digit
+    __shared__ uint32_t tstart[kRadix];     // first position of each digit in the exchanged tile
+    __shared__ uint32_t wcnt[kRadixWarps][kRadix];
+    __shared__ uint32_t s_key[kRadixTile];
+    __shared__ uint32_t s_val[kRadixTile];
+    __shared__ uint32_t warp_sums[32];
+    const int64_t n = *d_n;
+    const int64_t chunk = radix_chunk(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    if (beg >= end) return;                 // uniform across the block
+    const int t = threadIdx.x;
+    run[t] = hist[(int64_t)t * gridDim.x + blockIdx.x];
+    const int warp = t >> 5, lane = t & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int64_t tbase = beg; tbase < end; tbase += kRadixTile) {
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; w++) wcnt[w][t] = 0;
+        __syncthreads();
+        uint32_t k[kRadixItems], v[kRadixItems], rank[kRadixItems];
+        const int64_t wbase = tbase + (int64_t)warp * 32 * kRadixItems;
+#pragma unroll
+        for (int it = 0; it < kRadixItems; it++) {
+            const int64_t i = wbase + it * 32 + lane;
+            const bool valid = i < end;
+            k[it] = valid ? keys_in[i] : 0u;
+            v[it] = valid ? vals_in[i] : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kRadixItems; it++) {
+            const int64_t i = wbase + it * 32 + lane;
+            const bool valid = i < end;
+            const uint32_t d = valid ? (k[it] >> shift) & (kRadix - 1) : (uint32_t)(kRadix + lane);
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t prior = valid ? wcnt[warp][d] : 0u;
+            rank[it] = prior + __popc(peers & lt_mask);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = prior + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // thread t = digit t: exclusive offsets over the warps, then over the digits
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; w++) {
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = tot;
+            tot += c;
+        }
+        tstart[t] = block_exclusive_scan(tot, warp_sums, nullptr);
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kRadixItems; it++) {
+            const int64_t i = wbase + it * 32 + lane;
+            if (i < end) {
+                const uint32_t d = (k[it] >> shift) & (kRadix - 1);
+                const uint32_t lpos = tstart[d] + wcnt[warp][d] + rank[it];
+                s_key[lpos] = k[it];
+                s_val[lpos] = v[it];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)kRadixTile, end - tbase);
+        for (int i = t; i < cnt; i += kRadixThreads) {
+            const uint32_t key = s_key[i];
+            const uint32_t d = (key >> shift) & (kRadix - 1);
+            const uint32_t pos = run[d] + (uint32_t)i - tstart[d];
+            keys_out[pos] = key;
+            vals_out[pos] = s_val[i];
+        }
+        __syncthreads();
+        run[t] += tot;
+        __syncthreads();
+    }
+}
+
+// Item count of the call into a device scalar, and each item's depth key
+// (float bits: depth > 0 for every item with tiles, so the bits order like the
+// depths; items without tiles sort last) with the item index as value.
+__global__ void k_item_keys(int64_t n, const float *__restrict__ depth, const uint32_t *__restrict__ touched,
+                            uint32_t *__restrict__ key, uint32_t *__restrict__ val, int64_t *__restrict__ d_n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *d_n = n;
+    if (i >= n) return;
+    key[i] = touched[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
+    val[i] = (uint32_t)i;
+}
+
+// Exclusive scan of touched[] in the depth order (out[s] = first pair of
+// item idx[s], out[n] = the total): per-block sums, one block scanning them,
+// then the per-block scans.
+constexpr int kGatherItems = 4;
+
+__device__ __forceinline__ int64_t gather_chunk(int64_t n, int blocks)
+{
+    const int64_t t = kScanThreads * kGatherItems;
+    const int64_t c = (n + blocks - 1) / blocks;
+    return (c + t - 1) / t * t;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_gather_reduce(const uint32_t *__restrict__ counts,
+                                                                const uint32_t *__restrict__ idx, int64_t n,
+                                                                int64_t *__restrict__ block_sums)
+{
+    __shared__ int64_t red[kScanThreads];
+    const int64_t chunk = gather_chunk(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    int64_t s = 0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) s += counts[idx[i]];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < (unsigned)off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+}
+
+// Exclusive scan of the per-block sums (blocks <= 1024) in one block; total at [blocks].
+__global__ void __launch_bounds__(1024) k_gather_top(int64_t *__restrict__ block_sums, int blocks)
+{
+    __shared__ int64_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t x = (int)threadIdx.x < blocks ? block_sums[threadIdx.x] : 0;
+    int64_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t w = warp_sums[lane];
+        int64_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        warp_sums[lane] = wi - w;
+        if (lane == 31) block_sums[blocks] = wi;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < blocks) block_sums[threadIdx.x] = warp_sums[warp] + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_gather_down(const uint32_t *__restrict__ counts,
+                                                              const uint32_t *__restrict__ idx, int64_t n,
+                                                              const int64_t *__restrict__ block_sums,
+                                                              int64_t *__restrict__ out)
+{
+    __shared__ int64_t warp_sums[kScanThreads / 32];
+    __shared__ int64_t carry;
+    const int64_t chunk = gather_chunk(n, gridDim.x);
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, beg + chunk);
+    if (threadIdx.x == 0) carry = block_sums[blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t tb = beg; tb < end; tb += kScanThreads * kGatherItems) {
+        int64_t v[kGatherItems];
+        int64_t local = 0;
+#pragma unroll
+        for (int it = 0; it < kGatherItems; it++) {
+            const int64_t i = tb + (int64_t)threadIdx.x * kGatherItems + it;
+            v[it] = i < end ? (int64_t)counts[idx[i]] : 0;
+            local += v[it];
+        }
+        int64_t incl = local;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        int64_t wpre = 0, tot = 0;
+        for (int w = 0; w < kScanThreads / 32; w++) {
+            if (w < warp) wpre += warp_sums[w];
+            tot += warp_sums[w];
+        }
+        int64_t r = carry + wpre + incl - local;
+#pragma unroll
+        for (int it = 0; it < kGatherItems; it++) {
+            const int64_t i = tb + (int64_t)threadIdx.x * kGatherItems + it;
+            if (i < end) out[i] = r;
+            r += v[it];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = block_sums[gridDim.x];
+}
+
+// Pairs of the items in depth order: item idx[s] owns [offsets[s],
+// offsets[s + 1]).  Nothing is emitted when the total exceeds the capacity
+// (the tile scan has already reported it).
+__global__ void k_emit_pairs(const uint32_t *__restrict__ idx, const int64_t *__restrict__ offsets, int64_t n,
+                             const uint32_t *__restrict__ listed, const int4 *__restrict__ rect,
+                             const float4 *__restrict__ geo, const float *__restrict__ conic_c,
+                             const float4 *__restrict__ cull, const float *__restrict__ tau,
+                             const int64_t *__restrict__ view_item_offset, int vb, int vc, int TX, int TY, int tw,
+                             int th, int W, int H, int64_t capacity, uint32_t *__restrict__ pair_tile,
+                             uint32_t *__restrict__ pair_item)
+{
+    if (offsets[n] > capacity) return;
+    const int64_t base_item = view_item_offset[vb];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: emit_listed needs every lane of the warp
+    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += stride) {
+        const int64_t s = s0 + threadIdx.x;
+        uint32_t word = 0, item = 0, tile0 = 0;
+        int64_t beg = 0;
+        TileTest t = {};
+        if (s < n && offsets[s + 1] != offsets[s]) {
+            beg = offsets[s];
+            item = idx[s];
+            word = listed[item];
+            int lo = 0, hi = vc - 1;   // view of the item: last v with offset <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (view_item_offset[vb + mid] - base_item <= (int64_t)item) lo = mid; else hi = mid - 1;
+            }
+            const float4 g = geo[item], cu = cull[item];
+            t = TileTest{g.x, g.y, g.z, g.w, conic_c[item], cu.z, cu.w, tau[item], rect[item]};
+            tile0 = (uint32_t)lo * (uint32_t)(TX * TY);
+        }
+        emit_listed(word, t, tile0, item, beg, TX, tw, th, W, H, pair_tile, pair_item);
+    }
+}
+
+int ceil_log2(int64_t x)
+{
+    int b = 0;
+    while ((int64_t(1) << b) < x) b++;
+    return b;
+}
+
 }  // namespace
 
 int bin_chunks(int64_t n_tiles) { return (int)std::max<int64_t>(1, (n_tiles + kTilesPerChunk - 1) / kTilesPerChunk); }
+
+int radix_blocks() { return num_sms() * 4; }
+int scan_blocks() { return std::min(1024, num_sms() * 4); }
+size_t radix_hist_words(int blocks) { return (size_t)kRadix * blocks + kRadix; }
+
+namespace {
+
+// Stable LSD radix sort of (keys, vals) on their low `bits` key bits, 8 bits
+// a pass, between the two buffers; returns the buffer holding the result.
+// The grid is fixed by n_max (graph capture); the count is read from d_n.
+vbm_status radix_sort(uint32_t *keys[2], uint32_t *vals[2], const int64_t *d_n, int64_t n_max, int bits,
+                      const vbm_plan *p, int *result, cudaStream_t st)
+{
+    int cur = 0;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->radix_blocks,
+                                                                   (n_max + kRadixTile - 1) / kRadixTile));
+    for (int shift = 0; shift < bits; shift += kRadixBits) {
+        VBM_CUDA(cudaMemsetAsync(p->radix_total, 0, kRadix * sizeof(uint32_t), st));
+        k_radix_upsweep<<<blocks, kRadixThreads, 0, st>>>(keys[cur], d_n, shift, p->radix_hist, p->radix_total);
+        VBM_LAUNCH("radix_upsweep");
+        k_radix_offsets<<<kRadix, kRadixThreads, 0, st>>>(p->radix_hist, p->radix_total, blocks);
+        VBM_LAUNCH("radix_offsets");
+        k_radix_downsweep<<<blocks, kRadixThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], d_n,
+                                                            shift, p->radix_hist);
+        VBM_LAUNCH("radix_downsweep");
+        note_launches(3);
+        cur = 1 - cur;
+    }
+    *result = cur;
+    return VBM_OK;
+}
+
+// Radix-sort ordering of the pairs (VBM_PLAN_RADIX_SORT): the items by depth,
+// their pairs emitted in that order, then the pairs stably by tile.  The
+// ranges come from the tile scan (the same counts); the result lands in
+// pair_tile / pair_item, with the bucketed path's key buffer as the second
+// buffer of the pair sort.
+vbm_status radix_order(vbm_plan *p, int vb, int vc, int64_t n_tiles, cudaStream_t st)
+{
+    const int64_t n_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
+    if (n_items == 0) return VBM_OK;
+    k_item_keys<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(n_items, p->depth, p->touched, p->item_key[0],
+                                                                    p->item_val[0], p->d_n_items);
+    VBM_LAUNCH("item_keys");
+    note_launches(1);
+    int a = 0;
+    vbm_status s = radix_sort(p->item_key, p->item_val, p->d_n_items, n_items, 32, p, &a, st);
+    if (s != VBM_OK) return s;
+    k_gather_reduce<<<p->scan_blocks, kScanThreads, 0, st>>>(p->touched, p->item_val[a], n_items, p->scan_sums);
+    VBM_LAUNCH("gather_reduce");
+    k_gather_top<<<1, 1024, 0, st>>>(p->scan_sums, p->scan_blocks);
+    VBM_LAUNCH("gather_top");
+    k_gather_down<<<p->scan_blocks, kScanThreads, 0, st>>>(p->touched, p->item_val[a], n_items, p->scan_sums,
+                                                            p->item_offset);
+    VBM_LAUNCH("gather_down");
+    note_launches(3);
+    // emit into the buffer from which an even number of tile passes ends in pair_tile / pair_item
+    const int64_t cap = p->desc.pair_capacity;
+    uint32_t *tiles[2] = {p->pair_tile, reinterpret_cast<uint32_t *>(p->pair_key)};
+    uint32_t *items[2] = {p->pair_item, reinterpret_cast<uint32_t *>(p->pair_key) + cap};
+    const int tile_bits = ceil_log2(n_tiles);
+    const int passes = (tile_bits + kRadixBits - 1) / kRadixBits;
+    const int first = passes & 1;
+    k_emit_pairs<<<num_sms() * 4, 256, 0, st>>>(p->item_val[a], p->item_offset, n_items, p->listed, p->rect, p->geo,
+                                                 p->conic_c, p->cull, p->tau, p->d_view_item_offset, vb, vc, p->TX,
+                                                 p->TY, p->desc.tile_w, p->desc.tile_h, p->desc.width, p->desc.height,
+                                                 cap, tiles[first], items[first]);
+    VBM_LAUNCH("emit_pairs");
+    note_launches(1);
+    uint32_t *tk[2] = {tiles[first], tiles[1 - first]};
+    uint32_t *tv[2] = {items[first], items[1 - first]};
+    int r = 0;
+    s = radix_sort(tk, tv, p->d_n_pairs, cap, tile_bits, p, &r, st);
+    if (s != VBM_OK) return s;
+    if (tk[r] != p->pair_tile) {   // cannot happen: the emission buffer was chosen for this
+        set_error("radix ordering ended in the scratch buffer");
+        return VBM_ERR_CUDA;
+    }
+    return VBM_OK;
+}
+
+}  // namespace
 
 cudaError_t binning_setup()
 {
@@ -585,8 +1041,13 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
                                                  b.long_count, o);
     VBM_LAUNCH("tile_scan");
     note_launches(2);
+    const bool radix = (p->desc.flags & VBM_PLAN_RADIX_SORT) != 0;
+    if (radix) {
+        vbm_status s = radix_order(p, vb, vc, n_tiles, st);
+        if (s != VBM_OK) return s;
+    }
     // 2. every item's key into a slot of each listed tile
-    if (p->max_scene > 0) {
+    if (!radix && p->max_scene > 0) {
         dim3 grid((unsigned)((p->max_scene + 255) / 256), (unsigned)vc);
         k_place_pairs<<<grid, 256, 0, st>>>(p->d_scene_offset, p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
                                             p->d_view_item_offset, vb, p->listed, p->rect, p->geo, p->conic_c,
@@ -605,12 +1066,15 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     const int sw = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * sort_per_sm,
                                                                (n_tiles + kSortWarps - 1) / kSortWarps));
     k_tile_sort_warp<<<sw, kSortWarps * 32, 0, st>>>(p->ranges, n_tiles, p->pair_key, p->pair_tile, p->pair_item,
-                                                     p->tile_count, b.long_tiles, b.long_count, o);
+                                                     p->tile_count, b.long_tiles, b.long_count, o, radix ? 0 : 1);
     VBM_LAUNCH("tile_sort_warp");
-    k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
-        p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);
-    VBM_LAUNCH("tile_sort_block");
-    note_launches(2);
+    note_launches(1);
+    if (!radix) {
+        k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
+            p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);
+        VBM_LAUNCH("tile_sort_block");
+        note_launches(1);
+    }
     return VBM_OK;
 }
 

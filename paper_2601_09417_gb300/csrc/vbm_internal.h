@@ -126,7 +126,8 @@ __device__ __forceinline__ int2 rect_pos(int k, int cols, float inv_cols, int ar
 constexpr uint32_t kWideRect = 1u << 31;
 
 __device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, int tw, int th, int W, int H,
-                                                 uint32_t *__restrict__ tile_count, uint32_t tile0, int TX)
+                                                 uint32_t *__restrict__ tile_count, uint32_t tile0, int TX,
+                                                 uint32_t *n_listed = nullptr)
 {
     const int cols = t.rc.z - t.rc.x;
     const int area = valid ? cols * (t.rc.w - t.rc.y) : 0;
@@ -160,16 +161,18 @@ __device__ __forceinline__ uint32_t listed_tiles(bool valid, const TileTest &t, 
         const int b_cols = b.rc.z - b.rc.x;
         const int a = b_cols * (b.rc.w - b.rc.y);
         const float inv_cols = 1.0f / (float)b_cols;
-        bool any = false;
+        uint32_t cnt = 0;
         for (int k0 = 0; k0 < a; k0 += 32) {
             const int k = k0 + lane;
             const int2 pos = rect_pos(k, b_cols, inv_cols, a);
             const bool ok = k < a && listed_at(b, pos.x, pos.y, tw, th, W, H);
             if (ok) atomicAdd(&tile_count[tile_id_at(b, pos.x, pos.y, b_tile0, TX)], 1u);
-            any |= __any_sync(0xffffffffu, ok);
+            cnt += __popc(__ballot_sync(0xffffffffu, ok));
         }
-        if (lane == src && any) word = kWideRect;
+        if (lane == src && cnt) word = kWideRect;
+        if (lane == src && n_listed) *n_listed = cnt;
     }
+    if (n_listed && !(word & kWideRect)) *n_listed = __popc(word);
     return word;
 }
 
@@ -233,6 +236,56 @@ __device__ __forceinline__ void place_listed(uint32_t word, const TileTest &t, u
                 const int64_t slot = (int64_t)atomicSub(&tile_count[id], 1u) - 1;
                 if (slot >= 0 && slot < n_total) pair_key[slot] = b_key;
             }
+        }
+    }
+}
+
+// Pair emission in a given order (radix-sort ordering): the lane's item owns
+// pair slots [beg, beg + its listed-tile count) and writes one (tile, item)
+// pair per listed tile of its rectangle, row-major (a wide rectangle's tiles
+// are tested again, by the whole warp, with the same code).  All 32 lanes must
+// call it; word = 0 for a lane without an item.
+__device__ __forceinline__ void emit_listed(uint32_t word, const TileTest &t, uint32_t tile0, uint32_t item,
+                                            int64_t beg, int TX, int tw, int th, int W, int H,
+                                            uint32_t *__restrict__ pair_tile, uint32_t *__restrict__ pair_item)
+{
+    const int lane = threadIdx.x & 31;
+    if (word && !(word & kWideRect)) {
+        const int cols = t.rc.z - t.rc.x;
+        int64_t o = beg;
+        int col = 0, row = 0;
+        for (int k = 0; k < kSerialTiles; k++) {
+            if ((word >> k) & 1u) {
+                pair_tile[o] = tile_id_at(t, col, row, tile0, TX);
+                pair_item[o] = item;
+                o++;
+            }
+            if (++col == cols) {
+                col = 0;
+                row++;
+            }
+        }
+    }
+    for (uint32_t big = __ballot_sync(0xffffffffu, (word & kWideRect) != 0); big; big &= big - 1) {
+        const int src = __ffs(big) - 1;
+        const TileTest b = shfl_test(t, src);
+        const uint32_t b_tile0 = __shfl_sync(0xffffffffu, tile0, src);
+        const uint32_t b_item = __shfl_sync(0xffffffffu, item, src);
+        int64_t run = (int64_t)__shfl_sync(0xffffffffu, (long long)beg, src);
+        const int b_cols = b.rc.z - b.rc.x;
+        const int a = b_cols * (b.rc.w - b.rc.y);
+        const float inv_cols = 1.0f / (float)b_cols;
+        for (int k0 = 0; k0 < a; k0 += 32) {
+            const int k = k0 + lane;
+            const int2 pos = rect_pos(k, b_cols, inv_cols, a);
+            const bool ok = k < a && listed_at(b, pos.x, pos.y, tw, th, W, H);
+            const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int64_t o = run + __popc(bal & ((1u << lane) - 1u));
+                pair_tile[o] = tile_id_at(b, pos.x, pos.y, b_tile0, TX);
+                pair_item[o] = b_item;
+            }
+            run += __popc(bal);
         }
     }
 }
@@ -311,6 +364,9 @@ struct BinScratch {
 };
 int bin_chunks(int64_t n_tiles);
 cudaError_t binning_setup();   // once per plan, before any capture: kernel attributes
+int radix_blocks();            // blocks of the radix-sort kernels
+int scan_blocks();             // blocks of the item scan (<= 1024)
+size_t radix_hist_words(int blocks);
 
 }  // namespace vbm
 
@@ -360,6 +416,17 @@ struct vbm_plan {
                                              // then (recompute plans) (T_final, last contributor bits, 0, 0)
     int *ckpt_base = nullptr;                // [V * TX * TY] first slot of a segmented tile, else -1
     int2 *seg_units = nullptr;               // [2 * ckpt_cap] (tile, segment) backward work units
+
+    // radix-sort ordering (VBM_PLAN_RADIX_SORT)
+    uint32_t *touched = nullptr;             // [items] listed tiles per item
+    uint32_t *item_key[2] = {nullptr, nullptr};   // [items] depth bits, double buffer
+    uint32_t *item_val[2] = {nullptr, nullptr};   // [items] item index, double buffer
+    int64_t *item_offset = nullptr;          // [items + 1] first pair of each item in depth order
+    int64_t *d_n_items = nullptr;            // items of the call (device scalar)
+    uint32_t *radix_hist = nullptr;          // [256 * radix_blocks + 256]
+    uint32_t *radix_total = nullptr;         // [256]
+    int64_t *scan_sums = nullptr;            // [scan_blocks + 1]
+    int radix_blocks = 0, scan_blocks = 0;
 
     // per pixel
     float *T_final = nullptr;

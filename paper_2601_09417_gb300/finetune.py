@@ -26,7 +26,7 @@ def default_lrs(extent):
 class FineTuner:
     def __init__(self, params, cam_records, targets, scene_offset=None, view_scene=None, tile=(16, 16), ppt=0,
                  persistent=False, pair_capacity=None, lrs=None, lam=0.2, bg=(0.0, 0.0, 0.0), extent=None,
-                 device="cuda", group_lanes=0, recompute=False, segment_len=0):
+                 device="cuda", group_lanes=0, recompute=False, segment_len=0, radix_sort=False):
         self.device = torch.device(device)
         self.params = params
         self.n = params.shape[1] if scene_offset is None else int(scene_offset[-1])
@@ -44,7 +44,8 @@ class FineTuner:
         self.plan = vbm.Plan(self.scene_offset, self.V, self.W, self.H, view_scene=view_scene, tile_w=tile[0],
                              tile_h=tile[1], pair_capacity=min(pair_capacity, vbm.MAX_PAIR_CAPACITY), pixels_per_thread=ppt,
                              flags=(vbm.PLAN_PERSISTENT if persistent else 0) |
-                             (vbm.PLAN_RECOMPUTE if recompute else 0), group_lanes=group_lanes,
+                             (vbm.PLAN_RECOMPUTE if recompute else 0) |
+                             (vbm.PLAN_RADIX_SORT if radix_sort else 0), group_lanes=group_lanes,
                              segment_len=segment_len)
         self.img = torch.zeros((self.V, 3, self.H, self.W), device=self.device)
         self.dimg = torch.zeros_like(self.img)

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvbm.so")
 VBM_OK, VBM_ERR_ARG, VBM_ERR_CAPACITY, VBM_ERR_CUDA, VBM_ERR_TIMEOUT, VBM_ERR_NOMEM, VBM_ERR_NUMERIC = range(7)
 PLAN_RECOMPUTE = 1
 PLAN_PERSISTENT = 2
+PLAN_RADIX_SORT = 4
 
 EXPORTED = ["vbm_last_error", "vbm_version", "vbm_bank_build", "vbm_tf_apply", "vbm_dwt3d",
             "vbm_build_workspace_size", "vbm_build", "vbm_render_dvr", "vbm_plan_create",

@@ -21,13 +21,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _forward(vbm, P, cams, W, H, tile=(16, 16), cap=1 << 22, scene_offset=None, view_scene=None, bg=(0, 0, 0),
-             ppt=0, persistent=False, gl=0, seg=0):
+             ppt=0, persistent=False, gl=0, seg=0, radix=False):
     params, cams_dev = to_device(P, cams)
     V = len(cams)
     so = [0, P.shape[1]] if scene_offset is None else scene_offset
+    flags = (vbm.PLAN_PERSISTENT if persistent else 0) | (vbm.PLAN_RADIX_SORT if radix else 0)
     plan = vbm.Plan(so, V, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1], pair_capacity=cap,
-                    pixels_per_thread=ppt, flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=gl,
-                    segment_len=seg)
+                    pixels_per_thread=ppt, flags=flags, group_lanes=gl, segment_len=seg)
     img = torch.zeros((V, 3, H, W), device="cuda")
     alpha = torch.zeros((V, H, W), device="cuda")
     plan.forward(params, cams_dev, img, alpha, bg=bg)
@@ -70,15 +70,16 @@ def test_preprocess_matches_oracle(cuda_lib):
     assert flagged < 0.01 * 3 * n
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (8, 4)])
-def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile):
+@pytest.mark.parametrize("tile,radix", [((16, 16), False), ((8, 8), False), ((8, 4), False), ((16, 16), True),
+                                        ((8, 8), True)])
+def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile, radix):
     """Pair lists, order and ranges equal, bit for bit, the oracle's (tile, depth, index)
     sort of the GPU's rectangles and depths, with the oracle's float32 tile test on the
     GPU's float32 splat records; the records' B/C and B/A are the float32 quotients of the
     GPU's own conic, and the test removes pairs (the lists are shorter than the
     rectangles)."""
     P, cams, cams32 = scene(seed=2, n=2500, V=3, W=100, H=76)
-    plan, *_ = _forward(cuda_lib, P, cams, 100, 76, tile=tile)
+    plan, *_ = _forward(cuda_lib, P, cams, 100, 76, tile=tile, radix=radix, persistent=radix)
     st = plan_state(plan, 3)
     n = P.shape[1]
     TX, TY = _tiles(100, 76, tile)
@@ -98,7 +99,8 @@ def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile):
     assert np.array_equal(st["ranges"], ranges)
 
 
-def test_binning_long_lists_bit_exact(cuda_lib):
+@pytest.mark.parametrize("radix", [False, True])
+def test_binning_long_lists_bit_exact(cuda_lib, radix):
     """Crowded scene: one cluster of 10,000 small Gaussians (plus 500 exact copies, so
     equal depths must fall back to the index order) projects into a few tiles, whose
     lists exceed the 4096 keys one block sorts in shared memory; a wider cluster gives
@@ -112,7 +114,7 @@ def test_binning_long_lists_bit_exact(cuda_lib):
     wide = random_gaussians(3000, 8.0, 24.0, seed=22, scale_range=(0.2, 1.5), opacity_logit_range=(-2.0, 2.0))
     P = np.concatenate([core, core[:, :500], wide], axis=1).astype(np.float32)
     cams = orbit_cameras((G, G, G), 1, W, H)
-    plan, *_ = _forward(cuda_lib, P, cams, W, H, tile=tile)
+    plan, *_ = _forward(cuda_lib, P, cams, W, H, tile=tile, radix=radix)
     st = plan_state(plan, 1)
     TX, TY = _tiles(W, H, tile)
     lengths = st["ranges"][:, 1] - st["ranges"][:, 0]
@@ -138,13 +140,14 @@ def test_binning_long_lists_bit_exact(cuda_lib):
                                                     ((16, 16), 1, False, 8), ((16, 16), 2, True, 16),
                                                     ((16, 8), 4, False, 8), ((8, 8), 2, False, 8),
                                                     ((8, 4), 1, True, 16), ((8, 4), 1, False, 32),
-                                                    ((16, 4), 1, True, 8)])
+                                                    ((16, 4), 1, True, 8), ((8, 8), 1, "radix", 16)])
 def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt, persistent, gl):
+    """persistent = "radix": a persistent plan ordering its pairs by device radix sorts."""
     W, H = 100, 76
     P, cams, cams32 = scene(seed=3, n=2500, V=2, W=W, H=H)
     bg = (0.1, 0.2, 0.05)
-    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt, persistent=persistent,
-                                      gl=gl)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, tile=tile, bg=bg, ppt=ppt, persistent=bool(persistent),
+                                      gl=gl, radix=persistent == "radix")
     st = plan_state(plan, 2)
     splat, color = gpu_splats_as_oracle(st)
     ref = oraster.render(2, W, H, tile[0], tile[1], st["ranges"], st["pair_item"].astype(np.int32), splat, color,
@@ -435,3 +438,34 @@ def test_segmented_backward_equals_whole_walk(cuda_lib, tile, ppt, gl):
     for k in range(3):
         nrm, elt = rel_group_error(gs[6 + k], c_ref[:, k])
         assert nrm < 1e-3 and elt < 1e-3, (k, nrm, elt)
+
+
+@pytest.mark.parametrize("tile,persistent", [((8, 8), True), ((16, 16), False)])
+def test_radix_ordering_equals_bucketed_ordering(cuda_lib, tile, persistent):
+    """The device radix sorts (items by depth, pairs stably by tile) and the bucketed
+    per-tile sort give the same lists, ranges, images and (up to atomic order) gradients,
+    on uneven scenes of a batch."""
+    vbm = cuda_lib
+    W, H = 96, 72
+    P1, cams, _ = scene(seed=41, n=1800, V=3, W=W, H=H)
+    P2, _, _ = scene(seed=42, n=700, V=3, W=W, H=H)
+    P = np.concatenate([P1, P2], axis=1)
+    so, vs = [0, P1.shape[1], P.shape[1]], [0, 1, 1]
+    w = torch.from_numpy(np.random.default_rng(5).standard_normal((3, 3, H, W)).astype(np.float32)).cuda()
+    out = []
+    for radix in (False, True):
+        plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, tile=tile, scene_offset=so, view_scene=vs,
+                                                  persistent=persistent, radix=radix)
+        grad = torch.zeros_like(params)
+        plan.backward(params, cams_dev, w, grad)
+        torch.cuda.synchronize()
+        out.append((plan_state(plan, 3), img, grad.cpu().numpy()))
+        ok, need = plan.check()
+        assert ok, need
+    (a, ia, ga), (b, ib, gb) = out
+    assert a["n_pairs"] == b["n_pairs"] > 0
+    for k in ("pair_tile", "pair_item", "ranges"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(ia, ib)
+    nrm, elt = rel_group_error(gb, ga)
+    assert nrm < 1e-5 and elt < 1e-4, (nrm, elt)
