@@ -142,7 +142,7 @@ VBM_API vbm_status vbm_bank_build(int levels, int wavelet, double tau, double ri
 #define VBM_BANK_ISOTROPIC 1     /* ablation "w/o transition bank": one shared isotropic covariance */
 #define VBM_BANK_UNIT_WEIGHT 2   /* ablation "w/o energy projection": w = 1 */
 
-/* Turn a bank into an ablation variant of Sec. 5.3, in place (host only).
+/* Turn a bank into an ablation variant of Sec. 5.4, in place (host only).
  * VBM_BANK_ISOTROPIC: every covariance becomes sigma_iso^2 I, with sigma_iso
  * the mean over the bank's subbands of det(Sigma)^(1/6) (the paper's "average
  * spatial extent in the full model"; centres and weights unchanged).

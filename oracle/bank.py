@@ -126,7 +126,7 @@ def build_bank(levels, wavelet="bior4.4", tau=0.1, ridge_rel=1e-6):
 
 
 def ablate(entries, isotropic=False, unit_weight=False):
-    """Bank of the ablation variants of Sec. 5.3 (entries are not modified).
+    """Bank of the ablation variants of Sec. 5.4 (entries are not modified).
 
     isotropic (w/o transition bank): every covariance becomes sigma_iso^2 I, with
     sigma_iso the average spatial extent of the full bank, read as the mean over

@@ -1,7 +1,7 @@
 """Convergence of the image-space fine-tuning from the VBM initialisation versus a
 random initialisation with the same number of Gaussians (the comparison behind the
-paper's fine-tuning experiments, Sec. 5.2 / Table 1, run here on a synthetic workload),
-and the ablation variants of Sec. 5.3: the bank's covariances collapsed to one
+paper's fine-tuning experiments, Sec. 5.3 / Table 1, run here on a synthetic workload),
+and the ablation variants of Sec. 5.4: the bank's covariances collapsed to one
 isotropic one, unit energy weights, and the Haar wavelet instead of bior4.4.
 
 Both runs use the same targets (vbm_render_dvr), cameras, loss, learning rates and

@@ -291,7 +291,7 @@ extern "C" vbm_status vbm_bank_build(int levels, int wavelet, double tau, double
     return VBM_OK;
 }
 
-// Ablation variants of the bank (Sec. 5.3).  VBM_BANK_ISOTROPIC ("w/o
+// Ablation variants of the bank (Sec. 5.4).  VBM_BANK_ISOTROPIC ("w/o
 // transition bank"): every covariance becomes sigma_iso^2 I, sigma_iso the
 // mean over the bank's subbands of det(Sigma_{j,o})^(1/6), the average
 // spatial extent of the full bank; centres and weights are kept.

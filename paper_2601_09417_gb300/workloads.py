@@ -58,7 +58,7 @@ def _render_targets(Fd, dims, tf, cams, width, height, device):
 
 def make_workload(key, device="cuda", wavelet=0, ablation=0):
     """Build workload `key`; wavelet 1 (Haar) and the bank ablation flags give the
-    ablation variants of Sec. 5.3 (the targets are the same DVR images)."""
+    ablation variants of Sec. 5.4 (the targets are the same DVR images)."""
     cfg = config(key)
     tf = vbm.make_tf(TF_KNOTS_X, TF_KNOTS_RGBA)
     if "edges" in cfg:                      # uneven batch of independent volumes

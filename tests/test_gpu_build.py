@@ -92,7 +92,7 @@ def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0, knots=None
                                                            (32, 2, 4096, 0, 0, 1), (64, 3, 20000, 1, 0, 3)])
 def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation, mode):
     """vbm_build against the oracle: pyramid, kept indices (bit-exact), Gaussians; also
-    with the ablated banks of Sec. 5.3 (isotropic covariance, unit weight) and with two of
+    with the ablated banks of Sec. 5.4 (isotropic covariance, unit weight) and with two of
     the TF modes of Sec. 4.4 (non-zero over one value interval only)."""
     from vbm_inputs import tf_mode
     F = blob_volume(G, 4 if G == 32 else 12, seed=seed)

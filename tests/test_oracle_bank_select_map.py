@@ -37,7 +37,7 @@ def test_haar_bank_closed_form(j):
 
 
 def test_ablated_banks_haar_closed_form():
-    """Ablation variants (Sec. 5.3) of the Haar bank, whose subband covariances are
+    """Ablation variants (Sec. 5.4) of the Haar bank, whose subband covariances are
     (4^j - 1)/12 I: isotropic gives every subband sigma_iso^2 I with sigma_iso the mean
     over the 7J + 1 subbands of sqrt((4^j - 1)/12), keeping centres and weights; unit
     weight sets every w to 1 and changes nothing else."""

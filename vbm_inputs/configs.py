@@ -6,8 +6,8 @@ the adaptive filter; because the MAD threshold leaves many subbands below
 their share, the number of Gaussians kept is smaller, and each K_tot is set
 so that the kept count lands at the workload's stated size (c0 keeps ~3.4k,
 the cap of its MAD candidate set; c1 ~1.0e5; c2 ~5.0e5; c4 ~2.9e6).  Sizes follow the scale of the
-paper's datasets (Sec. 5.1: 256^3 to 512^3 volumes, ~1.8e5 Gaussians for
-Supernova) while staying synthetic.
+paper's datasets (Sec. 5.1: 256^3 to 512^3 volumes; Sec. 5.3: ~1.8e5 Gaussians
+for Supernova) while staying synthetic.
 """
 
 import numpy as np
