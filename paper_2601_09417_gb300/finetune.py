@@ -23,6 +23,20 @@ def default_lrs(extent):
     return [1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3]
 
 
+# Share of the device memory free at plan creation that the stored per-pixel
+# compositing state (final transmittance and last contributor, 8 bytes per
+# pixel of the batch) may take before recompute="auto" chooses to recompute it
+# in the backward instead.
+STATE_MEMORY_SHARE = 0.05
+
+
+def choose_recompute(n_pixels, free_bytes, share=STATE_MEMORY_SHARE):
+    """True when storing the per-pixel state of n_pixels would take more than `share` of
+    the free device memory: the backward then replays the forward's walk (only short
+    lists in persistent plans) instead of reading stored state."""
+    return 8 * int(n_pixels) > share * float(free_bytes)
+
+
 class FineTuner:
     def __init__(self, params, cam_records, targets, scene_offset=None, view_scene=None, tile=(16, 16), ppt=0,
                  persistent=False, pair_capacity=None, lrs=None, lam=0.2, bg=(0.0, 0.0, 0.0), extent=None,
@@ -41,6 +55,10 @@ class FineTuner:
             pair_capacity = vbm.default_pair_capacity(vbm.batch_items(self.scene_offset, self.V, view_scene))
         self.tile, self.ppt, self.persistent = tuple(tile), int(ppt), bool(persistent)
         self.group_lanes = int(group_lanes)
+        if recompute == "auto":
+            free, _ = torch.cuda.mem_get_info(self.device)
+            recompute = choose_recompute(self.V * self.H * self.W, free)
+        self.recompute = bool(recompute)
         self.plan = vbm.Plan(self.scene_offset, self.V, self.W, self.H, view_scene=view_scene, tile_w=tile[0],
                              tile_h=tile[1], pair_capacity=min(pair_capacity, vbm.MAX_PAIR_CAPACITY), pixels_per_thread=ppt,
                              flags=(vbm.PLAN_PERSISTENT if persistent else 0) |

@@ -1,5 +1,6 @@
-"""Host logic of the autotuner, without a GPU: the candidate list and the configuration
-tuples handed to the timing trials (segment length last, pair capacity in its place)."""
+"""Host logic without a GPU: the autotuner's candidate list and the configuration tuples
+handed to its timing trials (segment length last, pair capacity in its place), and the
+fine-tuner's choice to recompute per-pixel state when storing it would crowd memory."""
 
 import pytest
 
@@ -34,3 +35,12 @@ def test_retime_passes_segment_length_and_capacity(monkeypatch):
                     [((8, 8), 1, 16, True), ((16, 8), 2, 8, True, 128)], 12345, rounds=2, iters=1, recompute=True)
     assert made == [((8, 8), 1, 16, True, 12345, 0, True), ((16, 8), 2, 8, True, 12345, 128, True)]
     assert len(out) == 2
+
+
+def test_recompute_is_chosen_when_state_would_crowd_memory():
+    from paper_2601_09417_gb300.finetune import STATE_MEMORY_SHARE, choose_recompute
+    px = 8 * 1024 * 1024                       # 8 views of 1024^2: 64 MiB of state
+    assert not choose_recompute(px, 200 << 30)  # a mostly free GB300
+    assert choose_recompute(px, 1 << 30)        # 1 GiB free: 64 MiB is above the share
+    edge = 8 * px / STATE_MEMORY_SHARE
+    assert not choose_recompute(px, edge) and choose_recompute(px, edge - 1)
