@@ -308,34 +308,42 @@ def test_uneven_multi_scene_batch(cuda_lib):
         assert np.abs(img[v] - single["img"][0])[:, gd].max() <= 1e-3
 
 
-def test_capacity_overflow_is_reported(cuda_lib):
+@pytest.mark.parametrize("persistent,radix", [(False, False), (True, False), (True, True), (False, True)])
+def test_capacity_overflow_is_reported(cuda_lib, persistent, radix):
     W, H = 64, 48
     P, cams, _ = scene(seed=8, n=800, V=1, W=W, H=H)
-    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, cap=16, bg=(0.3, 0.2, 0.1))
+    plan, params, cams_dev, img, _ = _forward(cuda_lib, P, cams, W, H, cap=16, bg=(0.3, 0.2, 0.1),
+                                              persistent=persistent, radix=radix)
     ok, need = plan.check()
     assert not ok and need > 16
     assert np.allclose(img[0, 0], 0.3) and np.allclose(img[0, 2], 0.1)
+    # the backward of a call that overflowed leaves the gradient at zero
+    grad = torch.zeros_like(params)
+    plan.backward(params, cams_dev, torch.ones((1, 3, H, W), device="cuda"), grad)
+    torch.cuda.synchronize()
+    assert not grad.any()
     ok, _ = plan.check()         # the status word is cleared by the check
     assert ok
 
 
-def test_empty_and_culled_scenes(cuda_lib):
+@pytest.mark.parametrize("persistent,radix", [(False, False), (True, True)])
+def test_empty_and_culled_scenes(cuda_lib, persistent, radix):
     W, H = 40, 24
     bg = (0.25, 0.5, 0.75)
     P = np.zeros((14, 0), dtype=np.float32)
     _, cams, _ = scene(seed=0, n=1, V=2, W=W, H=H)
-    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg, persistent=persistent, radix=radix)
     assert np.array_equal(img[:, 0], np.full((2, H, W), 0.25, dtype=np.float32)) and alpha.max() == 0
     # every Gaussian behind the camera (camera-space z = -5)
     P, cams, _ = scene(seed=9, n=50, V=1, W=W, H=H)
     R, t = np.asarray(cams[0]["R"]), np.asarray(cams[0]["t"])
     P[0:3] = (R.T @ (np.array([0.0, 0.0, -5.0]) - t))[:, None]
-    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg)
+    plan, _, _, img, alpha = _forward(cuda_lib, P, cams, W, H, bg=bg, persistent=persistent, radix=radix)
     assert alpha.max() == 0 and np.allclose(img[0, 2], 0.75)
 
 
 @pytest.mark.parametrize("persistent,gl,seg", [(False, 32, 0), (True, 32, 0), (True, 8, 0), (True, 16, 32),
-                                              (True, 32, 64)])
+                                              (True, 32, 64), (True, 16, "radix")])
 def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl, seg):
     """VBM_PLAN_RECOMPUTE keeps no per-pixel state; the backward replays the forward's
     decisions (for lists split into segments of seg entries, it reads the final state the
@@ -347,8 +355,10 @@ def test_recompute_mode_matches_stored_state(cuda_lib, persistent, gl, seg):
     params, cams_dev = to_device(P, cams)
     w = torch.from_numpy(np.random.default_rng(3).standard_normal((V, 3, H, W)).astype(np.float32)).cuda()
     out = []
+    radix = seg == "radix"        # radix-sort ordering, default segments
+    seg = 0 if radix else seg
     for flags in (0, vbm.PLAN_RECOMPUTE):
-        fl = flags | (vbm.PLAN_PERSISTENT if persistent else 0)
+        fl = flags | (vbm.PLAN_PERSISTENT if persistent else 0) | (vbm.PLAN_RADIX_SORT if radix else 0)
         plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 22, flags=fl, tile_w=8, tile_h=8,
                         pixels_per_thread=1, group_lanes=gl, segment_len=seg)
         img = torch.zeros((V, 3, H, W), device="cuda")
