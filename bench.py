@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread with --tile")
     ap.add_argument("--persistent", action="store_true", help="persistent compositing kernels with --tile")
     ap.add_argument("--gl", type=int, default=32, help="lanes per compositing group with --tile (8, 16, 32)")
+    ap.add_argument("--bwd-ppt", type=int, default=0, help="backward pixels per thread (0 = the forward's)")
+    ap.add_argument("--bwd-gl", type=int, default=0, help="backward lanes per group (0 = the forward's)")
     ap.add_argument("--radix", action="store_true",
                     help="order the pairs by device radix sorts (items by depth, pairs by tile)")
     ap.add_argument("--seg", type=int, default=0,
@@ -278,6 +280,7 @@ def main():
     if args.tile:
         tile, ppt, gl, pers = tuple(int(x) for x in args.tile.split("x")), args.ppt, args.gl, args.persistent
         seg = args.seg
+        bppt, bgl = args.bwd_ppt, args.bwd_gl
         tune_table = []
     else:
         from paper_2601_09417_gb300.autotune import autotune
@@ -289,12 +292,15 @@ def main():
         for _ in range(TUNE_WARM_STEPS):
             ftw.step_batched()
         torch.cuda.synchronize()
-        (tile, ppt, gl, pers, seg), tune_table = autotune(ftw.params, recs, V, W, H, scene_offset=w.scene_offset,
+        (tile, ppt, gl, pers, seg, bppt, bgl), tune_table = autotune(ftw.params, recs, V, W, H, scene_offset=w.scene_offset,
                                                            view_scene=w.view_scene, recompute=batch["recompute"])
         del ftw
     if args.seg:
         seg = args.seg
-    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=seg, radix_sort=args.radix)
+    if args.bwd_ppt or args.bwd_gl:
+        bppt, bgl = args.bwd_ppt, args.bwd_gl
+    launch = dict(tile=tile, ppt=ppt, persistent=pers, group_lanes=gl, segment_len=seg, radix_sort=args.radix,
+                  bwd_ppt=bppt, bwd_group_lanes=bgl)
     if args.profile_only:
         ftp = FineTuner(params, recs, targets, **batch, **launch)
         for _ in range(args.warmup + args.steps):
@@ -450,6 +456,7 @@ def main():
             "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
                        "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "group_lanes": gl, "persistent": pers,
                        "segment_len": (seg if seg else 256) if pers else None,
+                       "bwd_pixels_per_thread": bppt or ppt, "bwd_group_lanes": bgl or gl,
                        "pair_order": "device radix sorts" if args.radix else "bucketed per-tile sort",
                        "compositing_state": "recomputed in the backward" if batch["recompute"] else "stored",
                        "pairs_mean": n_pairs,
@@ -461,11 +468,16 @@ def main():
             "autotune": {"candidates": len(tune_table),
                          "fastest": [{"tile": "%dx%d" % tuple(r["tile"]), "ppt": r["ppt"],
                                       "group_lanes": r["group_lanes"], "persistent": r["persistent"],
-                                      "ms_fwd_bwd": r["ms"], "ms_fwd_bwd_retimed": r.get("ms_final")}
-                                     for r in sorted((r for r in tune_table if r.get("stage") != "segment"),
-                                                     key=lambda r: r.get("ms_final", r["ms"]))[:6]],
+                                      "ms_fwd_bwd": r["ms"], "ms_fwd": r.get("ms_fwd"), "ms_bwd": r.get("ms_bwd")}
+                                     for r in sorted((r for r in tune_table if r.get("stage") is None),
+                                                     key=lambda r: r["ms"])[:6]],
+                         "pairs_retimed": [{"tile": "%dx%d" % tuple(r["tile"]), "fwd": [r["ppt"], r["group_lanes"]],
+                                            "bwd": [r["bwd_ppt"], r["bwd_group_lanes"]], "persistent": r["persistent"],
+                                            "ms_estimate": r["ms"], "ms_fwd_bwd_retimed": r["ms_final"]}
+                                           for r in tune_table if r.get("stage") == "combination"],
                          "segment_len": [{"segment_len": r["segment_len"], "ms_fwd_bwd": r["ms"]}
                                          for r in tune_table if r.get("stage") == "segment"],
+
                          "tuned_after_steps": TUNE_WARM_STEPS if tune_table else 0},
             "batched_over_plain": plain_ms / ms_per_step,
             "step_ms_percentiles": {"p10": float(np.percentile(step_ms, 10)),

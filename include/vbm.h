@@ -246,6 +246,9 @@ typedef struct {
                                       65536; -1 = never split.  Ignored by other plans.  Results
                                       equal the unsplit walk's up to FP32 rounding of the
                                       transmittance and of the colour sums. */
+    int32_t bwd_pixels_per_thread; /* the backward compositing kernel's own pixels per thread and */
+    int32_t bwd_group_lanes;       /* lanes per group (0 = the forward's); its warp regions are its
+                                      own, so results do not depend on them */
 } vbm_plan_desc;
 
 /* Create a plan (allocates device memory, synchronous). */

@@ -9,13 +9,16 @@ memory per round; lanes per group sets the pixel block whose own entry list a
 lane group walks (smaller groups: fewer idle lanes, more reductions per
 pixel in the backward); persistent runs the compositing kernels as one grid
 of resident blocks taking tiles longest-list-first from a work queue instead
-of one block per tile.  For a persistent winner a second stage times the
-per-warp list length: the number of list entries beyond which the backward
-walks a tile's list as separate segments (SEGMENT_LENGTHS; -1 never splits).
+of one block per tile.
 Each candidate runs the batch's forward and backward calls on the caller's
 own Gaussians and cameras (median of a few timed repetitions, CUDA events on
-the current stream); the fastest few are then timed again, in turns, with
-more repetitions, and the fastest of those wins.  Results are cached in a
+the current stream), the two calls timed apart; for each tile shape and
+persistence the fastest forward configuration is paired with the fastest
+backward one (the backward's warp regions are its own), and the best few
+pairs are timed again together, in turns, with more repetitions.  For a
+persistent winner a last stage times the per-warp list length: the number of
+list entries beyond which the backward walks a tile's list as separate
+segments (SEGMENT_LENGTHS; -1 never splits).  Results are cached in a
 JSON file keyed by device name and workload signature.
 """
 
@@ -36,7 +39,7 @@ CANDIDATES = [(tile, ppt, gl, pers)
               if tile[1] % (4 * ppt) == 0]   # a warp region is 4 thread rows of ppt pixels
 SEGMENT_LENGTHS = (64, 128, 256, 512, -1)
 DEFAULT = ((16, 16), 2, 32, False, 0)
-CACHE_FORMAT = "v5"
+CACHE_FORMAT = "v6"
 
 
 def _cache_path():
@@ -58,27 +61,29 @@ class _Trial:
     """A plan and buffers for one candidate; times forward + backward calls of the batch."""
 
     def __init__(self, params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent,
-                 pair_capacity, segment_len=0, recompute=False):
+                 pair_capacity, segment_len=0, bwd_ppt=0, bwd_gl=0, recompute=False):
         self.params, self.cams = params, cams_dev
         self.plan = vbm.Plan(scene_offset, n_views, W, H, view_scene=view_scene, tile_w=tile[0], tile_h=tile[1],
                              pair_capacity=pair_capacity, pixels_per_thread=ppt,
                              flags=(vbm.PLAN_PERSISTENT if persistent else 0) |
                              (vbm.PLAN_RECOMPUTE if recompute else 0), group_lanes=gl,
-                             segment_len=segment_len)
+                             segment_len=segment_len, bwd_pixels_per_thread=bwd_ppt, bwd_group_lanes=bwd_gl)
         self.img = torch.zeros((n_views, 3, H, W), device=params.device)
         self.dimg = torch.full_like(self.img, 1e-6)
         self.grad = torch.zeros_like(params)
 
-    def run(self, iters):
+    def run(self, iters, split=False):
+        """ms of `iters` forward + backward calls; with split, (forward ms, backward ms) pairs."""
         times = []
         for _ in range(iters):
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s, m, e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             s.record()
             self.plan.forward(self.params, self.cams, self.img)
+            m.record()
             self.plan.backward(self.params, self.cams, self.dimg, self.grad)
             e.record()
             e.synchronize()
-            times.append(s.elapsed_time(e))
+            times.append((s.elapsed_time(m), m.elapsed_time(e)) if split else s.elapsed_time(e))
         return times
 
     def close(self):
@@ -89,17 +94,22 @@ class _Trial:
 
 def time_config(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent, pair_capacity,
                 iters=5, recompute=False):
-    """Median ms of one forward + backward call of the whole batch with this configuration."""
+    """Median ms of one forward + backward call of the whole batch with this configuration, and
+    the medians of the forward and the backward call alone; plus the pairs needed."""
     t = _Trial(params, cams_dev, n_views, W, H, scene_offset, view_scene, tile, ppt, gl, persistent, pair_capacity,
                recompute=recompute)
-    times = t.run(iters + 2)[2:]
+    times = t.run(iters + 2, split=True)[2:]
     ok, need = t.close()
-    return (float(np.median(times)) if ok else float("inf")), need
+    if not ok:
+        return float("inf"), float("inf"), float("inf"), need
+    return (float(np.median([a + b for a, b in times])), float(np.median([a for a, _ in times])),
+            float(np.median([b for _, b in times])), need)
 
 
 def retime(params, cams_dev, n_views, W, H, scene_offset, view_scene, configs, pair_capacity, rounds=8, iters=3,
            recompute=False):
-    """Median ms of each configuration (tile, ppt, group lanes, persistent[, segment length]),
+    """Median ms of each configuration (tile, ppt, group lanes, persistent[, segment length[,
+    backward ppt, backward group lanes]]),
     timed in turns (rounds x iters calls each) so that clock or thermal drift affects them
     alike."""
     trials = [_Trial(params, cams_dev, n_views, W, H, scene_offset, view_scene, *c[:4], pair_capacity, *c[4:],
@@ -119,8 +129,9 @@ def retime(params, cams_dev, n_views, W, H, scene_offset, view_scene, configs, p
 
 def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=None, pair_capacity=None,
              candidates=None, use_cache=True, recompute=False):
-    """Best ((tile_w, tile_h), ppt, group_lanes, persistent, segment_len) for this workload, plus the
-    table of timings (segment_len 0: the library's default; only persistent plans split lists).
+    """Best ((tile_w, tile_h), ppt, group_lanes, persistent, segment_len, bwd_ppt, bwd_group_lanes)
+    for this workload, plus the table of timings (segment_len 0: the library's default; only
+    persistent plans split lists; bwd_* 0: the forward's).
     recompute: time plans that keep no per-pixel state (VBM_PLAN_RECOMPUTE), as the caller will run."""
     n = int(params.shape[1] if scene_offset is None else scene_offset[-1])
     so = [0, n] if scene_offset is None else list(scene_offset)
@@ -137,38 +148,49 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
             cache = {}
     if use_cache and key in cache:
         ent = cache[key]
-        return (tuple(ent["tile"]), ent["ppt"], ent["group_lanes"], ent["persistent"], ent["segment_len"]), \
-            ent["table"]
+        return (tuple(ent["tile"]), ent["ppt"], ent["group_lanes"], ent["persistent"], ent["segment_len"],
+                ent["bwd_ppt"], ent["bwd_group_lanes"]), ent["table"]
     cams_dev = vbm.cameras_to_device(cam_records, params.device)
     cap = pair_capacity if pair_capacity is not None else vbm.default_pair_capacity(
         vbm.batch_items(so, n_views, view_scene))
     cap = min(cap, vbm.MAX_PAIR_CAPACITY)
     table = []
     for tile, ppt, gl, persistent in (candidates or CANDIDATES):
-        ms, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, gl, persistent, cap,
-                               recompute=recompute)
+        ms, ms_f, ms_b, need = time_config(params, cams_dev, n_views, W, H, so, view_scene, tile, ppt, gl,
+                                           persistent, cap, recompute=recompute)
         table.append({"tile": list(tile), "ppt": ppt, "group_lanes": gl, "persistent": persistent, "ms": ms,
-                      "pairs_needed": need})
-    # the fastest few again, in turns and with more repetitions
-    top = sorted(range(len(table)), key=lambda k: table[k]["ms"])[:4]
+                      "ms_fwd": ms_f, "ms_bwd": ms_b, "pairs_needed": need})
+    # per (tile, persistence): the fastest forward configuration with the fastest
+    # backward one; the best few of these pairs again, in turns, together
+    combos = []
+    for tp in sorted({(tuple(r["tile"]), r["persistent"]) for r in table}):
+        rows = [r for r in table if (tuple(r["tile"]), r["persistent"]) == tp]
+        f = min(rows, key=lambda r: r["ms_fwd"])
+        b = min(rows, key=lambda r: r["ms_bwd"])
+        combos.append((f["ms_fwd"] + b["ms_bwd"], tp[0], f["ppt"], f["group_lanes"], tp[1], b["ppt"],
+                       b["group_lanes"]))
+    combos = sorted(c for c in combos if np.isfinite(c[0]))[:4] or [(0.0,) + tuple(DEFAULT[:4]) + (0, 0)]
     finals = retime(params, cams_dev, n_views, W, H, so, view_scene,
-                    [(tuple(table[k]["tile"]), table[k]["ppt"], table[k]["group_lanes"], table[k]["persistent"])
-                     for k in top], cap, recompute=recompute)
-    for k, ms in zip(top, finals):
-        table[k]["ms_final"] = ms
-    best = table[top[int(np.argmin(finals))]]
+                    [(c[1], c[2], c[3], c[4], 0, c[5], c[6]) for c in combos], cap, recompute=recompute)
+    for c, ms in zip(combos, finals):
+        table.append({"tile": list(c[1]), "ppt": c[2], "group_lanes": c[3], "persistent": c[4], "bwd_ppt": c[5],
+                      "bwd_group_lanes": c[6], "ms": c[0], "ms_final": ms, "stage": "combination"})
+    _, tile, ppt_b, gl_b, pers_b, bwd_ppt, bwd_gl = combos[int(np.argmin(finals))]
+    best = {"tile": list(tile), "ppt": ppt_b, "group_lanes": gl_b, "persistent": pers_b}
     seg = 0
-    if best["persistent"]:
+    if pers_b:
         segs = retime(params, cams_dev, n_views, W, H, so, view_scene,
-                      [(tuple(best["tile"]), best["ppt"], best["group_lanes"], True, s) for s in SEGMENT_LENGTHS], cap,
+                      [(tile, ppt_b, gl_b, True, s_len, bwd_ppt, bwd_gl) for s_len in SEGMENT_LENGTHS], cap,
                       recompute=recompute)
         for s_len, ms in zip(SEGMENT_LENGTHS, segs):
-            table.append({"tile": best["tile"], "ppt": best["ppt"], "group_lanes": best["group_lanes"],
-                          "persistent": True, "segment_len": s_len, "ms": ms, "ms_final": ms, "stage": "segment"})
+            table.append({"tile": list(tile), "ppt": ppt_b, "group_lanes": gl_b, "persistent": True,
+                          "bwd_ppt": bwd_ppt, "bwd_group_lanes": bwd_gl, "segment_len": s_len, "ms": ms,
+                          "ms_final": ms, "stage": "segment"})
         seg = SEGMENT_LENGTHS[int(np.argmin(segs))]
     if use_cache:
         cache[key] = {"tile": best["tile"], "ppt": best["ppt"], "group_lanes": best["group_lanes"],
-                      "persistent": best["persistent"], "segment_len": seg, "table": table}
+                      "persistent": best["persistent"], "segment_len": seg, "bwd_ppt": bwd_ppt,
+                      "bwd_group_lanes": bwd_gl, "table": table}
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             tmp = path + ".%d.tmp" % os.getpid()
@@ -177,4 +199,4 @@ def autotune(params, cam_records, n_views, W, H, scene_offset=None, view_scene=N
             os.replace(tmp, path)
         except OSError:
             pass
-    return (tuple(best["tile"]), best["ppt"], best["group_lanes"], best["persistent"], seg), table
+    return (tuple(best["tile"]), best["ppt"], best["group_lanes"], best["persistent"], seg, bwd_ppt, bwd_gl), table

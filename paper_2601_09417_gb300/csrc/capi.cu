@@ -109,6 +109,12 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     VBM_ARG(d->pixels_per_thread == 0 || d->pixels_per_thread == 1 || d->pixels_per_thread == 2 ||
                 d->pixels_per_thread == 4,
             "pixels_per_thread must be 0, 1, 2 or 4");
+    VBM_ARG(d->bwd_group_lanes == 0 || d->bwd_group_lanes == 8 || d->bwd_group_lanes == 16 ||
+                d->bwd_group_lanes == 32,
+            "bwd_group_lanes must be 0, 8, 16 or 32");
+    VBM_ARG(d->bwd_pixels_per_thread == 0 || d->bwd_pixels_per_thread == 1 || d->bwd_pixels_per_thread == 2 ||
+                d->bwd_pixels_per_thread == 4,
+            "bwd_pixels_per_thread must be 0, 1, 2 or 4");
     VBM_ARG(d->segment_len == -1 || (d->segment_len >= 0 && d->segment_len <= 65536 && d->segment_len % 32 == 0),
             "segment_len must be -1, 0 or a positive multiple of 32 up to 65536");
     VBM_ARG(d->scene_offset[0] == 0, "scene_offset[0] must be 0");

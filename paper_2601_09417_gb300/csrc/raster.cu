@@ -809,15 +809,25 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 }
 
-int pixels_per_thread(const vbm_plan *p)
+// Pixels per thread and lanes per group of the forward (bwd = false) or the
+// backward compositing kernel; the backward takes the forward's unless the
+// plan sets its own.  Each kernel's warp regions are its own: the backward
+// reads only per-pixel state and tile-indexed checkpoints of the forward.
+int pixels_per_thread(const vbm_plan *p, bool bwd = false)
 {
     const int th = p->desc.tile_h;
-    int ppt = p->desc.pixels_per_thread > 0 ? p->desc.pixels_per_thread : 2;
+    const int want = bwd && p->desc.bwd_pixels_per_thread > 0 ? p->desc.bwd_pixels_per_thread
+                                                               : p->desc.pixels_per_thread;
+    int ppt = want > 0 ? want : 2;
     while (ppt > 1 && th % (kRegionRows * ppt) != 0) ppt >>= 1;
     return ppt;
 }
 
-int group_lanes(const vbm_plan *p) { return p->desc.group_lanes > 0 ? p->desc.group_lanes : 32; }
+int group_lanes(const vbm_plan *p, bool bwd = false)
+{
+    const int want = bwd && p->desc.bwd_group_lanes > 0 ? p->desc.bwd_group_lanes : p->desc.group_lanes;
+    return want > 0 ? want : 32;
+}
 
 int regions_per_tile(const vbm_plan *p, int ppt)
 {
@@ -888,8 +898,8 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
 }
 
 // Dispatch on (pixels per thread, lanes per group).
-#define VBM_RASTER_DISPATCH(FN, ...)                                                                  \
-    switch (pixels_per_thread(p) * 64 + group_lanes(p)) {                                             \
+#define VBM_RASTER_DISPATCH(FN, BWD, ...)                                                             \
+    switch (pixels_per_thread(p, BWD) * 64 + group_lanes(p, BWD)) {                                   \
         case 1 * 64 + 8: return FN<1, 8>(__VA_ARGS__);                                                \
         case 1 * 64 + 16: return FN<1, 16>(__VA_ARGS__);                                              \
         case 1 * 64 + 32: return FN<1, 32>(__VA_ARGS__);                                              \
@@ -906,14 +916,14 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
 
 vbm_status raster_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img, float *alpha, cudaStream_t st)
 {
-    VBM_RASTER_DISPATCH(launch_fwd, p, vb, vc, bg, img, alpha, st)
+    VBM_RASTER_DISPATCH(launch_fwd, false, p, vb, vc, bg, img, alpha, st)
 }
 
 vbm_status raster_bwd(vbm_plan *p, const float *, int64_t, int vb, int vc, const float bg[3], const float *dimg,
                       const float *dalpha, float *, cudaStream_t st)
 {
     VBM_CUDA(cudaMemsetAsync(p->g_splat, 0, sizeof(float) * kGradStride * p->last_items, st));
-    VBM_RASTER_DISPATCH(launch_bwd, p, vb, vc, bg, dimg, dalpha, st)
+    VBM_RASTER_DISPATCH(launch_bwd, true, p, vb, vc, bg, dimg, dalpha, st)
 }
 
 }  // namespace vbm

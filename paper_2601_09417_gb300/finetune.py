@@ -40,7 +40,8 @@ def choose_recompute(n_pixels, free_bytes, share=STATE_MEMORY_SHARE):
 class FineTuner:
     def __init__(self, params, cam_records, targets, scene_offset=None, view_scene=None, tile=(16, 16), ppt=0,
                  persistent=False, pair_capacity=None, lrs=None, lam=0.2, bg=(0.0, 0.0, 0.0), extent=None,
-                 device="cuda", group_lanes=0, recompute=False, segment_len=0, radix_sort=False):
+                 device="cuda", group_lanes=0, recompute=False, segment_len=0, radix_sort=False, bwd_ppt=0,
+                 bwd_group_lanes=0):
         self.device = torch.device(device)
         self.params = params
         self.n = params.shape[1] if scene_offset is None else int(scene_offset[-1])
@@ -64,7 +65,8 @@ class FineTuner:
                              flags=(vbm.PLAN_PERSISTENT if persistent else 0) |
                              (vbm.PLAN_RECOMPUTE if recompute else 0) |
                              (vbm.PLAN_RADIX_SORT if radix_sort else 0), group_lanes=group_lanes,
-                             segment_len=segment_len)
+                             segment_len=segment_len, bwd_pixels_per_thread=bwd_ppt,
+                             bwd_group_lanes=bwd_group_lanes)
         self.img = torch.zeros((self.V, 3, self.H, self.W), device=self.device)
         self.dimg = torch.zeros_like(self.img)
         self.grad = torch.zeros_like(params)

@@ -65,7 +65,8 @@ class PlanDesc(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("pair_capacity", ctypes.c_int64), ("flags", ctypes.c_int32),
                 ("pixels_per_thread", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
-                ("segment_len", ctypes.c_int32)]
+                ("segment_len", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
+                ("bwd_group_lanes", ctypes.c_int32)]
 
 
 class PlanBuffers(ctypes.Structure):
@@ -275,7 +276,8 @@ class Plan:
     """Owner of a vbm_plan (device buffers of the splatting forward/backward)."""
 
     def __init__(self, scene_offset, n_views, width, height, view_scene=None, tile_w=16, tile_h=16,
-                 pair_capacity=1 << 20, flags=0, pixels_per_thread=0, group_lanes=0, segment_len=0):
+                 pair_capacity=1 << 20, flags=0, pixels_per_thread=0, group_lanes=0, segment_len=0,
+                 bwd_pixels_per_thread=0, bwd_group_lanes=0):
         lib = load()
         self._lib = lib
         so = np.ascontiguousarray(scene_offset, dtype=np.int64)
@@ -300,6 +302,8 @@ class Plan:
         self.group_lanes = int(group_lanes)
         d.segment_len = int(segment_len)
         self.segment_len = int(segment_len)
+        d.bwd_pixels_per_thread = int(bwd_pixels_per_thread)
+        d.bwd_group_lanes = int(bwd_group_lanes)
         h = ctypes.c_void_p()
         _check(lib.vbm_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h

@@ -21,8 +21,8 @@ def test_retime_passes_segment_length_and_capacity(monkeypatch):
 
     class Trial:
         def __init__(self, params, cams, n_views, W, H, so, vs, tile, ppt, gl, persistent, cap, segment_len=0,
-                     recompute=False):
-            made.append((tile, ppt, gl, persistent, cap, segment_len, recompute))
+                     bwd_ppt=0, bwd_gl=0, recompute=False):
+            made.append((tile, ppt, gl, persistent, cap, segment_len, bwd_ppt, bwd_gl, recompute))
 
         def run(self, iters):
             return [1.0 + len(made)] * iters
@@ -32,9 +32,11 @@ def test_retime_passes_segment_length_and_capacity(monkeypatch):
 
     monkeypatch.setattr(at, "_Trial", Trial)
     out = at.retime(None, None, 2, 8, 8, [0, 1], None,
-                    [((8, 8), 1, 16, True), ((16, 8), 2, 8, True, 128)], 12345, rounds=2, iters=1, recompute=True)
-    assert made == [((8, 8), 1, 16, True, 12345, 0, True), ((16, 8), 2, 8, True, 12345, 128, True)]
-    assert len(out) == 2
+                    [((8, 8), 1, 16, True), ((16, 8), 2, 8, True, 128), ((8, 8), 1, 16, True, 64, 2, 8)], 12345,
+                    rounds=2, iters=1, recompute=True)
+    assert made == [((8, 8), 1, 16, True, 12345, 0, 0, 0, True), ((16, 8), 2, 8, True, 12345, 128, 0, 0, True),
+                    ((8, 8), 1, 16, True, 12345, 64, 2, 8, True)]
+    assert len(out) == 3
 
 
 def test_recompute_is_chosen_when_state_would_crowd_memory():

@@ -21,9 +21,15 @@ def test_autotune_picks_a_candidate_and_a_segment_length(cuda_lib):
     from vbm_inputs.cameras import camera_array
     recs = camera_array(cams)
     cands = [((8, 8), 1, 16, True), ((16, 16), 1, 32, False)]
-    (tile, ppt, gl, pers, seg), table = autotune.autotune(params, recs, V, W, H, candidates=cands, use_cache=False)
+    (tile, ppt, gl, pers, seg, bppt, bgl), table = autotune.autotune(params, recs, V, W, H, candidates=cands,
+                                                                     use_cache=False)
     assert (tile, ppt, gl, pers) in cands
-    main = [r for r in table if r.get("stage") != "segment"]
+    main = [r for r in table if r.get("stage") is None]
+    assert all(np.isfinite(r["ms_fwd"]) and np.isfinite(r["ms_bwd"]) for r in main)
+    pairs = [r for r in table if r.get("stage") == "combination"]
+    assert pairs and all(np.isfinite(r["ms_final"]) for r in pairs)
+    assert (list(tile), ppt, gl, pers, bppt, bgl) in [(r["tile"], r["ppt"], r["group_lanes"], r["persistent"],
+                                                       r["bwd_ppt"], r["bwd_group_lanes"]) for r in pairs]
     assert len(main) == len(cands) and all(np.isfinite(r["ms"]) and r["ms"] > 0 for r in main)
     segs = [r for r in table if r.get("stage") == "segment"]
     if pers:
@@ -33,10 +39,10 @@ def test_autotune_picks_a_candidate_and_a_segment_length(cuda_lib):
         assert seg == 0 and not segs
     # the tuned plan renders the image of an untuned one bit for bit
     imgs = []
-    for t, p_, g_, per, s_ in ((tile, ppt, gl, pers, seg), ((16, 16), 1, 32, False, 0)):
+    for t, p_, g_, per, s_, bp, bg in ((tile, ppt, gl, pers, seg, bppt, bgl), ((16, 16), 1, 32, False, 0, 0, 0)):
         plan = vbm.Plan([0, P.shape[1]], V, W, H, tile_w=t[0], tile_h=t[1], pair_capacity=1 << 22,
                         pixels_per_thread=p_, group_lanes=g_, flags=vbm.PLAN_PERSISTENT if per else 0,
-                        segment_len=s_)
+                        segment_len=s_, bwd_pixels_per_thread=bp, bwd_group_lanes=bg)
         img = torch.zeros((V, 3, H, W), device="cuda")
         plan.forward(params, cams_dev, img)
         torch.cuda.synchronize()

@@ -479,3 +479,31 @@ def test_radix_ordering_equals_bucketed_ordering(cuda_lib, tile, persistent):
     assert np.array_equal(ia, ib)
     nrm, elt = rel_group_error(gb, ga)
     assert nrm < 1e-5 and elt < 1e-4, (nrm, elt)
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_backward_launch_configuration_is_its_own(cuda_lib, recompute):
+    """The backward compositing kernel may run its own pixels per thread and lane groups
+    (its warp regions do not depend on the forward's): gradients equal, up to atomic order
+    and FP32 rounding, those of the backward in the forward's configuration."""
+    vbm = cuda_lib
+    W, H, V = 96, 80, 2
+    P, cams, _ = scene(seed=15, n=2000, V=V, W=W, H=H)
+    params, cams_dev = to_device(P, cams)
+    w = torch.from_numpy(np.random.default_rng(6).standard_normal((V, 3, H, W)).astype(np.float32)).cuda()
+    flags = vbm.PLAN_PERSISTENT | (vbm.PLAN_RECOMPUTE if recompute else 0)
+    out = []
+    for bppt, bgl in ((0, 0), (2, 8), (1, 32)):
+        plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 22, flags=flags, tile_w=8, tile_h=8,
+                        pixels_per_thread=1, group_lanes=16, segment_len=64, bwd_pixels_per_thread=bppt,
+                        bwd_group_lanes=bgl)
+        img = torch.zeros((V, 3, H, W), device="cuda")
+        plan.forward(params, cams_dev, img)
+        grad = torch.zeros_like(params)
+        plan.backward(params, cams_dev, w, grad)
+        torch.cuda.synchronize()
+        out.append((img.cpu().numpy(), grad.cpu().numpy()))
+    for img, g in out[1:]:
+        assert np.array_equal(img, out[0][0])
+        nrm, elt = rel_group_error(g, out[0][1])
+        assert nrm < 1e-5 and elt < 1e-4, (nrm, elt)

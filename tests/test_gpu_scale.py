@@ -1,6 +1,7 @@
 """GPU parity at the full workload sizes, on samples the oracle can compute.
 
-  * c2 (256^3 turbulence, ~5e5 Gaussians, 16 views of 800x800), c3 (32 uneven
+  * c1 (128^3, ~1e5 Gaussians, 8 views of 512x512, the benchmark's launch
+    configuration), c2 (256^3 turbulence, ~5e5 Gaussians, 16 views of 800x800), c3 (32 uneven
     volumes, 128 views of 256x256, one batch) and c4 (512^3 shells, ~2.9e6
     Gaussians, 8 views of 1024x1024, compositing state recomputed in the
     backward): the FP64 oracle composites a random sample of tiles from the
@@ -39,10 +40,13 @@ def _sample_tiles(ranges, n, rng, longest=4):
     return np.unique(np.concatenate([pick, top[lengths[top] > 0]]))
 
 
-@pytest.mark.parametrize("key,tile,ppt,gl,recompute", [("c2", (16, 8), 1, 16, False),
-                                                        ("c3", (16, 16), 2, 8, False),
-                                                        ("c4", (8, 8), 1, 16, True)])
-def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
+@pytest.mark.parametrize("key,tile,ppt,gl,recompute,seg", [("c1", (8, 8), 2, 8, False, 128),
+                                                            ("c2", (16, 8), 1, 16, False, 0),
+                                                            ("c3", (16, 16), 2, 8, False, 0),
+                                                            ("c4", (8, 8), 1, 16, True, 0)])
+def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute, seg):
+    """c1 runs in the launch configuration the benchmark's autotuner picks for it (8x8
+    tiles, 2 pixels per thread, 8-lane groups, persistent, 128-entry backward segments)."""
     from paper_2601_09417_gb300.workloads import make_workload
     vbm = cuda_lib
     w = make_workload(key)
@@ -51,7 +55,8 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
     cams_dev = vbm.cameras_to_device(w.cam_records)
     flags = vbm.PLAN_PERSISTENT | (vbm.PLAN_RECOMPUTE if recompute else 0)
     plan = vbm.Plan(so, V, W, H, view_scene=w.view_scene, tile_w=tile[0], tile_h=tile[1], pixels_per_thread=ppt,
-                    group_lanes=gl, flags=flags, pair_capacity=vbm.default_pair_capacity(vbm.batch_items(so, V, w.view_scene)))
+                    group_lanes=gl, flags=flags, segment_len=seg,
+                    pair_capacity=vbm.default_pair_capacity(vbm.batch_items(so, V, w.view_scene)))
     bg = (0.05, 0.1, 0.2)
     img = torch.zeros((V, 3, H, W), device="cuda")
     plan.forward(w.params, cams_dev, img, bg=bg)
@@ -82,8 +87,8 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute):
     # --- sampled tiles: compact lists and the splats they reference
     rng = np.random.default_rng(7)
     sel = _sample_tiles(ranges, 48, rng)
-    if recompute:   # the sample holds lists the backward splits into segments (default 256 entries)
-        assert (ranges[sel, 1] - ranges[sel, 0]).max() > 256
+    if recompute or seg:   # the sample holds lists the backward splits into segments
+        assert (ranges[sel, 1] - ranges[sel, 0]).max() > (seg or 256)
     lists = [pair_item[ranges[t, 0]:ranges[t, 1]].cpu().numpy().astype(np.int64) for t in sel]
     used = np.unique(np.concatenate(lists))
     remap = {int(it): i for i, it in enumerate(used)}
