@@ -38,13 +38,13 @@ constexpr uint64_t kPadKey = ~0ull;
 // Longest-list-first order of the tiles for the persistent compositing
 // kernels: tiles are grouped by floor(log2(length + 1)), longest group first
 // (order within a group is arbitrary; each tile is processed independently).
-// The scan that produces the ranges also counts the groups, and the warp sort
-// places each tile into the order before it sorts; lanes of a warp with the
-// same group share one atomic.  The words q hold the two work-queue counters
+// A grid-stride kernel after the range scan counts the groups (and claims the
+// list segments), and the warp sort places each tile into the order before it
+// sorts; lanes of a warp with the same group share one atomic.  The words q hold the two work-queue counters
 // (q[0], q[1]), the group sizes (q[2 + g]) and the group cursors (q[34 + g]),
 // then the list-segment counters; the first scan kernel zeroes them.
 //
-// With list segments of length L (seg_len > 0), the scan also gives each tile
+// With list segments of length L (seg_len > 0), the counting also gives each tile
 // whose list is longer than L ceil(len / L) - 1 checkpoint slots (one per
 // segment boundary), plus one for its final per-pixel state when the plan
 // stores none (final_slot), and ceil(len / L) backward work units (tile,
@@ -120,20 +120,17 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_chunk_sums(const uint32_t
 // chunks before its own and of all chunks.  If the total exceeds the capacity
 // every range is empty, the pair count is 0, the counters are cleared and the
 // status records the size needed.  Also resets the long-list queue of the
-// sort and, with an ordering (o.q), counts the tiles of each length group and
-// claims the list segments.
+// sort.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict__ tile_count, int64_t n_tiles,
                                                             const int64_t *__restrict__ chunk_sums, int chunks,
                                                             int64_t capacity, int2 *__restrict__ ranges,
                                                             int64_t *__restrict__ n_pairs,
                                                             int64_t *__restrict__ status,
-                                                            uint32_t *__restrict__ long_count, TileOrder o)
+                                                            uint32_t *__restrict__ long_count)
 {
     __shared__ int64_t red[2][kScanThreads / 32];
     __shared__ int64_t warp_off[kScanThreads / 32];
-    __shared__ int hist[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
     int64_t before = 0, total = 0;
     for (int c = threadIdx.x; c < chunks; c += kScanThreads) {
         const int64_t v = chunk_sums[c];
@@ -196,17 +193,28 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict
         }
         run += c[it];
     }
-    if (!o.q) return;                                          // block-uniform
-    // length groups of this thread's tiles (segmented tiles are placed ahead
-    // of the groups), one shared atomic per group among a warp's lanes
-#pragma unroll
-    for (int it = 0; it < kScanItems; it++) {
-        const int64_t t = t0 + it;
-        const int len = overflow ? 0 : (int)c[it];
+}
+
+// Tile counts of each length group and the list-segment claims, one tile per
+// thread over a grid-stride loop (segmented tiles are placed ahead of the
+// groups); one shared atomic per group among a warp's lanes.  A kernel of its
+// own with a full grid: in the scan's few blocks, a thread's consecutive long
+// tiles would chain their claims' atomic round trips.
+__global__ void __launch_bounds__(kScanThreads) k_tile_group_count(const int2 *__restrict__ ranges, int64_t n_tiles,
+                                                                   TileOrder o)
+{
+    __shared__ int hist[32];
+    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n_tiles; t0 += stride) {   // uniform per block
+        const int64_t t = t0 + threadIdx.x;
         int g = 32 + lane;                                      // no group: unique per lane
         if (t < n_tiles) {
-            g = length_group(len);
-            if (o.ckpt_base && claim_segments(len, (int)t, o)) g = 32 + lane;
+            const int2 r = ranges[t];
+            g = length_group(r.y - r.x);
+            if (o.ckpt_base && claim_segments(r.y - r.x, (int)t, o)) g = 32 + lane;
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, g);
         if (g < 32 && lane == __ffs(peers) - 1) atomicAdd(&hist[g], __popc(peers));
@@ -1038,9 +1046,16 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     VBM_LAUNCH("tile_chunk_sums");
     k_tile_scan<<<chunks, kScanThreads, 0, st>>>(p->tile_count, n_tiles, b.chunk_sums, chunks,
                                                  p->desc.pair_capacity, p->ranges, p->d_n_pairs, p->d_status,
-                                                 b.long_count, o);
+                                                 b.long_count);
     VBM_LAUNCH("tile_scan");
     note_launches(2);
+    if (o.q) {
+        const int og = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 4,
+                                                                   (n_tiles + kScanThreads - 1) / kScanThreads));
+        k_tile_group_count<<<og, kScanThreads, 0, st>>>(p->ranges, n_tiles, o);
+        VBM_LAUNCH("tile_group_count");
+        note_launches(1);
+    }
     const bool radix = (p->desc.flags & VBM_PLAN_RADIX_SORT) != 0;
     if (radix) {
         vbm_status s = radix_order(p, vb, vc, n_tiles, st);
