@@ -21,13 +21,21 @@ __global__ void k_adam(float *__restrict__ P, const float *__restrict__ G, float
                        float lr0, float lr1, float lr2, float lr3, float lr4, float beta1, float beta2, float eps,
                        uint32_t *__restrict__ nonfinite)
 {
+    // the bias corrections are the same for every scalar: one thread of the
+    // block evaluates them
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) {
+        const int t = *step;
+        s_bc[0] = 1.f - powf(beta1, (float)t);
+        s_bc[1] = 1.f - powf(beta2, (float)t);
+    }
+    __syncthreads();
     const int row = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float lr = row < 3 ? lr0 : row < 6 ? lr1 : row < 10 ? lr2 : row < 11 ? lr3 : lr4;
-    const int t = *step;
-    const float bc1 = 1.f - powf(beta1, (float)t);
-    const float bc2 = 1.f - powf(beta2, (float)t);
+    const float bc1 = s_bc[0];
+    const float bc2 = s_bc[1];
     const int64_t e = row * stride + i;
     const float g = G[e];
     if (!isfinite(g)) {

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict
     const bool overflow = total > capacity;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *n_pairs = overflow ? 0 : total;
-        *long_count = 0;
+        long_count[0] = long_count[1] = 0;
         if (overflow) {
             atomicOr((unsigned long long *)&status[0], (unsigned long long)kStatusCapacity);
             atomicMax((unsigned long long *)&status[1], (unsigned long long)total);
@@ -389,6 +389,9 @@ __device__ __forceinline__ uint64_t *group_merge_sort(const uint64_t *__restrict
 constexpr int kSortWarps = 8;                                    // warps per block of k_tile_sort_warp
 constexpr int kWarpSortMax = 32 * kMergeE;                       // longest list one warp sorts
 constexpr int kWarpBufWords = padded(kWarpSortMax);
+constexpr int kMidSortThreads = 128;
+constexpr int kMidSortMax = kMidSortThreads * kMergeE;           // longest list a 128-thread block sorts
+constexpr int kMidBufWords = padded(kMidSortMax);
 constexpr int kBlockSortThreads = 512;
 constexpr int kBlockSortKeys = kBlockSortThreads * kMergeE;      // longest list sorted in shared memory
 constexpr int kBlockBufWords = padded(kBlockSortKeys);
@@ -396,7 +399,8 @@ constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
 
 // One warp per tile (grid-stride over the tiles): lists of up to 32 keys are
 // sorted in registers, up to kWarpSortMax by the warp's merge sort; longer
-// ones are queued for k_tile_sort_block.  Also clears every tile's counter
+// ones are queued for k_tile_sort_mid (up to kMidSortMax keys) or
+// k_tile_sort_block.  Also clears every tile's counter
 // for the next call and, with an ordering (o.q), first places every tile into
 // the longest-first order (the scan has counted the groups).  With sort = 0
 // (radix-sort ordering) it only clears the counters and places the tiles.
@@ -453,7 +457,12 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *
         if (n == 0 || !sort) continue;                          // radix ordering: counters only
         const uint64_t *keys = pair_key + r.x;
         if (n > kWarpSortMax) {
-            if (lane == 0) long_tiles[atomicAdd(long_count, 1u)] = (uint32_t)t;
+            // queued: lists up to kMidSortMax from the front for k_tile_sort_mid,
+            // longer ones from the back for k_tile_sort_block
+            if (lane == 0) {
+                if (n <= kMidSortMax) long_tiles[atomicAdd(&long_count[0], 1u)] = (uint32_t)t;
+                else long_tiles[n_tiles - 1 - atomicAdd(&long_count[1], 1u)] = (uint32_t)t;
+            }
         } else if (n <= 32) {
             const uint64_t a = warp_bitonic32(lane < n ? keys[lane] : kPadKey);
             if (lane < n) write_sorted(a, r.x + lane, (uint32_t)t, pair_tile, pair_item);
@@ -462,6 +471,29 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *
             for (int i = lane; i < n; i += 32) write_sorted(src[padded(i)], r.x + i, (uint32_t)t, pair_tile, pair_item);
             __syncwarp();
         }
+    }
+}
+
+// Lists of kWarpSortMax + 1 to kMidSortMax keys, one 128-thread block per list
+// at a time (grid-stride over the front of the queue): the block's merge sort
+// in shared memory, every thread with 8 keys of the padded list at most.
+__global__ void __launch_bounds__(kMidSortThreads) k_tile_sort_mid(const int2 *__restrict__ ranges,
+                                                                   const uint64_t *__restrict__ pair_key,
+                                                                   uint32_t *__restrict__ pair_tile,
+                                                                   uint32_t *__restrict__ pair_item,
+                                                                   const uint32_t *__restrict__ long_tiles,
+                                                                   const uint32_t *__restrict__ long_count)
+{
+    __shared__ uint64_t buf[2][kMidBufWords];
+    const uint32_t n_mid = long_count[0];
+    const int t = threadIdx.x;
+    for (uint32_t q = blockIdx.x; q < n_mid; q += gridDim.x) {
+        const uint32_t tile = long_tiles[q];
+        const int2 r = ranges[tile];
+        const int n = r.y - r.x;
+        const uint64_t *src = group_merge_sort<kMidSortThreads, true>(pair_key + r.x, n, buf[0], buf[1], t);
+        for (int i = t; i < n; i += kMidSortThreads) write_sorted(src[padded(i)], r.x + i, tile, pair_tile, pair_item);
+        __syncthreads();
     }
 }
 
@@ -514,14 +546,15 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
                                                                        uint32_t *__restrict__ pair_tile,
                                                                        uint32_t *__restrict__ pair_item,
                                                                        const uint32_t *__restrict__ long_tiles,
-                                                                       const uint32_t *__restrict__ long_count)
+                                                                       const uint32_t *__restrict__ long_count,
+                                                                       int64_t n_tiles)
 {
     extern __shared__ uint64_t smem_keys[];
     uint64_t *s0 = smem_keys, *s1 = smem_keys + kBlockBufWords;
-    const uint32_t n_long = *long_count;
+    const uint32_t n_long = long_count[1];
     const int t = threadIdx.x;
     for (uint32_t q = blockIdx.x; q < n_long; q += gridDim.x) {
-        const uint32_t tile = long_tiles[q];
+        const uint32_t tile = long_tiles[n_tiles - 1 - q];
         const int2 r = ranges[tile];
         const int64_t n = r.y - r.x;
         uint64_t *g = pair_key + r.x;
@@ -1085,10 +1118,13 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     VBM_LAUNCH("tile_sort_warp");
     note_launches(1);
     if (!radix) {
+        k_tile_sort_mid<<<num_sms() * 8, kMidSortThreads, 0, st>>>(p->ranges, p->pair_key, p->pair_tile,
+                                                                    p->pair_item, b.long_tiles, b.long_count);
+        VBM_LAUNCH("tile_sort_mid");
         k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
-            p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);
+            p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count, n_tiles);
         VBM_LAUNCH("tile_sort_block");
-        note_launches(1);
+        note_launches(2);
     }
     return VBM_OK;
 }

@@ -354,13 +354,14 @@ constexpr int kDefaultSegmentLen = 256;
 constexpr int64_t kCheckpointPairsPerItem = 2;
 constexpr int64_t kCheckpointBytes = 1ll << 30;
 
-// Scratch of the binning: per-chunk sums of the tile counts and the list of
-// tiles too long for one warp's sort.
+// Scratch of the binning: per-chunk sums of the tile counts and the lists of
+// tiles too long for one warp's sort (mid-size from the front, the longest
+// from the back).
 struct BinScratch {
     int64_t *chunk_sums = nullptr;  // [chunks]
     int chunks = 0;                 // ceil(max tiles / tiles per chunk)
     uint32_t *long_tiles = nullptr; // [max tiles]
-    uint32_t *long_count = nullptr; // [1]
+    uint32_t *long_count = nullptr; // [2] queued lists for the mid and the block sort
 };
 int bin_chunks(int64_t n_tiles);
 cudaError_t binning_setup();   // once per plan, before any capture: kernel attributes
