@@ -218,8 +218,8 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     }
     p->bin_scratch.chunks = bin_chunks(tiles);
     ALLOC(p->bin_scratch.chunk_sums, p->bin_scratch.chunks);
-    ALLOC(p->bin_scratch.long_tiles, tiles);
-    ALLOC(p->bin_scratch.long_count, 2);
+    ALLOC(p->bin_scratch.long_tiles, 2 * tiles);
+    ALLOC(p->bin_scratch.long_count, 3);
     ALLOC(p->d_n_pairs, 1);
     ALLOC(p->d_status, 2);
 #undef ALLOC

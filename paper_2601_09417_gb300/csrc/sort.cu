@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(uint32_t *__restrict
     const bool overflow = total > capacity;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *n_pairs = overflow ? 0 : total;
-        long_count[0] = long_count[1] = 0;
+        long_count[0] = long_count[1] = long_count[2] = 0;
         if (overflow) {
             atomicOr((unsigned long long *)&status[0], (unsigned long long)kStatusCapacity);
             atomicMax((unsigned long long *)&status[1], (unsigned long long)total);
@@ -398,9 +398,9 @@ constexpr int kBlockBufWords = padded(kBlockSortKeys);
 constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
 
 // One warp per tile (grid-stride over the tiles): lists of up to 32 keys are
-// sorted in registers, up to kWarpSortMax by the warp's merge sort; longer
-// ones are queued for k_tile_sort_mid (up to kMidSortMax keys) or
-// k_tile_sort_block.  Also clears every tile's counter
+// sorted in registers; longer ones are queued for k_tile_sort_medium (up to
+// kWarpSortMax keys), k_tile_sort_mid (up to kMidSortMax) or k_tile_sort_block,
+// so that each of those kernels takes lists of similar cost.  Also clears every tile's counter
 // for the next call and, with an ordering (o.q), first places every tile into
 // the longest-first order (the scan has counted the groups).  With sort = 0
 // (radix-sort ordering) it only clears the counters and places the tiles.
@@ -413,7 +413,6 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *
                                                                     uint32_t *__restrict__ long_count, TileOrder o,
                                                                     int sort)
 {
-    __shared__ uint64_t buf[kSortWarps][2][kWarpBufWords];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (o.q) {                                                  // grid-uniform
         __shared__ int base[32];
@@ -466,11 +465,33 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_warp(const int2 *
         } else if (n <= 32) {
             const uint64_t a = warp_bitonic32(lane < n ? keys[lane] : kPadKey);
             if (lane < n) write_sorted(a, r.x + lane, (uint32_t)t, pair_tile, pair_item);
-        } else {
-            const uint64_t *src = group_merge_sort<32, false>(keys, n, buf[w][0], buf[w][1], lane);
-            for (int i = lane; i < n; i += 32) write_sorted(src[padded(i)], r.x + i, (uint32_t)t, pair_tile, pair_item);
-            __syncwarp();
+        } else if (lane == 0) {   // 33 to kWarpSortMax keys: queued for k_tile_sort_medium
+            long_tiles[n_tiles + atomicAdd(&long_count[2], 1u)] = (uint32_t)t;
         }
+    }
+}
+
+// Lists of 33 to kWarpSortMax keys, one warp per list (grid-stride over the
+// queue k_tile_sort_warp filled): the warp's merge sort in shared memory.
+__global__ void __launch_bounds__(kSortWarps * 32) k_tile_sort_medium(const int2 *__restrict__ ranges,
+                                                                      int64_t n_tiles,
+                                                                      const uint64_t *__restrict__ pair_key,
+                                                                      uint32_t *__restrict__ pair_tile,
+                                                                      uint32_t *__restrict__ pair_item,
+                                                                      const uint32_t *__restrict__ long_tiles,
+                                                                      const uint32_t *__restrict__ long_count)
+{
+    __shared__ uint64_t buf[kSortWarps][2][kWarpBufWords];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t n_med = long_count[2];
+    const uint32_t warps = gridDim.x * kSortWarps;
+    for (uint32_t q = blockIdx.x * kSortWarps + w; q < n_med; q += warps) {
+        const uint32_t tile = long_tiles[n_tiles + q];
+        const int2 r = ranges[tile];
+        const int n = r.y - r.x;
+        const uint64_t *src = group_merge_sort<32, false>(pair_key + r.x, n, buf[w][0], buf[w][1], lane);
+        for (int i = lane; i < n; i += 32) write_sorted(src[padded(i)], r.x + i, tile, pair_tile, pair_item);
+        __syncwarp();
     }
 }
 
@@ -1118,6 +1139,16 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     VBM_LAUNCH("tile_sort_warp");
     note_launches(1);
     if (!radix) {
+        static int medium_per_sm = 0;
+        if (medium_per_sm == 0) {
+            VBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&medium_per_sm, k_tile_sort_medium,
+                                                                   kSortWarps * 32, 0));
+            medium_per_sm = std::max(medium_per_sm, 1);
+        }
+        k_tile_sort_medium<<<num_sms() * medium_per_sm, kSortWarps * 32, 0, st>>>(
+            p->ranges, n_tiles, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count);
+        VBM_LAUNCH("tile_sort_medium");
+        note_launches(1);
         k_tile_sort_mid<<<num_sms() * 8, kMidSortThreads, 0, st>>>(p->ranges, p->pair_key, p->pair_tile,
                                                                     p->pair_item, b.long_tiles, b.long_count);
         VBM_LAUNCH("tile_sort_mid");

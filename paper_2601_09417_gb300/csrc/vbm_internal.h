@@ -360,8 +360,8 @@ constexpr int64_t kCheckpointBytes = 1ll << 30;
 struct BinScratch {
     int64_t *chunk_sums = nullptr;  // [chunks]
     int chunks = 0;                 // ceil(max tiles / tiles per chunk)
-    uint32_t *long_tiles = nullptr; // [max tiles]
-    uint32_t *long_count = nullptr; // [2] queued lists for the mid and the block sort
+    uint32_t *long_tiles = nullptr; // [2 max tiles]: mid and longest lists, then medium ones
+    uint32_t *long_count = nullptr; // [3] queued lists for the mid, the block and the medium sort
 };
 int bin_chunks(int64_t n_tiles);
 cudaError_t binning_setup();   // once per plan, before any capture: kernel attributes
