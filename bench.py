@@ -149,10 +149,15 @@ def time_steps(fn, steps, flush):
 
 
 def kernel_source_hash():
+    """Hash of the compositing kernels' code (raster.cu and vbm_internal.h with // comments
+    and blank lines removed, so that a comment edit keeps a capture of unchanged code)."""
     h = hashlib.sha256()
     for name in ("raster.cu", "vbm_internal.h"):
-        with open(os.path.join(ROOT, "paper_2601_09417_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2601_09417_gb300", "csrc", name), encoding="utf-8") as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -37,7 +37,15 @@
 //
 // Launch: blocks of kWarps warps; each warp takes work items (tile, region)
 // either by its global warp index or, persistent, from an atomic queue whose
-// items follow the tiles' longest-list-first order.
+// items follow the tiles' longest-list-first order.  In persistent plans a
+// tile whose list is longer than the segment length L is walked by the
+// backward as independent units (tile, segment, region) of L entries, taken
+// ahead of the whole tiles: the forward stores, per pixel still compositing
+// at each segment boundary, the transmittance and the colour still to come
+// (and, in recompute plans, the tile's final per-pixel state), from which a
+// unit starts its walk; one warp's walk of a very long list otherwise
+// outlasted the rest of the launch.  The backward may run its own pixels per
+// thread and lane groups: its regions are independent of the forward's.
 #include "vbm_internal.h"
 
 namespace vbm {

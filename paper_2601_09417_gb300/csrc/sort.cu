@@ -13,10 +13,14 @@
 // The result is unique, so it equals the oracle's (tile, depth, index) sort
 // bit for bit however the atomics interleave.
 //
-// Lists of up to 256 keys are sorted by one warp in registers (bitonic
-// network, keys i = 32 r + lane); longer lists go to a queue that blocks sort
-// with a bitonic network in shared memory (4096 keys), or, beyond that, with
-// the network's long-distance steps in global memory.
+// The kernel that walks every tile sorts lists of up to 32 keys with a warp's
+// bitonic network in registers and queues the longer ones by size, so that
+// each later kernel takes lists of similar cost: up to 256 keys a warp's
+// merge sort in shared memory (one warp per list), up to 1024 a 128-thread
+// block's, up to 4096 a 512-thread block's; longer lists run the bitonic
+// network with its long-distance steps in global memory.  A plan option
+// (VBM_PLAN_RADIX_SORT) orders the pairs by device LSD radix sorts instead,
+// with the same result.
 //
 // Compared with sorting all pairs on a (tile | depth) key, nothing is sorted
 // globally: the pair array is written once by the placement and once by the
