@@ -1,7 +1,8 @@
 // Fused Adam update of the Gaussian parameters (Sec. 5.2 uses Adam).
 //
-// One thread per scalar of P[14][stride] (first n columns), reading p, g, m,
-// v and writing p, m, v: 28 bytes of HBM traffic per scalar, coalesced.  The
+// Updates the first n columns of P[14][stride], reading p, g, m, v and
+// writing p, m, v: 28 bytes of HBM traffic per scalar, coalesced; four
+// scalars per thread when the rows are packed (stride == n), one otherwise.  The
 // step counter lives on the device so the update can be replayed from a CUDA
 // graph: a one-thread kernel increments it, the update reads it.
 #include <cmath>
@@ -16,39 +17,113 @@ __global__ void k_step_inc(int32_t *step)
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
 }
 
-__global__ void k_adam(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
-                       float *__restrict__ V, int64_t n, int64_t stride, const int32_t *__restrict__ step,
-                       float lr0, float lr1, float lr2, float lr3, float lr4, float beta1, float beta2, float eps,
-                       uint32_t *__restrict__ nonfinite)
+// One scalar's update (p, m, v in place); false when g is not finite (nothing
+// is changed).
+__device__ __forceinline__ bool adam_elem(float &p, float &m, float &v, float g, float lr, float beta1,
+                                          float beta2, float eps, float bc1, float bc2)
 {
-    // the bias corrections are the same for every scalar: one thread of the
-    // block evaluates them
-    __shared__ float s_bc[2];
+    if (!isfinite(g)) return false;
+    m = beta1 * m + (1.f - beta1) * g;
+    v = beta2 * v + (1.f - beta2) * g * g;
+    const float mhat = m / bc1;
+    const float vhat = v / bc2;
+    p -= lr * mhat / (sqrtf(vhat) + eps);
+    return true;
+}
+
+__device__ __forceinline__ float row_lr(int row, float lr0, float lr1, float lr2, float lr3, float lr4)
+{
+    return row < 3 ? lr0 : row < 6 ? lr1 : row < 10 ? lr2 : row < 11 ? lr3 : lr4;
+}
+
+// the bias corrections are the same for every scalar: one thread of the block
+// evaluates them
+__device__ __forceinline__ void bias_corrections(float *s_bc, const int32_t *step, float beta1, float beta2)
+{
     if (threadIdx.x == 0) {
         const int t = *step;
         s_bc[0] = 1.f - powf(beta1, (float)t);
         s_bc[1] = 1.f - powf(beta2, (float)t);
     }
     __syncthreads();
+}
+
+// Rows packed back to back (stride == n): the 14 n scalars are one array,
+// four per thread with 16-byte loads and stores; each scalar takes its own
+// row's learning rate (a quad may cross rows).
+__global__ void k_adam_flat(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
+                            float *__restrict__ V, int64_t n, const int32_t *__restrict__ step, float lr0, float lr1,
+                            float lr2, float lr3, float lr4, float beta1, float beta2, float eps,
+                            uint32_t *__restrict__ nonfinite)
+{
+    __shared__ float s_bc[2];
+    bias_corrections(s_bc, step, beta1, beta2);
+    const int64_t total = 14 * n;
+    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e0 >= total) return;
+    const float bc1 = s_bc[0];
+    const float bc2 = s_bc[1];
+    int row = (int)(e0 / n);
+    int64_t row_end = (int64_t)(row + 1) * n;
+    uint32_t bad = 0;
+    if (e0 + 4 <= total) {
+        float4 g4 = *reinterpret_cast<const float4 *>(G + e0);
+        float4 p4 = *reinterpret_cast<const float4 *>(P + e0);
+        float4 m4 = *reinterpret_cast<const float4 *>(M + e0);
+        float4 v4 = *reinterpret_cast<const float4 *>(V + e0);
+        float *g = &g4.x, *p = &p4.x, *m = &m4.x, *v = &v4.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            while (e0 + k >= row_end) {
+                ++row;
+                row_end += n;
+            }
+            bad += !adam_elem(p[k], m[k], v[k], g[k], row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, bc1,
+                              bc2);
+        }
+        *reinterpret_cast<float4 *>(P + e0) = p4;
+        *reinterpret_cast<float4 *>(M + e0) = m4;
+        *reinterpret_cast<float4 *>(V + e0) = v4;
+    } else {
+        for (int64_t e = e0; e < total; ++e) {
+            while (e >= row_end) {
+                ++row;
+                row_end += n;
+            }
+            float p = P[e], m = M[e], v = V[e];
+            if (!adam_elem(p, m, v, G[e], row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, bc1, bc2)) {
+                ++bad;
+                continue;
+            }
+            P[e] = p;
+            M[e] = m;
+            V[e] = v;
+        }
+    }
+    if (bad && nonfinite) atomicAdd(nonfinite, bad);
+}
+
+// Rows with padding (stride > n) or unaligned pointers: one scalar per
+// thread, one grid row per parameter row.
+__global__ void k_adam_rows(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
+                            float *__restrict__ V, int64_t n, int64_t stride, const int32_t *__restrict__ step,
+                            float lr0, float lr1, float lr2, float lr3, float lr4, float beta1, float beta2, float eps,
+                            uint32_t *__restrict__ nonfinite)
+{
+    __shared__ float s_bc[2];
+    bias_corrections(s_bc, step, beta1, beta2);
     const int row = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float lr = row < 3 ? lr0 : row < 6 ? lr1 : row < 10 ? lr2 : row < 11 ? lr3 : lr4;
-    const float bc1 = s_bc[0];
-    const float bc2 = s_bc[1];
     const int64_t e = row * stride + i;
-    const float g = G[e];
-    if (!isfinite(g)) {
+    float p = P[e], m = M[e], v = V[e];
+    if (!adam_elem(p, m, v, G[e], row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, s_bc[0], s_bc[1])) {
         if (nonfinite) atomicAdd(nonfinite, 1u);
         return;
     }
-    const float m = beta1 * M[e] + (1.f - beta1) * g;
-    const float v = beta2 * V[e] + (1.f - beta2) * g * g;
+    P[e] = p;
     M[e] = m;
     V[e] = v;
-    const float mhat = m / bc1;
-    const float vhat = v / bc2;
-    P[e] -= lr * mhat / (sqrtf(vhat) + eps);
 }
 
 }  // namespace
@@ -60,9 +135,17 @@ vbm_status adam_step(float *P, const float *G, float *M, float *V, int64_t n, in
     VBM_LAUNCH("adam_step_inc");
     note_launches(1);
     if (n == 0) return VBM_OK;
-    dim3 grid((unsigned)((n + 255) / 256), 14);
-    k_adam<<<grid, 256, 0, st>>>(P, G, M, V, n, stride, step, lrs[0], lrs[1], lrs[2], lrs[3], lrs[4], beta1, beta2,
-                                 eps, nonfinite);
+    const bool flat = stride == n && ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) |
+                                       reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(V)) & 15) == 0;
+    if (flat) {
+        const int64_t quads = (14 * n + 3) / 4;
+        k_adam_flat<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(P, G, M, V, n, step, lrs[0], lrs[1], lrs[2],
+                                                                     lrs[3], lrs[4], beta1, beta2, eps, nonfinite);
+    } else {
+        dim3 grid((unsigned)((n + 255) / 256), 14);
+        k_adam_rows<<<grid, 256, 0, st>>>(P, G, M, V, n, stride, step, lrs[0], lrs[1], lrs[2], lrs[3], lrs[4], beta1,
+                                          beta2, eps, nonfinite);
+    }
     VBM_LAUNCH("adam");
     note_launches(1);
     return VBM_OK;

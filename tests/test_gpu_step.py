@@ -39,10 +39,13 @@ def test_loss_and_gradient(cuda_lib, shape):
     assert abs(L2.item() - L.item()) <= 1e-12 * max(1.0, L.item())
 
 
-def test_adam_matches_oracle(cuda_lib):
+@pytest.mark.parametrize("n, stride", [(1000, 1003), (1001, 1001), (513, 513), (3, 3)])
+def test_adam_matches_oracle(cuda_lib, n, stride):
+    """Padded rows (stride > n): one scalar per thread and row; packed rows: four scalars per
+    thread over the flat array, quads crossing rows, a ragged last quad (14 n not a multiple
+    of 4), and n < 4 (a quad spanning three rows)."""
     vbm = cuda_lib
     rng = np.random.default_rng(3)
-    n, stride = 1000, 1003
     P = rng.standard_normal((14, stride)).astype(np.float32)
     lrs = oadam.default_lrs(64.0)
     Pt = torch.from_numpy(P.copy()).cuda()
@@ -61,11 +64,22 @@ def test_adam_matches_oracle(cuda_lib):
     assert np.array_equal(out[:, n:], P[:, n:])      # columns beyond n untouched
     # a non-finite gradient element is counted and leaves its parameter alone
     G = np.zeros((14, stride), dtype=np.float32)
-    G[2, 5] = np.nan
+    G[2, 5 % n] = np.nan
+    G[3, 6 % n] = np.inf
+    G[4, 7 % n] = -np.inf
+    G[13, n - 1] = np.nan
     before = Pt.cpu().numpy()
     vbm.adam(Pt, torch.from_numpy(G).cuda(), m, v, n, step, lrs, nonfinite=bad)
     torch.cuda.synchronize()
-    assert bad.item() == 1 and Pt.cpu().numpy()[2, 5] == before[2, 5]
+    after = Pt.cpu().numpy()
+    bad_at = ((2, 5 % n), (3, 6 % n), (4, 7 % n), (13, n - 1))
+    assert bad.item() == 4
+    for r, c in bad_at:
+        assert after[r, c] == before[r, c]
+    ok = np.ones((14, n), dtype=bool)
+    for r, c in bad_at:
+        ok[r, c] = False
+    assert np.all(after[:, :n][ok] != before[:, :n][ok])   # finite scalars of the same quads move
 
 
 def test_gradient_central_differences(cuda_lib):
