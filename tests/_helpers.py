@@ -1,9 +1,28 @@
-"""Shared helpers of the GPU parity tests: seeded scenes and device-buffer readers."""
+"""Shared helpers of the parity tests: seeded scenes, device-buffer readers and the
+oracle's transition banks (cached: the five-level bior4.4 bank takes ~25 s)."""
+
+import functools
 
 import numpy as np
 
 from vbm_inputs import gaussians_in_view, orbit_cameras
 from vbm_inputs.cameras import camera_array, cameras_as_float32
+
+@functools.lru_cache(maxsize=None)
+def _oracle_bank_cached(levels, wavelet):
+    from oracle import bank as obank
+    return tuple(obank.build_bank(levels, "bior4.4" if wavelet == 0 else "haar"))
+
+
+def oracle_bank(levels, wavelet=0, ablation=0):
+    """The oracle's FP64 bank for `levels` (wavelet 0 bior4.4, 1 Haar); ablation flags
+    1 (isotropic covariance) and 2 (unit weight) as in vbm_bank_ablate."""
+    from oracle import bank as obank
+    entries = [dict(e) for e in _oracle_bank_cached(levels, wavelet)]
+    if ablation:
+        entries = obank.ablate(entries, isotropic=bool(ablation & 1), unit_weight=bool(ablation & 2))
+    return entries
+
 
 def read_device(ptr, shape, dtype):
     """Copy device memory at a raw pointer into a numpy array."""

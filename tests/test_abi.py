@@ -57,11 +57,13 @@ def test_host_argument_validation(lib):
     assert "levels" in lib.load().vbm_last_error().decode()
 
 
-@pytest.mark.parametrize("levels,wavelet", [(2, 0), (1, 1), (3, 1)])
+@pytest.mark.parametrize("levels,wavelet", [(2, 0), (4, 0), (5, 0), (1, 1), (3, 1), (5, 1)])
 def test_host_bank_matches_oracle(lib, levels, wavelet):
-    from oracle import bank as obank
+    """Every entry of the library's bank against the oracle's, up to the five bior4.4
+    levels of the 512^3 workload (levels 3 and up take the oracle's separable kernel)."""
+    from _helpers import oracle_bank
     got = lib.bank_to_dicts(lib.bank_build(levels, wavelet))
-    ref = obank.build_bank(levels, "bior4.4" if wavelet == 0 else "haar")
+    ref = oracle_bank(levels, wavelet)
     assert len(got) == len(ref) == 7 * levels + 1
     for a, b in zip(got, ref):
         assert (a["j"], tuple(a["o"])) == (b["j"], tuple(b["o"]))
@@ -69,18 +71,19 @@ def test_host_bank_matches_oracle(lib, levels, wavelet):
         assert np.allclose(a["cov"], b["cov"], atol=1e-10)
         assert abs(a["w"] - b["w"]) < 1e-10 * b["w"]
         assert np.allclose(a["log_scale"], b["log_scale"], atol=1e-6)
+        assert np.allclose(a["quat"], b["quat"], atol=1e-7)
 
 
 @pytest.mark.parametrize("wavelet,flags", [(0, 1), (0, 2), (1, 3)])
 def test_host_bank_ablation_matches_oracle(lib, wavelet, flags):
-    """vbm_bank_ablate (host only) against the oracle's ablation of the library's own bank."""
-    from oracle import bank as obank
+    """vbm_bank_ablate (host only) against the oracle's ablation of its own bank."""
+    from _helpers import oracle_bank
     bank = lib.bank_build(3, wavelet)
-    ref = obank.ablate(lib.bank_to_dicts(bank), isotropic=bool(flags & 1), unit_weight=bool(flags & 2))
+    ref = oracle_bank(3, wavelet, ablation=flags)
     got = lib.bank_to_dicts(lib.bank_ablate(bank, flags))
     for a, b in zip(got, ref):
-        assert np.allclose(a["u"], b["u"], atol=0) and np.allclose(a["cov"], b["cov"], rtol=1e-12, atol=1e-14)
-        assert abs(a["w"] - b["w"]) <= 1e-12 * abs(b["w"])
+        assert np.allclose(a["u"], b["u"], atol=1e-9) and np.allclose(a["cov"], b["cov"], rtol=1e-10, atol=1e-10)
+        assert abs(a["w"] - b["w"]) <= 1e-10 * abs(b["w"])
         assert np.allclose(a["log_scale"], b["log_scale"], atol=1e-6)
         assert np.allclose(a["quat"], b["quat"], atol=1e-7)
     with pytest.raises(lib.VbmError) as e:

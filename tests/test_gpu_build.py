@@ -5,8 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import read_device
-from oracle import bank as obank
+from _helpers import oracle_bank, read_device
 from oracle import dvr as odvr
 from oracle.dwt import dwt3d, subband_slices, subbands
 from oracle.filters import filter_bank
@@ -50,25 +49,18 @@ def test_dwt3d(cuda_lib, wavelet, levels, dims):
 
 @pytest.mark.parametrize("levels,wavelet", [(3, 0), (5, 0), (2, 1)])
 def test_bank_matches_oracle(cuda_lib, levels, wavelet):
-    """Host FP64 bank of the library against the oracle's (levels <= 3 use the oracle's 3D IDWT)."""
-    if levels == 5:
-        pytest.importorskip("numpy")
+    """Host FP64 bank of the library against the oracle's, every entry (five levels:
+    the 512^3 workload's bank)."""
     lib_bank = cuda_lib.bank_to_dicts(cuda_lib.bank_build(levels, wavelet))
-    ref = obank.build_bank(min(levels, 3) if levels == 5 else levels, "bior4.4" if wavelet == 0 else "haar")
-    by_key = {(e["j"], tuple(e["o"])): e for e in ref}
-    assert len(lib_bank) == 7 * levels + 1
-    matched = 0
-    for e in lib_bank:
-        r = by_key.get((e["j"], tuple(e["o"])))
-        if r is None:
-            continue
-        matched += 1
+    ref = oracle_bank(levels, wavelet)
+    assert len(lib_bank) == len(ref) == 7 * levels + 1
+    for e, r in zip(lib_bank, ref):
+        assert (e["j"], tuple(e["o"])) == (r["j"], tuple(r["o"]))
         assert np.allclose(e["u"], r["u"], atol=1e-9)
         assert np.allclose(e["cov"], r["cov"], atol=1e-9 * np.abs(r["cov"]).max())
         assert abs(e["w"] - r["w"]) < 1e-9 * r["w"]
         assert np.allclose(e["log_scale"], r["log_scale"], atol=1e-6)
         assert np.allclose(e["quat"], r["quat"], atol=1e-6)
-    assert matched >= 7 * min(levels, 3)
 
 
 def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0, knots=None):
@@ -87,24 +79,27 @@ def _build(vbm, F, J, K_tot, wavelet=0, energy_comp=True, ablation=0, knots=None
             keep.cpu().numpy().reshape(F.shape).astype(bool), bank)
 
 
-@pytest.mark.parametrize("G,J,K_tot,seed,ablation,mode", [(32, 2, 4096, 0, 0, None), (64, 3, 20000, 1, 0, None),
-                                                           (32, 2, 4096, 0, 1, None), (32, 2, 4096, 0, 2, None),
-                                                           (32, 2, 4096, 0, 0, 1), (64, 3, 20000, 1, 0, 3)])
-def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation, mode):
-    """vbm_build against the oracle: pyramid, kept indices (bit-exact), Gaussians; also
-    with the ablated banks of Sec. 5.4 (isotropic covariance, unit weight) and with two of
-    the TF modes of Sec. 4.4 (non-zero over one value interval only)."""
+@pytest.mark.parametrize("G,J,K_tot,seed,ablation,mode,wavelet", [
+    (32, 2, 4096, 0, 0, None, 0), (64, 3, 20000, 1, 0, None, 0),
+    (32, 2, 4096, 0, 1, None, 0), (32, 2, 4096, 0, 2, None, 0),
+    (32, 2, 4096, 0, 0, 1, 0), (64, 3, 20000, 1, 0, 3, 0),
+    (32, 2, 4096, 0, 0, None, 1), (64, 3, 20000, 1, 0, None, 1), (64, 3, 20000, 1, 3, None, 1)])
+def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation, mode, wavelet):
+    """vbm_build against the oracle: pyramid, kept indices (bit-exact), Gaussians mapped
+    with the oracle's own bank; also with the ablated banks of Sec. 5.4 (isotropic
+    covariance, unit weight), with the Haar basis of the same ablation study, and with two
+    of the TF modes of Sec. 4.4 (non-zero over one value interval only)."""
     from vbm_inputs import tf_mode
     F = blob_volume(G, 4 if G == 32 else 12, seed=seed)
     knots = None if mode is None else tf_mode(mode)
-    P, count, A_gpu, keep_gpu, bank = _build(cuda_lib, F, J, K_tot, ablation=ablation, knots=knots)
+    P, count, A_gpu, keep_gpu, bank = _build(cuda_lib, F, J, K_tot, wavelet=wavelet, ablation=ablation, knots=knots)
     # 1. coefficient pyramid vs the FP64 oracle pipeline (TF + DWT)
     if knots is None:
         x, rgba = _tf32()
     else:     # the library holds the knots in float32
         x, rgba = (k.astype(np.float32).astype(np.float64) for k in knots)
     RF = apply_tf_vectorised(F.astype(np.float64), x, rgba)
-    fb = filter_bank(0)
+    fb = filter_bank(wavelet)
     A_ref = np.stack([dwt3d(RF[..., c], J, fb) for c in range(4)])
     assert np.abs(A_gpu - A_ref).max() < 2e-6 * np.abs(A_ref).max()
     # 2. selection: same decisions in the same precision (float32) on the GPU's pyramid
@@ -116,8 +111,8 @@ def test_build_matches_oracle(cuda_lib, G, J, K_tot, seed, ablation, mode):
         assert 0.5 * K_tot < count < 1.5 * K_tot
     else:
         assert count > 100
-    # 3. mapping on the GPU's pyramid and masks with the library's bank
-    ref = map_coefficients(A_gpu.astype(np.float64), masks, J, cuda_lib.bank_to_dicts(bank))
+    # 3. mapping on the GPU's pyramid and masks with the oracle's own bank
+    ref = map_coefficients(A_gpu.astype(np.float64), masks, J, oracle_bank(J, wavelet, ablation))
     assert ref.shape == P.shape
     assert np.allclose(P[0:3], ref[0:3], atol=1e-5 * G)
     assert np.allclose(P[3:10], ref[3:10], atol=1e-6)

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import rel_group_error
+from _helpers import oracle_bank, rel_group_error
 from oracle import raster as oraster
 
 pytestmark = pytest.mark.gpu
@@ -143,7 +143,8 @@ def test_build_full_size(cuda_lib, key, which):
     oracle's build: pyramid to 2e-6 relative to its largest coefficient for up to three
     levels and 1e-6 per level beyond (each level's three separable 9-tap passes round in
     FP32 at about 3e-7), kept indices bit-exact (decisions in float32 on the GPU's
-    pyramid), Gaussians to the same bounds as the small build test."""
+    pyramid), Gaussians, mapped with the oracle's own bank, to the same bounds as the
+    small build test."""
     from oracle.dwt import dwt3d, subband_slices, subbands
     from oracle.filters import filter_bank
     from oracle.mapping import map_coefficients, select_all
@@ -176,7 +177,7 @@ def test_build_full_size(cuda_lib, key, which):
     for (j, o), m in zip(subbands(J), masks):
         assert np.array_equal(keep_gpu[subband_slices(F.shape, j, o)], m), (j, o)
     assert count == sum(int(m.sum()) for m in masks)
-    ref = map_coefficients(A_gpu.astype(np.float64), masks, J, vbm.bank_to_dicts(bank))
+    ref = map_coefficients(A_gpu.astype(np.float64), masks, J, oracle_bank(J, 0))
     G = F.shape[0]
     assert ref.shape == P.shape
     assert np.allclose(P[0:3], ref[0:3], atol=1e-5 * G)
