@@ -18,6 +18,8 @@
 // deterministic and needs no launch of its own.
 #include <cmath>
 
+#include <mutex>
+
 #include "vbm_internal.h"
 
 namespace vbm {
@@ -316,11 +318,19 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
     }
 }
 
-bool g_win_ready = false;
+// The window lives in __constant__ memory, which each device holds separately:
+// the upload is tracked per device (the first loss call on a device makes it).
+constexpr int kMaxWinDevices = 64;
+std::mutex g_win_mutex;
+bool g_win_ready[kMaxWinDevices] = {};
 
 vbm_status ensure_window()
 {
-    if (g_win_ready) return VBM_OK;
+    int dev = 0;
+    VBM_CUDA(cudaGetDevice(&dev));
+    VBM_ARG(dev >= 0 && dev < kMaxWinDevices, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_win_mutex);
+    if (g_win_ready[dev]) return VBM_OK;
     double g[kWin], s = 0.0;
     for (int i = 0; i < kWin; i++) {
         const double d = i - kHalf;
@@ -330,7 +340,7 @@ vbm_status ensure_window()
     float w[kWin];
     for (int i = 0; i < kWin; i++) w[i] = (float)(g[i] / s);
     VBM_CUDA(cudaMemcpyToSymbol(c_win, w, sizeof(w)));
-    g_win_ready = true;
+    g_win_ready[dev] = true;
     return VBM_OK;
 }
 
@@ -349,9 +359,16 @@ size_t loss_workspace_bytes(int n_images, int H, int W)
     return bytes + loss_blocks(n_images, H, W) * 2 * sizeof(double);
 }
 
+int loss_max_images()
+{
+    return 65535 / 3;     // one grid z-slice per (image, channel)
+}
+
 vbm_status loss_fwd_bwd(const float *img, const float *target, int n_images, int H, int W, float lambda,
                         double scale, double *loss, int accumulate, float *dimg, void *ws, cudaStream_t st)
 {
+    VBM_ARG(n_images <= loss_max_images(), "loss batch of more than 21845 images (3 channels each exceed the "
+                                           "grid's 65535 z-slices): split it and use accumulate");
     vbm_status s = ensure_window();
     if (s != VBM_OK) return s;
     const size_t n = (size_t)n_images * 3 * H * W;

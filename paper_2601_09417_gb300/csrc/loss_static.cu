@@ -11,12 +11,14 @@
 //
 // The array's name is a host-side stand-in in host code, not a device
 // address: the host looks up the device address once per device with
-// cudaGetSymbolAddress (the first call on a device does this, so that first
-// call should come before any stream capture) and passes that pointer to the
-// kernels.  All calls share the array and it keeps the last call's contents;
-// every scratch word the loss kernels read is written earlier in the same
-// call, so nothing has to be cleared.  Calls whose kernels overlap on the GPU
-// (different streams, or different host threads) race on the array.
+// cudaGetSymbolAddress and passes that pointer to the kernels.  The first
+// call on a device does this and also uploads the SSIM window to that
+// device's constant memory (a synchronous copy), so that first call should
+// come before any stream capture.  All calls share the array and it keeps
+// the last call's contents; every scratch word the loss kernels read is
+// written earlier in the same call, so nothing has to be cleared.  Calls
+// whose kernels overlap on the GPU (different streams, or different host
+// threads) race on the array.
 #include <mutex>
 
 #include "vbm_internal.h"
