@@ -186,8 +186,12 @@ def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
     plan, _, _, img, _ = _forward(cuda_lib, P, cams, W, H)
     st = plan_state(plan, 1)
     ref = oraster.splat_forward(P.astype(np.float64), cams32, 16, 16)
-    bad = _flag_pixels_of_unsafe_items(ref, st["rect"], 1, W, H, (16, 16), P.shape[1]) | (ref["margin"] < 1e-3)
-    assert bad.mean() < 0.3, bad.mean()
+    # excluded: pixels within 1e-5 (relative) of a compositing cut-off in FP64, and the
+    # pixels of tiles whose listing an FP32 rounding of a rectangle changed; the share
+    # must stay under 1% and is reported
+    bad = _flag_pixels_of_unsafe_items(ref, st["rect"], 1, W, H, (16, 16), P.shape[1]) | (ref["margin"] < 1e-5)
+    print("excluded pixels: %d of %d" % (bad.sum(), bad.size))
+    assert bad.mean() < 0.01, bad.mean()
     err = np.abs(img - ref["img"]).transpose(1, 0, 2, 3)[:, ~bad]
     assert err.max() <= 1e-4, err.max()
 
@@ -262,7 +266,7 @@ def test_backward_end_to_end_fp64(cuda_lib):
     g = grad.cpu().numpy()
     for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
         nrm, elt = rel_group_error(g[lo:hi], gref[lo:hi])
-        assert nrm < 1e-3, (lo, nrm, elt)
+        assert nrm < 1e-3 and elt < 1e-3, (lo, nrm, elt)
 
 
 def test_per_view_calls_equal_batched_call(cuda_lib):

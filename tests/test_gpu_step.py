@@ -133,10 +133,18 @@ def test_gradient_central_differences(cuda_lib):
 
 
 def test_full_step_matches_oracle_step(cuda_lib):
+    """One whole fine-tuning step (forward, L1 + D-SSIM, backward, Adam) against the FP64
+    oracle's step.  The scene is one whose every pixel stays at least 2e-5 (relative) from
+    each compositing cut-off in the oracle and whose image differs from the target by more
+    than 1e-5 everywhere (asserted), so FP32 takes the same decisions as FP64 and no pixel
+    is excluded.  Bars: loss 1e-6 relative; gradient 1e-3 per parameter group in norm and
+    element-wise; Adam element-wise: against the oracle's Adam on the GPU's own gradient,
+    and against the oracle's step wherever the gradient's sign is decided (|g_ref| above
+    1e-2 of its group's rms; elsewhere the update is bounded by the learning rate)."""
     vbm = cuda_lib
     from oracle.step import finetune_step
     W, H, V, G = 64, 48, 2, 32
-    P, cams, cams32 = scene(seed=31, n=800, V=V, W=W, H=H)
+    P, cams, cams32 = scene(seed=40, n=800, V=V, W=W, H=H)
     target = np.random.default_rng(2).uniform(0, 0.4, (V, 3, H, W)).astype(np.float32)
     params, cams_dev = to_device(P, cams)
     plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 20)
@@ -157,14 +165,30 @@ def test_full_step_matches_oracle_step(cuda_lib):
     P64 = P.astype(np.float64)
     m64, v64 = np.zeros_like(P64), np.zeros_like(P64)
     L_ref, g_ref, fwd = finetune_step(P64, m64, v64, 1, cams32, target.astype(np.float64), lrs)
-    assert abs(L.item() - L_ref) <= 1e-4 * L_ref
-    nrm, _ = rel_group_error(grad.cpu().numpy(), g_ref)
-    assert nrm < 2e-2, nrm   # pixels at cut-offs are not excluded here
-    # Adam's first step moves each parameter by about lr: compare the steps
-    d_gpu = params.cpu().numpy() - P
-    d_ref = P64 - P.astype(np.float64)
-    agree = np.sign(d_gpu) == np.sign(d_ref)
-    assert agree.mean() > 0.97
+    assert fwd["margin"].min() > 2e-5
+    assert np.abs(fwd["img"] - target).min() > 1e-5
+    assert np.abs(img.cpu().numpy() - fwd["img"]).max() <= 1e-4
+    assert abs(L.item() - L_ref) <= 1e-6 * L_ref
+    g = grad.cpu().numpy()
+    for lo, hi in oadam.ROW_GROUPS:
+        nrm, elt = rel_group_error(g[lo:hi], g_ref[lo:hi])
+        assert nrm < 1e-3 and elt < 1e-3, (lo, nrm, elt)
+    P_gpu = params.cpu().numpy().astype(np.float64)
+    # Adam itself, element-wise, on the GPU's gradient
+    P_own = P.astype(np.float64)
+    oadam.adam_step(P_own, g.astype(np.float64), np.zeros_like(P_own), np.zeros_like(P_own), 1, lrs)
+    lr_row = np.concatenate([np.full(hi - lo, lr) for (lo, hi), lr in zip(oadam.ROW_GROUPS, lrs)])[:, None]
+    assert (np.abs(P_gpu - P_own) <= 1e-6 * np.abs(P_own) + 1e-5 * lr_row).all()
+    # the step against the oracle's step
+    decided = np.zeros_like(g_ref, dtype=bool)
+    for lo, hi in oadam.ROW_GROUPS:
+        rms = np.sqrt(np.mean(g_ref[lo:hi] ** 2))
+        decided[lo:hi] = np.abs(g_ref[lo:hi]) > 1e-2 * rms
+    tol = 1e-6 * np.abs(P64) + 1e-5 * lr_row
+    assert (np.abs(P_gpu - P64) <= tol)[decided].all()
+    step_gpu = P_gpu - P.astype(np.float64)
+    assert (np.abs(step_gpu) <= lr_row * (1 + 1e-5) + 1e-6 * np.abs(P64)).all()
+    assert decided.mean() > 0.5
 
 
 def test_gradient_central_differences_c1_full_size(cuda_lib):
