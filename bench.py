@@ -1,21 +1,29 @@
 """Benchmark of the VBM image-space fine-tuning step on GB300.
 
-Workload (default "c1"): a 128^3 synthetic volume (32 random blobs plus
-k^-2 band-limited noise), 3-level bior4.4 DWT, ~1e5 Gaussians built on the
-GPU by vbm_build, 8 orbit views at 512x512 rendered by vbm_render_dvr as
-targets.  One step = forward splatting of all views, L1 + D-SSIM loss,
-backward to every Gaussian parameter, Adam (Sec. 4.4).
+Workload (default "c4", the largest that fits one GPU): a 512^3 supernova-like
+synthetic volume (5 noisy concentric shells and a dense core), 5-level
+bior4.4 DWT, ~2.9e6 Gaussians built on the GPU by vbm_build, 8 orbit views at
+1024x1024 rendered by vbm_render_dvr as targets, per-pixel compositing state
+recomputed in the backward.  One step = forward splatting of all views,
+L1 + D-SSIM loss, backward to every Gaussian parameter, Adam (Sec. 4.4).
 
 value      steps/s of the batched step (all views per launch, CUDA graph),
            device time from CUDA events, L2 flushed between steps
 plain      steps/s of the same step run one view per launch sequence
-e2e        steps/s through FineTuner.step_host: targets copied from pinned
-           host memory every step, loss read back every step
-roofline   the dominant kernel (forward or backward compositing) timed live
-           with CUDA events recorded by the library on its launch stream
-cpu_baseline  the FP64 oracle on the host, one view of the step (scaled)
+e2e        steps/s through FineTuner.step_host on the host clock: every step
+           copies its targets from pinned host memory and the host reads the
+           loss back before the next step starts
+fwd_only   frames/s of the forward alone at 1920x1080 (one view, one call)
+roofline   the dominant kernel (backward compositing) against the FP32 peak
+           measured in this run by vbm_peak_probe; `kernels` lists every
+           kernel group of the step with its time (CUDA events recorded by
+           the library on its launch stream) and its algorithmic lower bound
+           (FP32, ex2 or HBM); step_frac = sum of the lower bounds / step time
+cpu_baseline  the FP64 oracle on the host cores: every view's sample in its
+           own process (spawn pool), extrapolated to the full step as stated
+           in the line, plus the one-thread figure
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config cN]
 Under torchrun with N > 1 every rank runs an independent replica (the step
 has no cross-GPU exchange in this build); rank 0 prints the line.
 """
@@ -23,10 +31,14 @@ has no cross-GPU exchange in this build); rank 0 prints the line.
 import argparse
 import hashlib
 import json
+import math
+import multiprocessing
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -36,18 +48,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fine-tune steps/sec (fwd+bwd, batched vs plain) on 1 GB300; raster Gpixel/s; %roofline"
+DEFAULT_CONFIG = "c4"
 FWD_FLOP_PER_PAIR = 20     # dx, dy, quadratic form, o*G, min, 1-a, T(1-a), a*T, 3 colour FMAs
 BWD_FLOP_PER_PAIR = 60     # T recovery, colour and alpha partials, exponent chain, 9 partial sums
+BWD_SFU_PER_PAIR = 2       # ex2 of the exponent, rcp of (1 - alpha)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c1")
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="WxH, skips the autotuner (with --ppt)")
@@ -81,8 +95,9 @@ def workload_extent(cfg):
 # Fine-tuning steps run (with a fixed launch configuration) before the autotuner times its candidates.
 TUNE_WARM_STEPS = 30
 
-# Oracle timing window for workloads whose full view would take minutes on one core.
-CPU_CROP = {"c4": 256}
+# Oracle sample per view: a centred window of this many pixels per side (None = the whole view).
+CPU_WINDOW = {"c2": 200, "c4": 128}
+REF_WINDOW = {"c2": 100, "c4": 64}
 
 
 # --------------------------------------------------------------------- clocks
@@ -148,6 +163,57 @@ def time_steps(fn, steps, flush):
     return [s.elapsed_time(e) for s, e in evs]
 
 
+def measured_peaks(device):
+    """FP32 FMA, FP32x2 FMA and ex2 rates of this GPU from vbm_peak_probe (best of 5 CUDA-event
+    timed launches of one wave-filling grid each), and the HBM copy bandwidth measured by the
+    pool's driver (MEASURED_PEAKS.json) or, without that file, by a 1 GiB device copy here."""
+    import torch
+    from paper_2601_09417_gb300 import vbm
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = sms * 8
+    out = torch.zeros(blocks * 256, device=device)
+    res = {}
+    for kind, name, iters in ((0, "fp32_fma_tflops", 32768), (1, "fp32x2_fma_tflops", 32768),
+                              (2, "ex2_tera_per_s", 4096)):
+        vbm.peak_probe(kind, blocks, iters, out)            # warm-up
+        best = None
+        for _ in range(5):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            ops = vbm.peak_probe(kind, blocks, iters, out)
+            e.record()
+            e.synchronize()
+            rate = ops / (s.elapsed_time(e) * 1e-3) / 1e12
+            best = rate if best is None else max(best, rate)
+        res[name] = best
+    res["fp32_tflops"] = max(res["fp32_fma_tflops"], res["fp32x2_fma_tflops"])
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = None
+    try:
+        with open(path) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+        res["hbm_source"] = "MEASURED_PEAKS.json (STREAM-style copy, driver-measured on this pool)"
+    except (OSError, ValueError, KeyError):
+        a = torch.empty(1 << 30, dtype=torch.uint8, device=device)
+        b = torch.empty_like(a)
+        best = 0.0
+        for _ in range(6):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            b.copy_(a)
+            e.record()
+            e.synchronize()
+            best = max(best, 2 * a.numel() / (s.elapsed_time(e) * 1e-3) / 1e9)
+        hbm = best
+        res["hbm_source"] = "measured here: 1 GiB device copy, read + write bytes, best of 6"
+        del a, b
+    res["hbm_gbs"] = hbm
+    res["derived_fp32_tflops"] = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    res["probe"] = ("vbm_peak_probe: %d blocks x 256 threads x 8 independent chains, CUDA events, best of 5"
+                    % blocks)
+    return res
+
+
 def kernel_source_hash():
     """Hash of the compositing kernels' code (raster.cu and vbm_internal.h with // comments
     and blank lines removed, so that a comment edit keeps a capture of unchanged code)."""
@@ -161,63 +227,196 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch from a committed ncu capture of the current kernel source, else None."""
+def profiled_traffic(kernel, workload_key):
+    """DRAM bytes per launch from a committed ncu capture of the current kernel source on this
+    workload, else None (with the reason)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
-        return None
-    ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
-        return None
-    return ent.get("dram_bytes_per_launch")
+        return None, "no profiles/traffic.json"
+    ent = rec.get(kernel, {}).get(workload_key)
+    if not ent:
+        return None, "no capture of %s on %s" % (kernel, workload_key)
+    if ent.get("source_hash") != kernel_source_hash():
+        return None, "kernel changed since the capture"
+    return ent.get("dram_bytes_per_launch"), ent.get("note", "")
+
+
+# ------------------------------------------------------- algorithmic work
+
+def step_work(N, V, HW, n_dup, p_fwd, p_bwd, recompute):
+    """Algorithmic work per step of each kernel group (FP32 FLOP, ex2/rcp evaluations, HBM bytes),
+    the counts of the method itself (N Gaussians, V views of HW pixels, n_dup (view, tile,
+    Gaussian) pairs, p_fwd / p_bwd evaluated pairs) and not of this implementation."""
+    items = N * V
+    px = V * HW
+    state = 0 if recompute else 8                      # T_final and the last contributor per pixel
+    return {
+        "projection": dict(flop=250 * items, sfu=0, bytes=N * 56 + items * 40),
+        "binning_sort": dict(flop=0, sfu=0, bytes=items * 8 + n_dup * 12 + n_dup * 12 * 2 + n_dup * 8),
+        "raster_fwd": dict(flop=FWD_FLOP_PER_PAIR * p_fwd, sfu=p_fwd, bytes=n_dup * 40 + px * (12 + state)),
+        "loss": dict(flop=0, sfu=0, bytes=px * 3 * 4 * 3),
+        "raster_bwd": dict(flop=BWD_FLOP_PER_PAIR * p_bwd, sfu=BWD_SFU_PER_PAIR * p_bwd,
+                           bytes=n_dup * 40 + px * (12 + 12 + state) + n_dup * 36),
+        "projection_bwd": dict(flop=400 * items, sfu=0, bytes=items * 36 + N * 56),
+        "adam": dict(flop=0, sfu=0, bytes=14 * N * 28),
+    }
+
+
+def lower_bound_ms(w, peaks):
+    """max(FLOP / FP32 peak, ex2 / SFU peak, bytes / HBM peak) in ms, and which one binds."""
+    t = {"alu": w["flop"] / (peaks["fp32_tflops"] * 1e12),
+         "sfu": w["sfu"] / (peaks["ex2_tera_per_s"] * 1e12),
+         "hbm": w["bytes"] / (peaks["hbm_gbs"] * 1e9)}
+    bound = max(t, key=t.get)
+    return t[bound] * 1e3, bound
 
 
 # ------------------------------------------------------------- cpu baseline
 
-def cpu_baseline(cfg, w, P_host, targets_host):
-    """FP64 oracle on the host: one view of the step (projection, binning, compositing, loss,
-    backward; a centred window of it for the largest workloads, scaled by pixel count) times
-    the number of views, plus Adam over all Gaussians."""
-    from oracle import adam as oadam
+def _window_camera(cam, window):
+    """The camera of a centred window (w, h) of cam's image: principal point shifted."""
+    c = dict(cam)
+    if window is None:
+        return c, (0, 0, cam["width"], cam["height"])
+    w = min(window, cam["width"])
+    h = min(window, cam["height"])
+    x0, y0 = (cam["width"] - w) // 2, (cam["height"] - h) // 2
+    c["cx"] -= x0
+    c["cy"] -= y0
+    c["width"], c["height"] = w, h
+    return c, (x0, y0, w, h)
+
+
+_WORKER_P = None
+
+
+def _oracle_worker_init(p_path):
+    """Spawned oracle worker: loads the Gaussians once (FP64 P[14][N])."""
+    global _WORKER_P
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    _WORKER_P = np.ascontiguousarray(np.load(p_path), dtype=np.float64)
+
+
+def _oracle_view_sample(job):
+    """One view's share of the step by the FP64 oracle, on a window of the view: projection of
+    all N Gaussians, binning, compositing, L1 + D-SSIM loss, backward and projection backward,
+    each phase timed (oracle.raster's per-phase timings)."""
     from oracle import loss as oloss
     from oracle import raster as oraster
-    from vbm_inputs.cameras import cameras_as_float32
-    V = len(w.cams)
-    so = [0, w.n] if w.scene_offset is None else [int(x) for x in w.scene_offset]
-    s0 = 0 if w.view_scene is None else int(w.view_scene[0])
-    P64 = P_host[:, so[s0]:so[s0 + 1]].astype(np.float64)
-    cam = dict(cameras_as_float32(w.cams)[0])
-    H, W = targets_host.shape[2], targets_host.shape[3]
-    tgt = targets_host[:1].astype(np.float64)
-    crop = CPU_CROP.get(cfg["key"])
-    scale = 1.0
-    if crop and crop < min(W, H):
-        x0, y0 = (W - crop) // 2, (H - crop) // 2
-        cam["cx"] -= x0
-        cam["cy"] -= y0
-        cam["width"] = cam["height"] = crop
-        tgt = tgt[:, :, y0:y0 + crop, x0:x0 + crop]
-        scale = (W * H) / float(crop * crop)
+    cam, target = job["cam"], job["target"]
+    tm = {}
     t0 = time.perf_counter()
-    fwd = oraster.splat_forward(P64, [cam])
-    _, dimg = oloss.loss_and_grad(fwd["img"], tgt)
-    dimg *= 1.0 / V
-    oraster.splat_backward(fwd, P64, [cam], dimg)
-    t_view = (time.perf_counter() - t0) * scale
+    fwd = oraster.splat_forward(_WORKER_P, [cam], timings=tm)
     t1 = time.perf_counter()
-    P_all = P_host.astype(np.float64)
-    oadam.adam_step(P_all, np.zeros_like(P_all), np.zeros_like(P_all), np.zeros_like(P_all), 1,
-                    oadam.default_lrs(workload_extent(cfg)))
-    t_adam = time.perf_counter() - t1
-    t_step = V * t_view + t_adam
-    what = ("a %dx%d window of 1 of %d views (x%.0f for the full view)" % (crop, crop, V, scale)
-            if scale != 1.0 else "1 of %d views" % V)
-    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%s (projection, binning, compositing, loss, backward) timed, x%d, plus Adam over all %d "
-                      "Gaussians; %.2f s per view" % (what, V, P_host.shape[1], t_view)}
+    _, dimg = oloss.loss_and_grad(fwd["img"], target)
+    tm["loss"] = time.perf_counter() - t1
+    dimg *= job["loss_scale"]
+    oraster.splat_backward(fwd, _WORKER_P, [cam], dimg, timings=tm)
+    tm["total"] = time.perf_counter() - t0
+    tm["pairs"] = int(fwd["items"].size)
+    tm["view"] = job["view"]
+    return tm
+
+
+def _extrapolate_view(tm, pairs_view, pixel_ratio):
+    """Full-view seconds from a window's phases: projection, binning and projection backward
+    run over all N items whatever the window (taken as measured, so binning's per-pair part is
+    not scaled); compositing forward and backward scale with the view's pairs over the
+    window's; the loss with the pixels."""
+    pr = pairs_view / max(1, tm["pairs"])
+    return (tm["project"] + tm["bin_sort"] + tm["project_bwd"] + (tm["render"] + tm["render_bwd"]) * pr
+            + tm["loss"] * pixel_ratio)
+
+
+class OracleSampler:
+    """A spawn pool of min(V, cpu) oracle processes holding the Gaussians; each run times one
+    window sample of every view (view v in its own process)."""
+
+    def __init__(self, P64, cams, targets, window, pairs_view):
+        self.V = len(cams)
+        self.workers = max(1, min(self.V, os.cpu_count() or 1))
+        fd, self.p_path = tempfile.mkstemp(suffix=".npy")
+        os.close(fd)
+        np.save(self.p_path, np.ascontiguousarray(P64, dtype=np.float64))
+        self.N = P64.shape[1]
+        self.jobs = []
+        W, H = cams[0]["width"], cams[0]["height"]
+        for v, cam in enumerate(cams):
+            c, (x0, y0, w, h) = _window_camera(cam, window)
+            self.jobs.append(dict(view=v, cam=c, target=np.ascontiguousarray(targets[v][:, y0:y0 + h, x0:x0 + w],
+                                                                              dtype=np.float64)[None],
+                                  loss_scale=(w * h) / float(self.V * W * H)))
+        self.win = (self.jobs[0]["cam"]["width"], self.jobs[0]["cam"]["height"])
+        self.pixel_ratio = (W * H) / float(self.win[0] * self.win[1])
+        self.pairs_view = [int(x) for x in pairs_view]
+        ctx = multiprocessing.get_context("spawn")
+        self.pool = ctx.Pool(self.workers, initializer=_oracle_worker_init, initargs=(self.p_path,))
+
+    def run(self):
+        """One sample: wall seconds, per-view extrapolated full-view seconds, raw phases."""
+        t0 = time.perf_counter()
+        res = sorted(self.pool.map(_oracle_view_sample, self.jobs, chunksize=1), key=lambda r: r["view"])
+        wall = time.perf_counter() - t0
+        per_view = [_extrapolate_view(r, self.pairs_view[r["view"]], self.pixel_ratio) for r in res]
+        return wall, per_view, res
+
+    def adam_seconds(self, extent):
+        from oracle import adam as oadam
+        P = np.load(self.p_path)
+        t0 = time.perf_counter()
+        oadam.adam_step(P, np.zeros_like(P), np.zeros_like(P), np.zeros_like(P), 1, oadam.default_lrs(extent))
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        try:
+            os.remove(self.p_path)
+        except OSError:
+            pass
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def baseline_record(sampler, per_view, wall, t_adam, window_label):
+    """cpu_baseline object from one sample run."""
+    V = sampler.V
+    rounds = math.ceil(V / sampler.workers)
+    t_step = rounds * max(per_view) + t_adam
+    t_step_1 = sum(per_view) + t_adam
+    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": sampler.workers, "kind": "oracle",
+            "value_1_thread": 1.0 / t_step_1, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "sample": ("FP64 oracle, one process per view (%d processes, spawn pool): a centred %dx%d window of each "
+                       "of the %d views (projection of all %d Gaussians, binning, compositing, loss, backward, "
+                       "projection backward), %.1f s wall; full view extrapolated per view: projection, binning "
+                       "and projection backward as measured, compositing forward/backward scaled by the view's "
+                       "pair count over the window's, loss by pixels (%s); step = slowest view x %d + Adam over all "
+                       "Gaussians (%.2f s); value_1_thread = the sum of the per-view seconds + Adam (each view "
+                       "measured in its own process on its own core)"
+                       % (sampler.workers, sampler.win[0], sampler.win[1], V, sampler.N, wall, window_label, rounds,
+                          t_adam)),
+            "s_per_view": [round(x, 3) for x in per_view]}
 
 
 def _gpu_id(torch, device, local):
@@ -228,31 +427,97 @@ def _gpu_id(torch, device, local):
     return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
 
 
+# ------------------------------------------------------------- reference arm
+
+def _oracle_inputs(cfg):
+    """The workload's Gaussians (FP64 P[14][N]) and per-view pair counts, its cameras and DVR
+    target windows, built by the oracle alone (no GPU, no libvbm): TF, DWT (the four RGBA
+    channels in threads), budget and MAD selection, the bank, the coefficient map; pair
+    counts from the oracle's projection of each full view."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import dvr as odvr
+    from oracle import raster as oraster
+    from oracle.bank import build_bank
+    from oracle.dwt import dwt3d
+    from oracle.filters import filter_bank
+    from oracle.mapping import map_coefficients, select_all
+    from oracle.tf import apply_tf_vectorised
+    from vbm_inputs import TF_KNOTS_RGBA, TF_KNOTS_X, orbit_cameras, volume_for_config
+    from vbm_inputs.cameras import cameras_as_float32
+    if "edges" in cfg or "modes" in cfg:
+        raise ValueError("the reference arm builds single-volume workloads")
+    F = volume_for_config(cfg).astype(np.float64)
+    J = cfg["levels"]
+    x32 = TF_KNOTS_X.astype(np.float32).astype(np.float64)
+    rgba32 = TF_KNOTS_RGBA.astype(np.float32).astype(np.float64)
+    RF = apply_tf_vectorised(F, x32, rgba32)
+    fb = filter_bank(0)
+    with ThreadPoolExecutor(5) as ex:
+        bank_f = ex.submit(build_bank, J)
+        chans = list(ex.map(lambda c: dwt3d(np.ascontiguousarray(RF[..., c]), J, fb), range(4)))
+        bank = bank_f.result()
+    del RF
+    A = np.stack(chans)
+    del chans
+    masks, _, _, _ = select_all(A, J, cfg["K_tot"])
+    P = map_coefficients(A, masks, J, bank)
+    del A
+    cams = cameras_as_float32(orbit_cameras(F.shape[::-1], cfg["views"], cfg["width"], cfg["height"]))
+    n = P.shape[1]
+    pairs_view = [int(oraster.project(P, c, np.arange(n), 16, 16)[:, 12].sum()) for c in cams]
+    window = REF_WINDOW.get(cfg["key"])
+    targets = []
+    for c in cams:
+        wc, (x0, y0, w, h) = _window_camera(c, window)
+        jj, ii = np.meshgrid(np.arange(y0, y0 + h), np.arange(x0, x0 + w), indexing="ij")
+        pix = np.stack([ii.reshape(-1), jj.reshape(-1)], 1)
+        rgba = odvr.render_dvr(F.astype(np.float64), x32, rgba32, c, step=0.5, pixels=pix)
+        img = np.zeros((3, c["height"], c["width"]))
+        img[:, y0:y0 + h, x0:x0 + w] = rgba[:3].reshape(3, h, w)
+        targets.append(img)
+    return P, cams, targets, pairs_view, window
+
+
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on the same workload, bounded samples."""
+    """Reference arm: the FP64 CPU oracle on the same workload, built and timed without the GPU.
+    Each step is one bounded sample (a window of every view, one process per view); the line's
+    ms_per_step is that sample's wall time, its value the full-step rate extrapolated from it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import torch
-    device = torch.device("cuda", 0) if torch.cuda.is_available() else None
-    if device is None:
-        print(json.dumps({"impl": "reference", "unavailable": "workload inputs are built on the GPU"}))
-        return
-    torch.cuda.set_device(device)
-    w = make_workload(args.config, device)
-    cfg, n = w.cfg, w.n
-    P = w.params.cpu().numpy()
-    T = w.targets.cpu().numpy()
-    vals = []
-    for _ in range(max(1, min(args.steps, 3))):
-        vals.append(cpu_baseline(cfg, w, P, T))
-    v = statistics.median([x["value"] for x in vals])
+    from vbm_inputs import config
+    cfg = config(args.config)
+    t0 = time.perf_counter()
+    P, cams, targets, pairs_view, window = _oracle_inputs(cfg)
+    t_build = time.perf_counter() - t0
+    sampler = OracleSampler(P, cams, targets, window, pairs_view)
+    try:
+        for _ in range(args.warmup):
+            sampler.run()
+        walls, rates, recs = [], [], []
+        t_adam = sampler.adam_seconds(workload_extent(cfg))
+        for _ in range(args.steps):
+            wall, per_view, _ = sampler.run()
+            walls.append(wall)
+            rec = baseline_record(sampler, per_view, wall, t_adam,
+                                  "whole view, nothing extrapolated" if window is None else "window %d" % window)
+            rates.append(rec["value"])
+            recs.append(rec)
+    finally:
+        sampler.close()
+    v = statistics.median(rates)
+    ms = 1e3 * statistics.median(walls)
+    rec = recs[len(recs) // 2]
+    rec["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["workload"], "gaussians": int(n)},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "config": {"workload": cfg["workload"], "gaussians": int(P.shape[1]),
+                       "inputs": "built by the FP64 oracle on the host (no GPU): %.0f s" % t_build},
+            "note": ("each timed step is one bounded sample of the workload (a %s window of every view); "
+                     "ms_per_step is that sample's wall time, value the full-step rate extrapolated from it "
+                     "(cpu_baseline.sample)" % ("%dx%d" % sampler.win)),
+            "cpu_baseline": rec,
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -320,11 +585,14 @@ def main():
     def flush():
         flush_buf.fill_(1)
 
+    peaks = measured_peaks(device)
+
     # ---------------------------------------------------------- batched form
     ft = FineTuner(params0.clone(), recs, targets, **batch, **launch)
-    # profiling hooks: events around the compositing kernels (recorded inside the
-    # graph) and the per-pixel evaluated-entry count of every forward
-    kev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    # profiling hooks: events at the kernel-group boundaries (recorded by the
+    # library inside the graph, on its launch stream) and the per-pixel
+    # evaluated-entry count of every forward
+    kev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
     for e in kev:          # torch creates the underlying cudaEvent on the first record
         e.record()
     torch.cuda.synchronize()
@@ -348,6 +616,7 @@ def main():
     ft.step_batched()
     torch.cuda.synchronize()
     launches_per_step = vbm.kernel_launches() - launches0
+    extra_steps = 1        # the launch-count step above
 
     clocks = ClockSampler(_gpu_id(torch, device, local))
     if world > 1:
@@ -355,7 +624,8 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     t_wall0 = time.perf_counter()
-    step_ms, fwd_ms, bwd_ms, p_fwd, p_bwd, pairs = [], [], [], 0, 0, []
+    groups = ("head", "projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam")
+    step_ms, grp_ms, p_fwd, p_bwd, pairs = [], {g: [] for g in groups}, 0, 0, []
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush()
@@ -364,8 +634,9 @@ def main():
         e_ev.record()
         e_ev.synchronize()
         step_ms.append(s_ev.elapsed_time(e_ev))
-        fwd_ms.append(kev[0].elapsed_time(kev[1]))
-        bwd_ms.append(kev[2].elapsed_time(kev[3]))
+        marks = [s_ev, kev[4], kev[5], kev[0], kev[1], kev[2], kev[3], kev[6], e_ev]
+        for g, a, b in zip(groups, marks[:-1], marks[1:]):
+            grp_ms[g].append(a.elapsed_time(b))
         p_fwd += int(n_eval.sum().item())
         p_bwd += int(n_contrib.sum().item())
         pairs.append(int(n_pairs_dev.item()))
@@ -378,6 +649,7 @@ def main():
     total_ms, value = job_rate(sum(step_ms), args.steps, device)
     ms_per_step = total_ms / args.steps
     ok, need, bad = ft.check()
+    state_ms = {g: float(np.median(grp_ms[g])) for g in groups}
 
     # forward alone (projection, binning, sort, compositing) and forward + loss +
     # backward, all views in one call each, no graph: the Gpixel/s figures
@@ -391,6 +663,14 @@ def main():
     n_px = min(args.steps, 100)
     fo = time_steps(fwd_only, n_px, flush)
     fb = time_steps(fwd_bwd, n_px, flush)
+    ft.plan.set_profile()
+    # pairs per view of the built Gaussians (the oracle baseline's state, for its
+    # extrapolation): the entries of each view's tile ranges after one forward
+    ft.plan.forward(params0, ft.cams, ft.img, bg=ft.bg)
+    TXY = ((W + tile[0] - 1) // tile[0]) * ((H + tile[1] - 1) // tile[1])
+    rng_host = vbm.device_tensor(bufs.ranges, (V * TXY, 2), np.int32).cpu().numpy()
+    pairs_view = [int((rng_host[v * TXY:(v + 1) * TXY, 1] - rng_host[v * TXY:(v + 1) * TXY, 0]).sum())
+                  for v in range(V)]
     del ft
 
     # ------------------------------------------ plain form: one view per launch
@@ -404,19 +684,31 @@ def main():
     del ftp
 
     # ------------------------------------------------------------ end to end
+    # host clock: flush L2 and drain the stream (untimed), then time the step
+    # from its launch through the host's read of the loss copied back
     fte = FineTuner(params0.clone(), recs, targets, **batch, **launch)
     host_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
     host_t.copy_(targets)
     host_l = torch.empty(1, dtype=torch.float64, pin_memory=True)
     fte.capture_host(host_t, host_l)
+    stream = torch.cuda.current_stream(device)
     for _ in range(args.warmup):
         fte.step_host(host_t, host_l)
-    e2e = time_steps(lambda: fte.step_host(host_t, host_l), args.steps, flush)
-    e2e_ms = sum(e2e) / len(e2e)
+    stream.synchronize()
+    e2e_s, losses = [], []
+    for _ in range(args.steps):
+        flush()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        fte.step_host(host_t, host_l)
+        stream.synchronize()
+        losses.append(float(host_l[0]))
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * sum(e2e_s) / len(e2e_s)
     del fte
 
     # --------------------------------------- forward-only frames (single view)
-    fwd_only = None
+    fwd_only_rec = None
     if cfg.get("fwd_only") and w.scene_offset is None:
         from vbm_inputs import orbit_cameras
         from vbm_inputs.cameras import camera_array
@@ -433,38 +725,60 @@ def main():
             frame()
         fo_ms = time_steps(frame, min(args.steps, 100), flush)
         ok1, need1 = plan1.check()
-        fwd_only = {"image": "%dx%d" % (fw, fh), "frames_per_s": 1e3 / float(np.median(fo_ms)),
-                    "ms_per_frame": float(np.median(fo_ms)), "pairs_ok": bool(ok1),
-                    "form": "projection + binning + sort + compositing of one view, one call"}
+        fwd_only_rec = {"image": "%dx%d" % (fw, fh), "frames_per_s": 1e3 / float(np.median(fo_ms)),
+                        "ms_per_frame": float(np.median(fo_ms)), "pairs_ok": bool(ok1),
+                        "gaussians": int(n),
+                        "form": "projection + binning + sort + compositing of one view, one call, the initial "
+                                "Gaussians, L2 flushed before each frame"}
         plan1.close()
 
     # ------------------------------------------------------------- roofline
-    f_fwd = sum(fwd_ms) / len(fwd_ms)
-    f_bwd = sum(bwd_ms) / len(bwd_ms)
-    peak_tflops = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    if f_bwd >= f_fwd:
-        kname, flops, kms = "raster_bwd", p_bwd * BWD_FLOP_PER_PAIR, sum(bwd_ms)
-    else:
-        kname, flops, kms = "raster_fwd", p_fwd * FWD_FLOP_PER_PAIR, sum(fwd_ms)
-    achieved = flops / (kms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": profiled_traffic(kname), "kernel": kname,
-                "kernel_ms": kms / args.steps, "fwd_kernel_ms": f_fwd, "bwd_kernel_ms": f_bwd,
+    n_pairs = float(np.mean(pairs))
+    work = step_work(n, V, H * W, n_pairs, p_fwd / args.steps, p_bwd / args.steps, batch["recompute"])
+    kernels, lb_sum = {}, 0.0
+    for g in ("projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam"):
+        lb, bound = lower_bound_ms(work[g], peaks)
+        t = state_ms[g]
+        rec = {"ms": t, "lower_bound_ms": lb, "bound": bound, "frac": lb / t if t > 0 else None,
+               "hbm_gbs": work[g]["bytes"] / (t * 1e-3) / 1e9 if t > 0 else None,
+               "hbm_frac": work[g]["bytes"] / (t * 1e-3) / 1e9 / peaks["hbm_gbs"] if t > 0 else None,
+               "algorithmic_bytes": work[g]["bytes"]}
+        if work[g]["flop"]:
+            rec["tflops"] = work[g]["flop"] / (t * 1e-3) / 1e12 if t > 0 else None
+        kernels[g] = rec
+        lb_sum += lb
+    t_bwd, t_fwd = state_ms["raster_bwd"], state_ms["raster_fwd"]
+    kname = "raster_bwd" if t_bwd >= t_fwd else "raster_fwd"
+    flops = work[kname]["flop"]
+    achieved = flops / (state_ms[kname] * 1e-3) / 1e12
+    traffic, traffic_note = profiled_traffic(kname, cfg["key"])
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["fp32_tflops"], "traffic": traffic, "traffic_note": traffic_note,
+                "kernel": kname, "kernel_ms": state_ms[kname],
+                "peak_source": "measured in this run (vbm_peak_probe, FP32 FMA chains: %.1f, FP32x2 FMA chains: "
+                               "%.1f TFLOP/s); derived 152 SMs x 128 lanes x 2 x 2070 MHz = %.1f"
+                               % (peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"], peaks["derived_fp32_tflops"]),
+                "sfu_frac": work[kname]["sfu"] / (state_ms[kname] * 1e-3) / 1e12 / peaks["ex2_tera_per_s"],
                 "pairs_fwd_per_step": p_fwd / args.steps, "pairs_bwd_per_step": p_bwd / args.steps,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock",
-                "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR}}
-    n_pairs = int(np.mean(pairs))
+                "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR},
+                "step_frac": lb_sum / ms_per_step, "step_lower_bound_ms": lb_sum,
+                "kernels": kernels, "peaks": peaks}
 
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg["workload"], "gaussians": int(n), "views": V, "image": "%dx%d" % (W, H),
+            "config": {"workload": cfg["workload"], "key": cfg["key"], "gaussians": int(n), "views": V,
+                       "image": "%dx%d" % (W, H),
                        "tile": "%dx%d" % tile, "pixels_per_thread": ppt, "group_lanes": gl, "persistent": pers,
                        "segment_len": (seg if seg else 256) if pers else None,
                        "bwd_pixels_per_thread": bppt or ppt, "bwd_group_lanes": bgl or gl,
                        "pair_order": "device radix sorts" if args.radix else "bucketed per-tile sort",
                        "compositing_state": "recomputed in the backward" if batch["recompute"] else "stored",
-                       "pairs_mean": n_pairs,
+                       "pairs_mean": int(n_pairs),
+                       "timed_iterations": "fine-tuning iterations %d-%d from the built Gaussians (the launch "
+                                           "configuration was tuned on a copy %d iterations in)"
+                                           % (args.warmup + extra_steps + 1, args.warmup + extra_steps + args.steps,
+                                              TUNE_WARM_STEPS),
                        "form": "batched, CUDA graph, autotuned",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -482,7 +796,6 @@ def main():
                                            for r in tune_table if r.get("stage") == "combination"],
                          "segment_len": [{"segment_len": r["segment_len"], "ms_fwd_bwd": r["ms"]}
                                          for r in tune_table if r.get("stage") == "segment"],
-
                          "tuned_after_steps": TUNE_WARM_STEPS if tune_table else 0},
             "batched_over_plain": plain_ms / ms_per_step,
             "step_ms_percentiles": {"p10": float(np.percentile(step_ms, 10)),
@@ -490,19 +803,36 @@ def main():
                                     "p90": float(np.percentile(step_ms, 90))},
             "gpixel_per_s": {"fwd": V * H * W / (float(np.median(fo)) * 1e-3) / 1e9,
                              "fwd_loss_bwd": V * H * W / (float(np.median(fb)) * 1e-3) / 1e9,
-                             "raster_fwd_kernel": V * H * W / (f_fwd * 1e-3) / 1e9,
+                             "raster_fwd_kernel": V * H * W / (t_fwd * 1e-3) / 1e9,
                              "note": "fwd = projection + binning + sort + compositing of all views, one call, "
                                      "median of %d; raster_fwd_kernel = the compositing kernel alone" % n_px},
             "e2e": {"value": 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(targets.numel() * 4),
-                    "d2h_bytes_per_step": 8},
+                    "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms,
+                    "timing": "host clock per step: graph launch (targets copied from pinned host memory inside "
+                              "it), stream synchronize, host read of the loss; L2 flushed before each step, "
+                              "outside the timed interval",
+                    "loss_first_last": [losses[0], losses[-1]]},
             "roofline": roofline, "gpu_launches": int(launches_per_step * args.steps),
-            "wall_s_timed": wall}
-    if fwd_only is not None:
-        line["fwd_only"] = fwd_only
+            "launches_per_step": int(launches_per_step), "wall_s_timed": wall}
+    if fwd_only_rec is not None:
+        line["fwd_only"] = fwd_only_rec
     if clk is not None:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, w, params0.cpu().numpy(), targets.cpu().numpy())
+        from vbm_inputs.cameras import cameras_as_float32
+        if w.scene_offset is None:
+            cams32 = cameras_as_float32(cams)
+            window = CPU_WINDOW.get(cfg["key"])
+            sampler = OracleSampler(params0.cpu().numpy().astype(np.float64), cams32, targets.cpu().numpy(),
+                                    window, pairs_view)
+            try:
+                wall_c, per_view, _ = sampler.run()
+                t_adam = sampler.adam_seconds(workload_extent(cfg))
+            finally:
+                sampler.close()
+            line["cpu_baseline"] = baseline_record(
+                sampler, per_view, wall_c, t_adam,
+                "whole view, nothing extrapolated" if window is None else "window %d" % window)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

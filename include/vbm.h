@@ -329,7 +329,10 @@ VBM_API vbm_status vbm_loss_workspace_size(int n_images, int height, int width, 
  * with SSIM over an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2,
  * C2 = 0.03^2, zero padding, per channel; sign(0) = 0.  scale = 1 / (number
  * of elements of the whole batch) gives the mean.  *d_loss (double) is
- * overwritten, or added to when accumulate != 0. */
+ * overwritten, or added to when accumulate != 0.  At most 21845 images per
+ * call (VBM_ERR_ARG beyond: split the batch and accumulate).  The first call
+ * on a device uploads the SSIM window to its constant memory (a synchronous
+ * copy): make it before any stream capture. */
 VBM_API vbm_status vbm_loss(const float *d_img, const float *d_target, int n_images, int height, int width,
                     float lambda, double scale, double *d_loss, int32_t accumulate, float *d_dL_dimg,
                     void *d_ws, size_t ws_bytes, void *stream);
@@ -344,7 +347,8 @@ VBM_API vbm_status vbm_loss(const float *d_img, const float *d_target, int n_ima
  * that loads it, until exit): calls whose vbm_loss workspace would exceed
  * 32 MiB return VBM_ERR_CAPACITY without launching (split the batch and use
  * accumulate).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
+ * address (cudaGetSymbolAddress) and uploads the SSIM window to that
+ * device's constant memory; make that first call before any stream
  * capture.  All calls share the array: calls that overlap on the GPU race;
  * nothing in it needs clearing between calls. */
 VBM_API vbm_status vbm_loss_static(const float *d_img, const float *d_target, int n_images, int height, int width,
@@ -367,19 +371,34 @@ VBM_API vbm_status vbm_adam(float *d_params, const float *d_grad, float *d_m, fl
  * launch count of that sequence. */
 VBM_API int64_t vbm_kernel_launches(void);
 
-/* Profiling hooks of a plan (all optional, NULL disables):
- * events[0..1] are recorded on the call's stream just before and after the
- * compositing kernel of vbm_raster_fwd, events[2..3] around the compositing
- * kernel of vbm_raster_bwd (cudaEvent_t handles created by the caller with
- * timing enabled; under stream capture they are recorded as external event
- * nodes).  d_n_eval (int32 [V][H][W]) receives, per pixel of a forward call,
- * the number of list entries evaluated (up to and including the one that
- * ended compositing); d_n_contrib (int32 [V][H][W]) receives the contributor
- * count (one past the last blended entry) in plans created with
- * VBM_PLAN_RECOMPUTE, which keep none of their own.  The hooks stay set until
- * changed. */
-VBM_API vbm_status vbm_plan_set_profile(vbm_plan *plan, void *const events[4], int32_t *d_n_eval,
+/* Profiling hooks of a plan (all optional, NULL disables).  events holds
+ * n_events (0, 4 or 7) cudaEvent_t handles created by the caller with timing
+ * enabled, recorded on the call's stream (under stream capture as external
+ * event nodes):
+ *   [0], [1]  just before and after the compositing kernel of vbm_raster_fwd;
+ *   [2], [3]  just before and after the compositing kernel of vbm_raster_bwd;
+ *   [4]       at the start of vbm_raster_fwd (before the projection);
+ *   [5]       after the projection kernel (binning and sorting follow, up to [0]);
+ *   [6]       at the end of vbm_raster_bwd (after the projection backward).
+ * d_n_eval (int32 [V][H][W]) receives, per pixel of a forward call, the number
+ * of list entries evaluated (up to and including the one that ended
+ * compositing); d_n_contrib (int32 [V][H][W]) receives the contributor count
+ * (one past the last blended entry) in plans created with VBM_PLAN_RECOMPUTE,
+ * which keep none of their own.  The hooks stay set until changed. */
+VBM_API vbm_status vbm_plan_set_profile(vbm_plan *plan, int32_t n_events, void *const *events, int32_t *d_n_eval,
                                         int32_t *d_n_contrib);
+
+/* Throughput probe for the roofline denominators of the compositing kernels
+ * (not part of the method): one launch of `blocks` blocks of 256 threads, each
+ * thread running 8 independent dependent chains of `iters` links (a multiple
+ * of 16) of kind 0: scalar FP32 FMA, 1: packed FP32x2 FMA (fma.rn.f32x2),
+ * 2: ex2.approx.ftz.f32 (one FMA beside each).  *ops (host) receives the
+ * launch's work: FLOP for kinds 0 and 1 (2 per FMA), ex2 evaluations for kind
+ * 2.  The caller times the launch (CUDA events on `stream`) and divides.
+ * d_out needs blocks * 256 floats and is written only in a case that does not
+ * occur (it keeps the chains from being removed). */
+VBM_API vbm_status vbm_peak_probe(int32_t kind, int32_t blocks, int32_t iters, float *d_out, double *ops,
+                                  void *stream);
 
 #ifdef __cplusplus
 }

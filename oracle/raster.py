@@ -212,13 +212,16 @@ def items_of(n_gauss, n_views, scene_offset=None, view_scene=None):
     return np.concatenate(vs), np.concatenate(gs)
 
 
-def splat_forward(P, cams, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), scene_offset=None, view_scene=None):
-    """Full FP64 forward for a batch of views: projection, binning, compositing."""
+def splat_forward(P, cams, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), scene_offset=None, view_scene=None,
+                  timings=None):
+    """Full FP64 forward for a batch of views: projection, binning, compositing.  With a
+    dict `timings`, the wall time of each phase (project, bin_sort, render) is added to it."""
     P = _c64(P)
     n = P.shape[1]
     V = len(cams)
     W, H = cams[0]["width"], cams[0]["height"]
     TX, TY = (W + tile_w - 1) // tile_w, (H + tile_h - 1) // tile_h
+    clock = _PhaseClock(timings)
     view_of, g_of = items_of(n, V, scene_offset, view_scene)
     proj = np.zeros((view_of.size, NPROJ))
     for v in range(V):
@@ -226,23 +229,29 @@ def splat_forward(P, cams, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), scene_offse
         proj[sel] = project(P, cams[v], g_of[sel], tile_w, tile_h)
     rect = proj[:, [PJ["X0"], PJ["Y0"], PJ["X1"], PJ["Y1"]]].astype(np.int32)
     splat = proj[:, [PJ["U"], PJ["V"], PJ["A"], PJ["B"], PJ["C"], PJ["OPAC"]]]
+    clock.lap("project")
     tiles, items, ranges = bin_sort(view_of, rect, proj[:, PJ["DEPTH"]], TX, TY, V,
                                     splat64=splat_records(splat), tile=(tile_w, tile_h), image=(W, H))
+    clock.lap("bin_sort")
     color = P[11:14, g_of].T
     bg = np.asarray(bg, dtype=np.float64)
     out = render(V, W, H, tile_w, tile_h, ranges, items, splat, color, bg)
+    clock.lap("render")
     out.update(proj=proj, rect=rect, tiles=tiles, items=items, ranges=ranges, splat=splat, color=color,
                view_of=view_of, g_of=g_of, W=W, H=H, tile_w=tile_w, tile_h=tile_h, bg=bg)
     return out
 
 
-def splat_backward(fwd, P, cams, dL_dimg, dL_dalpha=None):
-    """FP64 gradient P[14][N] of a loss with image gradient dL_dimg (V, 3, H, W)."""
+def splat_backward(fwd, P, cams, dL_dimg, dL_dalpha=None, timings=None):
+    """FP64 gradient P[14][N] of a loss with image gradient dL_dimg (V, 3, H, W).  With a
+    dict `timings`, the wall time of each phase (render_bwd, project_bwd) is added to it."""
     P = _c64(P)
     n = P.shape[1]
+    clock = _PhaseClock(timings)
     g_splat, g_color = render_bwd(len(cams), fwd["W"], fwd["H"], fwd["tile_w"], fwd["tile_h"],
                                   fwd["ranges"], fwd["items"], fwd["splat"], fwd["color"], fwd["bg"],
                                   dL_dimg, dL_dalpha)
+    clock.lap("render_bwd")
     grad = np.zeros((14, n))
     view_of, g_of = fwd["view_of"], fwd["g_of"]
     for v in range(len(cams)):
@@ -250,4 +259,22 @@ def splat_backward(fwd, P, cams, dL_dimg, dL_dalpha=None):
         gp = project_bwd(P, cams[v], g_of[sel], g_splat[sel])
         np.add.at(grad.T, g_of[sel], gp)
     np.add.at(grad[11:14].T, g_of, g_color)
+    clock.lap("project_bwd")
     return grad, g_splat, g_color
+
+
+class _PhaseClock:
+    """Adds the wall time since the previous lap to timings[name] (no-op without a dict)."""
+
+    def __init__(self, timings):
+        import time
+        self._now = time.perf_counter
+        self.timings = timings
+        self.t = self._now()
+
+    def lap(self, name):
+        if self.timings is None:
+            return
+        t = self._now()
+        self.timings[name] = self.timings.get(name, 0.0) + (t - self.t)
+        self.t = t

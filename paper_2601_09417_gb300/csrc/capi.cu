@@ -83,10 +83,13 @@ int vbm_version(void) { return 101; }
 
 int64_t vbm_kernel_launches(void) { return g_launches.load(); }
 
-vbm_status vbm_plan_set_profile(vbm_plan *p, void *const events[4], int32_t *d_n_eval, int32_t *d_n_contrib)
+vbm_status vbm_plan_set_profile(vbm_plan *p, int32_t n_events, void *const *events, int32_t *d_n_eval,
+                                int32_t *d_n_contrib)
 {
     VBM_ARG(p, "null plan");
-    for (int i = 0; i < 4; i++) p->prof_ev[i] = events ? (cudaEvent_t)events[i] : nullptr;
+    VBM_ARG(n_events == 0 || n_events == 4 || n_events == kProfileEvents, "n_events must be 0, 4 or 7");
+    VBM_ARG(n_events == 0 || events, "null events");
+    for (int i = 0; i < kProfileEvents; i++) p->prof_ev[i] = i < n_events ? (cudaEvent_t)events[i] : nullptr;
     p->prof_n_eval = d_n_eval;
     p->prof_n_contrib = d_n_contrib;
     return VBM_OK;
@@ -294,7 +297,9 @@ vbm_status vbm_raster_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     p->last_view_begin = vb;
     p->last_view_count = vc;
     p->last_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
+    record_event(p->prof_ev[4], st);
     s = preprocess_fwd(p, params, stride, cams, vb, vc, st);
+    record_event(p->prof_ev[5], st);
     if (s == VBM_OK) s = binning(p, vb, vc, st);
     if (s == VBM_OK) s = raster_fwd(p, vb, vc, bg, img, alpha, st);
     return s;
@@ -312,6 +317,7 @@ vbm_status vbm_raster_bwd(vbm_plan *p, const float *params, int64_t stride, cons
     cudaStream_t st = (cudaStream_t)stream;
     s = raster_bwd(p, params, stride, vb, vc, bg, dimg, dalpha, grad, st);
     if (s == VBM_OK) s = preprocess_bwd(p, params, stride, cams, vb, vc, grad, accumulate, st);
+    record_event(p->prof_ev[6], st);
     return s;
 }
 

@@ -27,6 +27,7 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kCullMargin = 1e-3f;
 // Floats per item of the splat-gradient records: du dv dA dB dC dopacity dr dg db, padding.
 constexpr int kGradStride = 12;
+constexpr int kProfileEvents = 7;       // timing events a plan can record (vbm_plan_set_profile)
 
 #ifdef __CUDACC__
 // Binning tile test: smallest q = A dx^2 + 2 B dx dy + C dy^2 (dx = x - u,
@@ -439,7 +440,7 @@ struct vbm_plan {
     int64_t *d_status = nullptr;             // [0] status bits, [1] max pairs needed
 
     // profiling hooks
-    cudaEvent_t prof_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t prof_ev[vbm::kProfileEvents] = {};
     int32_t *prof_n_eval = nullptr;
     int32_t *prof_n_contrib = nullptr;       // contributor counts of recompute-mode forwards (profiling)
 

@@ -22,7 +22,8 @@ EXPORTED = ["vbm_last_error", "vbm_version", "vbm_bank_build", "vbm_tf_apply", "
             "vbm_build_workspace_size", "vbm_build", "vbm_render_dvr", "vbm_plan_create",
             "vbm_plan_destroy", "vbm_plan_check", "vbm_raster_fwd", "vbm_raster_bwd",
             "vbm_plan_get_buffers", "vbm_loss_workspace_size", "vbm_loss", "vbm_adam",
-            "vbm_kernel_launches", "vbm_plan_set_profile", "vbm_loss_static", "vbm_bank_ablate"]
+            "vbm_kernel_launches", "vbm_plan_set_profile", "vbm_loss_static", "vbm_bank_ablate",
+            "vbm_peak_probe"]
 
 
 class VbmError(RuntimeError):
@@ -113,7 +114,8 @@ def load():
         "vbm_adam": (I32, [V, V, V, V, I64, I64, V, ctypes.POINTER(F32 * 5), F32, F32, F32, V, V]),
         "vbm_kernel_launches": (I64, []),
         "vbm_loss_static": (I32, [V, V, I32, I32, I32, F32, F64, V, I32, V, V]),
-        "vbm_plan_set_profile": (I32, [V, ctypes.POINTER(V * 4), V, V]),
+        "vbm_plan_set_profile": (I32, [V, I32, ctypes.POINTER(V), V, V]),
+        "vbm_peak_probe": (I32, [I32, I32, I32, V, ctypes.POINTER(F64), V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -343,13 +345,12 @@ class Plan:
                                         int(bool(accumulate)), _stream()))
 
     def set_profile(self, events=None, n_eval=None, n_contrib=None):
-        """Record cudaEvents around the compositing kernels and/or per-pixel evaluated counts
-        (and, for recompute-mode plans, per-pixel contributor counts)."""
-        if events is None:
-            arr = None
-        else:
-            arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
-        _check(self._lib.vbm_plan_set_profile(self.handle, None if arr is None else ctypes.byref(arr),
+        """Record cudaEvents (4 or 7 torch.cuda.Event, see vbm_plan_set_profile) around the
+        compositing kernels and the projection, and/or per-pixel evaluated counts (and, for
+        recompute-mode plans, per-pixel contributor counts)."""
+        n_ev = 0 if events is None else len(events)
+        arr = (ctypes.c_void_p * max(1, n_ev))(*[ctypes.c_void_p(e.cuda_event) for e in (events or [])])
+        _check(self._lib.vbm_plan_set_profile(self.handle, n_ev, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),
                                               _ptr(n_eval), _ptr(n_contrib)))
         self._profile_keepalive = (events, n_eval, n_contrib)
 
@@ -375,6 +376,14 @@ def loss_static(img, target, n_images, height, width, lam, scale, loss_out, dimg
     """vbm_loss without a workspace: scratch lives in the library's static device array."""
     _check(load().vbm_loss_static(_ptr(img), _ptr(target), n_images, height, width, float(lam), float(scale),
                                   _ptr(loss_out), int(bool(accumulate)), _ptr(dimg), _stream()))
+
+
+def peak_probe(kind, blocks, iters, out):
+    """Launch one throughput probe (0 FP32 FMA, 1 FP32x2 FMA, 2 ex2) on the current stream;
+    returns its work (FLOP, or ex2 evaluations) for the caller's timing."""
+    ops = ctypes.c_double()
+    _check(load().vbm_peak_probe(int(kind), int(blocks), int(iters), _ptr(out), ctypes.byref(ops), _stream()))
+    return ops.value
 
 
 def adam(params, grad, m, v, n, step, lrs, beta1=0.9, beta2=0.999, eps=1e-15, nonfinite=None):
