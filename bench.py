@@ -257,7 +257,9 @@ def step_work(N, V, HW, n_dup, p_fwd, p_bwd, recompute):
         "projection": dict(flop=250 * items, sfu=0, bytes=N * 56 + items * 40),
         "binning_sort": dict(flop=0, sfu=0, bytes=items * 8 + n_dup * 12 + n_dup * 12 * 2 + n_dup * 8),
         "raster_fwd": dict(flop=FWD_FLOP_PER_PAIR * p_fwd, sfu=p_fwd, bytes=n_dup * 40 + px * (12 + state)),
-        "loss": dict(flop=0, sfu=0, bytes=px * 3 * 4 * 3),
+        # SSIM: two separable 11-tap passes (2 FLOP per tap) over the 5 moment maps forward and the 3
+        # gradient maps backward, plus about 40 FLOP of per-element algebra
+        "loss": dict(flop=px * 3 * (2 * 11 * 2 * (5 + 3) + 40), sfu=0, bytes=px * 3 * 4 * 3),
         "raster_bwd": dict(flop=BWD_FLOP_PER_PAIR * p_bwd, sfu=BWD_SFU_PER_PAIR * p_bwd,
                            bytes=n_dup * 40 + px * (12 + 12 + state) + n_dup * 36),
         "projection_bwd": dict(flop=400 * items, sfu=0, bytes=items * 36 + N * 56),

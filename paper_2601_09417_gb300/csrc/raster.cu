@@ -552,6 +552,100 @@ __device__ __forceinline__ void group_sum9(const float (&v)[kNV], float (&out)[G
     }
 }
 
+// One backward step of a lane for splat slot j over its PPT pixels (PPT
+// even), as pairs of pixels in packed FP32x2 operations and without
+// branches: a pixel that does not blend this splat (beyond its last
+// contributor, power > 0 or alpha < 1/255) gets zero weight and keeps its
+// T and Q.  The exponent and alpha are the forward's, operation for
+// operation (dy = g.y + (-pyc) equals g.y - pyc exactly), so the decisions
+// are the forward's.  Writes the nine partials of this lane's pixels to acc
+// (du, dv, dA, dB, dC, dopacity, dr, dg, db; conic terms in the natural-log
+// parameterisation) and returns whether any pixel blended.
+template <int PPT>
+__device__ __forceinline__ bool pair_step(const WarpSlots &s, int j, float pxc, const float2 (&npyc)[PPT / 2],
+                                          const int (&nc)[PPT], float (&T)[PPT], float (&Q)[PPT],
+                                          const float (&dC0)[PPT], const float (&dC1)[PPT],
+                                          const float (&dC2)[PPT], float (&acc)[kNV])
+{
+    const float2 cp = s.cp[j];
+    const int pos1 = __float_as_int(cp.y);
+    const float4 g = s.geo[j];
+    const float4 c = s.col[j];
+    const float dx = __fsub_rn(g.x, pxc);
+    const float t0 = __fmul_rn(__fmul_rn(g.z, dx), dx);
+    const float bdx = __fmul_rn(g.w, dx);
+    const float2 a_dy = make_float2(g.w, g.w);                  // du: 2 A' dx + B' dy
+    const float2 a_c = make_float2(2.f * g.z * dx, 2.f * g.z * dx);
+    const float2 b_dy = make_float2(2.f * cp.x, 2.f * cp.x);    // dv: 2 C' dy + B' dx
+    const float2 b_c = make_float2(g.w * dx, g.w * dx);
+    bool any = false;
+    float2 s_u = make_float2(0.f, 0.f), s_v = s_u, s_pw = s_u, s_dy = s_u, s_dy2 = s_u, s_G = s_u;
+    float2 s_r = s_u, s_g = s_u, s_b = s_u;
+#pragma unroll
+    for (int h = 0; h < PPT / 2; h++) {
+        const int k = 2 * h;
+        const float2 dy = __fadd2_rn(make_float2(g.y, g.y), npyc[h]);
+        const float2 t = __ffma2_rn(__fmul2_rn(make_float2(cp.x, cp.x), dy), dy, make_float2(t0, t0));
+        const float2 p2 = __ffma2_rn(make_float2(bdx, bdx), dy, t);
+        const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+        const float2 raw = __fmul2_rn(make_float2(c.w, c.w), G);
+        const float al0 = fminf(kAlphaMax, raw.x), al1 = fminf(kAlphaMax, raw.y);
+        const bool v0 = pos1 <= nc[k] && p2.x <= 0.f && al0 >= kAlphaMin;
+        const bool v1 = pos1 <= nc[k + 1] && p2.y <= 0.f && al1 >= kAlphaMin;
+        any |= v0 | v1;
+        const float2 alpha = make_float2(v0 ? al0 : 0.f, v1 ? al1 : 0.f);
+        // r_om = 1 / (1 - alpha) for a blended pixel, 1 otherwise (T unchanged)
+        const float2 r_om = make_float2(v0 ? rcp_approx(1.f - al0) : 1.f, v1 ? rcp_approx(1.f - al1) : 1.f);
+        float2 Tk = __fmul2_rn(make_float2(T[k], T[k + 1]), r_om);
+        const float2 wgt = __fmul2_rn(alpha, Tk);
+        const float2 d0 = make_float2(dC0[k], dC0[k + 1]), d1 = make_float2(dC1[k], dC1[k + 1]);
+        const float2 d2 = make_float2(dC2[k], dC2[k + 1]);
+        s_r = h == 0 ? __fmul2_rn(wgt, d0) : __ffma2_rn(wgt, d0, s_r);
+        s_g = h == 0 ? __fmul2_rn(wgt, d1) : __ffma2_rn(wgt, d1, s_g);
+        s_b = h == 0 ? __fmul2_rn(wgt, d2) : __ffma2_rn(wgt, d2, s_b);
+        const float2 cd = __ffma2_rn(make_float2(c.z, c.z), d2,
+                                     __ffma2_rn(make_float2(c.y, c.y), d1, __fmul2_rn(make_float2(c.x, c.x), d0)));
+        float2 Qk = make_float2(Q[k], Q[k + 1]);
+        const float2 dLda = __ffma2_rn(cd, Tk, __fmul2_rn(Qk, make_float2(-r_om.x, -r_om.y)));
+        Qk = __ffma2_rn(cd, wgt, Qk);
+        // the 0.99 clamp passes no gradient to the opacity and the exponent
+        const bool g0 = v0 && raw.x < kAlphaMax, g1 = v1 && raw.y < kAlphaMax;
+        const float2 dLdaG = __fmul2_rn(dLda, G), dpw = __fmul2_rn(dLda, raw);
+        const float2 dG = make_float2(g0 ? dLdaG.x : 0.f, g1 ? dLdaG.y : 0.f);
+        const float2 dpow = make_float2(g0 ? dpw.x : 0.f, g1 ? dpw.y : 0.f);
+        const float2 dpl = __fmul2_rn(dpow, make_float2(kLn2, kLn2));
+        if (h == 0) {      // the first pair starts the sums
+            s_G = dG;
+            s_u = __fmul2_rn(dpl, __ffma2_rn(a_dy, dy, a_c));
+            s_v = __fmul2_rn(dpl, __ffma2_rn(b_dy, dy, b_c));
+            s_pw = dpow;
+            s_dy = __fmul2_rn(dpow, dy);
+            s_dy2 = __fmul2_rn(dpow, __fmul2_rn(dy, dy));
+        } else {
+            s_G = __fadd2_rn(s_G, dG);
+            s_u = __ffma2_rn(dpl, __ffma2_rn(a_dy, dy, a_c), s_u);
+            s_v = __ffma2_rn(dpl, __ffma2_rn(b_dy, dy, b_c), s_v);
+            s_pw = __fadd2_rn(s_pw, dpow);
+            s_dy = __ffma2_rn(dpow, dy, s_dy);
+            s_dy2 = __ffma2_rn(dpow, __fmul2_rn(dy, dy), s_dy2);
+        }
+        T[k] = Tk.x;
+        T[k + 1] = Tk.y;
+        Q[k] = Qk.x;
+        Q[k + 1] = Qk.y;
+    }
+    acc[0] = s_u.x + s_u.y;
+    acc[1] = s_v.x + s_v.y;
+    acc[2] = -0.5f * dx * dx * (s_pw.x + s_pw.y);
+    acc[3] = -dx * (s_dy.x + s_dy.y);
+    acc[4] = -0.5f * (s_dy2.x + s_dy2.y);
+    acc[5] = s_G.x + s_G.y;
+    acc[6] = s_r.x + s_r.y;
+    acc[7] = s_g.x + s_g.y;
+    acc[8] = s_b.x + s_b.y;
+    return any;
+}
+
 template <int PPT, int GL>
 __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__restrict__ ranges,
                                            const uint32_t *__restrict__ pair_item, const float4 *__restrict__ geo,
@@ -620,6 +714,10 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
         }
         my_max = max(my_max, nc[k]);
     }
+    // -(pixel centre y) of each pixel pair, for the packed step
+    float2 npyc[(PPT + 1) / 2];
+#pragma unroll
+    for (int k = 0; k + 1 < PPT; k += 2) npyc[k / 2] = make_float2(-pyc[k], -pyc[k + 1]);
     // largest contributor count of each group and of the warp
     int gm = my_max;
 #pragma unroll
@@ -654,7 +752,13 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
 #pragma unroll
             for (int q = 0; q < kNV; q++) acc[q] = 0.f;
             bool any = false;
-            if (m) {
+            if constexpr (PPT % 2 == 0) {
+                if (m) {
+                    j = 31 - __clz(m);
+                    m &= ~(1u << j);
+                    any = pair_step<PPT>(s, j, wg.pxc, npyc, nc, T, Q, dC0, dC1, dC2, acc);
+                }
+            } else if (m) {
                 j = 31 - __clz(m);
                 m &= ~(1u << j);
                 const float2 cp = s.cp[j];
