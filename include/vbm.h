@@ -295,10 +295,10 @@ VBM_API vbm_status vbm_raster_bwd(vbm_plan *plan, const float *d_params, int64_t
  * view over the call's views. */
 typedef struct {
     int64_t n_items;          /* (view, Gaussian) items of the last call          */
-    const float *geo;         /* [n_items][4]: u, v, conic A, conic B              */
-    const float *col;         /* [n_items][4]: r, g, b, opacity                    */
-    const float *conic_c;     /* [n_items]: conic C                                */
-    const float *depth;       /* [n_items]: camera z                               */
+    const float *rec;         /* [n_items][16], one 64-byte record per item: u, v, conic A, conic B |
+                                 r, g, b, opacity | half-widths (x, y) of the alpha >= 1/255 box,
+                                 B / C, B / A | conic C, tau = 2 (ln(255 o) + 1e-3) (the binning
+                                 tile test's bound; -1 for an item without tiles), camera z, unused */
     const int32_t *rect;      /* [n_items][4]: tile x0, y0, x1, y1 (end exclusive)  */
     const int32_t *radius;    /* [n_items]                                         */
     const uint32_t *pair_tile;/* [n_pairs] sorted tile ids (relative to view_begin) */
@@ -308,8 +308,6 @@ typedef struct {
     const float *T_final;     /* [V][H][W] (absolute views; NULL in recompute mode) */
     const int32_t *n_contrib; /* [V][H][W]                                         */
     const float *g_splat;     /* [n_items][12] after a backward: du dv dA dB dC dopac dr dg db, 3 unused */
-    const float *cull;        /* [n_items][4]: half-widths of the alpha >= 1/255 box, B / C, B / A  */
-    const float *tau;         /* [n_items]: 2 (ln(255 o) + 1e-3), bound of the binning tile test  */
     const int32_t *seg_count; /* persistent plans, device [4]: backward units of the segmented tiles,
                                  segmented tiles, checkpoint slots requested (may exceed
                                  checkpoint_slots: the tiles that found none were walked whole), -;

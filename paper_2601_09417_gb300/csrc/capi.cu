@@ -168,12 +168,7 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->d_view_item_offset, d->n_views + 1);
     ALLOC(p->d_scene_view_ptr, d->n_scenes + 1);
     ALLOC(p->d_scene_views, d->n_views);
-    ALLOC(p->geo, items);
-    ALLOC(p->col, items);
-    ALLOC(p->conic_c, items);
-    ALLOC(p->cull, items);
-    ALLOC(p->tau, items);
-    ALLOC(p->depth, items);
+    ALLOC(p->rec, items);
     ALLOC(p->rect, items);
     ALLOC(p->radius, items);
     ALLOC(p->listed, items);
@@ -326,10 +321,7 @@ vbm_status vbm_plan_get_buffers(vbm_plan *p, vbm_plan_buffers *o)
     VBM_ARG(p && o, "null argument");
     std::memset(o, 0, sizeof(*o));
     o->n_items = p->last_items;
-    o->geo = (const float *)p->geo;
-    o->col = (const float *)p->col;
-    o->conic_c = p->conic_c;
-    o->depth = p->depth;
+    o->rec = (const float *)p->rec;
     o->rect = (const int32_t *)p->rect;
     o->radius = p->radius;
     o->pair_tile = p->pair_tile;
@@ -339,8 +331,6 @@ vbm_status vbm_plan_get_buffers(vbm_plan *p, vbm_plan_buffers *o)
     o->T_final = p->T_final;
     o->n_contrib = p->n_contrib;
     o->g_splat = p->g_splat;
-    o->cull = (const float *)p->cull;
-    o->tau = p->tau;
     o->seg_count = p->seg_len ? p->tile_queue + kQSegUnits : nullptr;
     o->checkpoint_slots = p->seg_len ? p->ckpt_cap : 0;
     return VBM_OK;

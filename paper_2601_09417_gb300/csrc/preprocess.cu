@@ -2,10 +2,10 @@
 //
 // One thread per (view, Gaussian) item.  Parameters are read from the SoA
 // layout P[14][stride], so the 14 loads of a warp are each one coalesced
-// 128-byte transaction.  The forward writes the per-item splat records the
-// rasteriser stages (geo = u, v, A, B; col = r, g, b, opacity; conic C), the
-// depth, the tile rectangle and the number of listed tiles, and adds the
-// item to the pair count of each listed tile.  The
+// 128-byte transaction.  The forward writes each item's splat record (one
+// 64-byte line: u, v, conic, colour, opacity, the culling box, the tile test's
+// bound and the depth; SplatRec), the tile rectangle and the listed tiles,
+// and adds the item to the pair count of each listed tile.  The
 // backward recomputes the forward state from the parameters (cheaper than
 // storing it) and sums the per-view contributions of a Gaussian in
 // registers, so the parameter gradient is written once, without atomics: the
@@ -117,9 +117,7 @@ __device__ __forceinline__ void project_state(const float *__restrict__ P, int64
 __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
                                  const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
                                  const int64_t *__restrict__ view_item_offset, int vb, int TX, int TY, int tw, int th,
-                                 int W, int H, float4 *__restrict__ geo, float4 *__restrict__ col, float *__restrict__ conic_c,
-                                 float4 *__restrict__ cull, float *__restrict__ tau_out, float *__restrict__ depth,
-                                 int4 *__restrict__ rect, int32_t *__restrict__ radius,
+                                 int W, int H, SplatRec *__restrict__ rec, int4 *__restrict__ rect, int32_t *__restrict__ radius,
                                  uint32_t *__restrict__ listed, uint32_t *__restrict__ tile_count,
                                  uint32_t *__restrict__ touched)
 {
@@ -138,9 +136,8 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
         const vbm_camera cam = cams[v];
         ProjState st;
         project_state(P, stride, g, cam, st);
-        float4 cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
-        col[item] = cg;
-        depth[item] = st.t[2];
+        SplatRec sr;
+        sr.c = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
         int4 rc = make_int4(0, 0, 0, 0);
         int r_int = 0;
         // A splat whose opacity is below the 1/255 compositing cut-off can never be
@@ -159,8 +156,7 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
             float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
             float u = cam.fx * st.xz + cam.cx;
             float vv = cam.fy * st.yz + cam.cy;
-            geo[item] = make_float4(u, vv, A, B);
-            conic_c[item] = C;
+            sr.g = make_float4(u, vv, A, B);
             // For the tile test and the compositing kernels' culling: tau =
             // 2 (ln(255 o) + margin); the bounding box of {q <= tau} has
             // half-widths sqrt(tau a) and sqrt(tau c) (the conic's determinant is
@@ -168,8 +164,8 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
             // B / A are rounded divisions of the stored conic.
             const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
             const float bc = __fdiv_rn(B, C), ba = __fdiv_rn(B, A);
-            cull[item] = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc, ba);
-            tau_out[item] = tau;
+            sr.cu = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc, ba);
+            sr.x = make_float4(C, tau, st.t[2], 0.f);
             r_int = (int)r;
             int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
             int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
@@ -182,11 +178,11 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
             tt = TileTest{u, vv, A, B, C, bc, ba, tau, rc};
             has_tiles = true;
         } else {
-            geo[item] = make_float4(0.f, 0.f, 0.f, 0.f);
-            conic_c[item] = 0.f;
-            cull[item] = make_float4(0.f, 0.f, 0.f, 0.f);
-            tau_out[item] = -1.f;
+            sr.g = make_float4(0.f, 0.f, 0.f, 0.f);
+            sr.cu = make_float4(0.f, 0.f, 0.f, 0.f);
+            sr.x = make_float4(0.f, -1.f, st.t[2], 0.f);
         }
+        rec[item] = sr;
         rect[item] = rc;
         radius[item] = r_int;
     }
@@ -340,8 +336,8 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     k_preprocess_fwd<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
                                               p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
                                               p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
-                                              p->desc.tile_h, p->desc.width, p->desc.height, p->geo, p->col,
-                                              p->conic_c, p->cull, p->tau, p->depth, p->rect, p->radius,
+                                              p->desc.tile_h, p->desc.width, p->desc.height, p->rec, p->rect,
+                                              p->radius,
                                               p->listed, p->tile_count, p->touched);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);

@@ -208,17 +208,16 @@ __device__ __forceinline__ uint32_t load_index(const uint32_t *__restrict__ pair
     return idx < end ? pair_item[idx] : kNoItem;
 }
 
-__device__ __forceinline__ Entry gather_entry(uint32_t it, const float4 *__restrict__ geo,
-                                              const float4 *__restrict__ col, const float *__restrict__ conic_c,
-                                              const float4 *__restrict__ cull)
+__device__ __forceinline__ Entry gather_entry(uint32_t it, const SplatRec *__restrict__ rec)
 {
     Entry e;
     e.it = it;
     if (it != kNoItem) {
-        e.g = geo[it];
-        e.cc = conic_c[it];
-        e.c = col[it];
-        e.cu = cull[it];
+        const SplatRec *r = rec + it;
+        e.g = r->g;
+        e.c = r->c;
+        e.cu = r->cu;
+        e.cc = r->x.x;
     } else {
         e.g = e.c = e.cu = make_float4(0.f, 0.f, 0.f, 0.f);
         e.cc = 0.f;
@@ -228,17 +227,16 @@ __device__ __forceinline__ Entry gather_entry(uint32_t it, const float4 *__restr
 
 // Start copying the lane's entry `it` of a round into stage st; one copy
 // group per round, empty when there is no entry.
-__device__ __forceinline__ void stage_entry(RawStages &rs, int st, uint32_t it, const float4 *__restrict__ geo,
-                                            const float4 *__restrict__ col, const float *__restrict__ conic_c,
-                                            const float4 *__restrict__ cull)
+__device__ __forceinline__ void stage_entry(RawStages &rs, int st, uint32_t it, const SplatRec *__restrict__ rec)
 {
     const int lane = threadIdx.x & 31;
     rs.it[st][lane] = it;
     if (it != kNoItem) {
-        cp_async16(&rs.geo[st][lane], geo + it);
-        cp_async16(&rs.col[st][lane], col + it);
-        cp_async16(&rs.cull[st][lane], cull + it);
-        cp_async4(&rs.cc[st][lane], conic_c + it);
+        const SplatRec *r = rec + it;
+        cp_async16(&rs.geo[st][lane], &r->g);
+        cp_async16(&rs.col[st][lane], &r->c);
+        cp_async16(&rs.cull[st][lane], &r->cu);
+        cp_async4(&rs.cc[st][lane], &r->x.x);
     }
     cp_async_commit();
 }
@@ -319,9 +317,7 @@ struct PixState {
 // through its asynchronous shared-memory stages.
 template <int PPT, int GL, bool COLOR = true>
 __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__restrict__ ranges,
-                                           const uint32_t *__restrict__ pair_item, const float4 *__restrict__ geo,
-                                           const float4 *__restrict__ col, const float *__restrict__ conic_c,
-                                           const float4 *__restrict__ cull, int W, int H, int vb, float bg0,
+                                           const uint32_t *__restrict__ pair_item, const SplatRec *__restrict__ rec, int W, int H, int vb, float bg0,
                                            float bg1, float bg2, float *__restrict__ img,
                                            float *__restrict__ alpha_out, float *__restrict__ T_final,
                                            int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval,
@@ -356,11 +352,11 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
     if constexpr (kAsync) {
 #pragma unroll
         for (int d = 0; d < kStages - 1; d++)
-            stage_entry(*rs, d, load_index(pair_item, rg.x + 32 * d + lane, rg.y), geo, col, conic_c, cull);
+            stage_entry(*rs, d, load_index(pair_item, rg.x + 32 * d + lane, rg.y), rec);
         it_next = load_index(pair_item, rg.x + 32 * (kStages - 1) + lane, rg.y);
     } else {
-        cur = gather_entry(load_index(pair_item, rg.x + lane, rg.y), geo, col, conic_c, cull);
-        nxt = gather_entry(load_index(pair_item, rg.x + 32 + lane, rg.y), geo, col, conic_c, cull);
+        cur = gather_entry(load_index(pair_item, rg.x + lane, rg.y), rec);
+        nxt = gather_entry(load_index(pair_item, rg.x + 32 + lane, rg.y), rec);
         it_next = load_index(pair_item, rg.x + 64 + lane, rg.y);
     }
     for (int r = 0; r < n_rounds; r++) {
@@ -379,13 +375,13 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
         }
         uint32_t m;
         if constexpr (kAsync) {
-            stage_entry(*rs, (r + kStages - 1) % kStages, it_next, geo, col, conic_c, cull);
+            stage_entry(*rs, (r + kStages - 1) % kStages, it_next, rec);
             it_next = load_index(pair_item, rg.x + 32 * (r + kStages) + lane, rg.y);
             cp_async_wait<kStages - 1>();
             m = commit_entry<PPT, GL>(read_entry(*rs, r % kStages), 32 * r + lane + 1, wg, s, nullptr);
         } else {
             const uint32_t it_after = load_index(pair_item, rg.x + 32 * (r + 3) + lane, rg.y);
-            const Entry nxt2 = gather_entry(it_next, geo, col, conic_c, cull);
+            const Entry nxt2 = gather_entry(it_next, rec);
             m = commit_entry<PPT, GL>(cur, 32 * r + lane + 1, wg, s, nullptr);
             cur = nxt;
             nxt = nxt2;
@@ -648,9 +644,7 @@ __device__ __forceinline__ bool pair_step(const WarpSlots &s, int j, float pxc, 
 
 template <int PPT, int GL>
 __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__restrict__ ranges,
-                                           const uint32_t *__restrict__ pair_item, const float4 *__restrict__ geo,
-                                           const float4 *__restrict__ col, const float *__restrict__ conic_c,
-                                           const float4 *__restrict__ cull, int W, int H, int vb, float bg0,
+                                           const uint32_t *__restrict__ pair_item, const SplatRec *__restrict__ rec, int W, int H, int vb, float bg0,
                                            float bg1, float bg2, const float *__restrict__ dimg,
                                            const float *__restrict__ dalpha, const float *__restrict__ T_final,
                                            const int32_t *__restrict__ n_contrib, float *__restrict__ gs,
@@ -671,10 +665,10 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     float pyc[PPT], T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], Q[PPT];
     int nc[PPT];
     int my_max = 0;
-    PixState<PPT> rec;
+    PixState<PPT> replay;
     if (!T_final && seg < 0)   // recompute mode, whole list: replay the forward decisions of this region
-        fwd_region<PPT, GL, false>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, nullptr,
-                                   nullptr, nullptr, nullptr, nullptr, s, &rec, &rs);
+        fwd_region<PPT, GL, false>(wg, ranges, pair_item, rec, W, H, vb, bg0, bg1, bg2, nullptr,
+                                   nullptr, nullptr, nullptr, nullptr, s, &replay, &rs);
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         const int py = wg.py0 + k;
@@ -693,8 +687,8 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
                 T[k] = f.x;
                 nc[k] = __float_as_int(f.y);
             } else {
-                T[k] = rec.T[k];
-                nc[k] = rec.last[k];
+                T[k] = replay.T[k];
+                nc[k] = replay.last[k];
             }
             dC0[k] = dimg[(v * 3 + 0) * HW + pix];
             dC1[k] = dimg[(v * 3 + 1) * HW + pix];
@@ -737,10 +731,10 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
     auto round_end = [&](int r) { return rg.x + wtop - 32 * r; };
     auto round_item = [&](int r) { return r < n_rounds ? load_index(pair_item, round_idx(r), round_end(r)) : kNoItem; };
 #pragma unroll
-    for (int d = 0; d < kStages - 1; d++) stage_entry(rs, d, round_item(d), geo, col, conic_c, cull);
+    for (int d = 0; d < kStages - 1; d++) stage_entry(rs, d, round_item(d), rec);
     uint32_t it_next = round_item(kStages - 1);
     for (int r = 0; r < n_rounds; r++) {
-        stage_entry(rs, (r + kStages - 1) % kStages, it_next, geo, col, conic_c, cull);
+        stage_entry(rs, (r + kStages - 1) % kStages, it_next, rec);
         it_next = round_item(r + kStages);
         cp_async_wait<kStages - 1>();
         const Entry cur = read_entry(rs, r % kStages);
@@ -851,8 +845,7 @@ template <int PPT, int GL, bool PERSIST>
 __global__ void __launch_bounds__(kWarps * 32)
     k_raster_fwd(const int *__restrict__ order, int *__restrict__ queue, int n_items_w, int n_regions,
                  const int2 *__restrict__ ranges, const uint32_t *__restrict__ pair_item,
-                 const float4 *__restrict__ geo, const float4 *__restrict__ col, const float *__restrict__ conic_c,
-                 const float4 *__restrict__ cull, int W, int H, int tw, int th, int TX, int TY, int vb, float bg0,
+                 const SplatRec *__restrict__ rec, int W, int H, int tw, int th, int TX, int TY, int vb, float bg0,
                  float bg1, float bg2, float *__restrict__ img, float *__restrict__ alpha_out,
                  float *__restrict__ T_final, int32_t *__restrict__ n_contrib, int32_t *__restrict__ n_eval,
                  float4 *__restrict__ ckpt, const int *__restrict__ ckpt_base, int seg_len)
@@ -867,7 +860,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         const WarpGeom wg = warp_geom<PPT, GL>(tile, q % n_regions, tw, th, TX, TY, W, H);
         if (wg.x0 > wg.x1 || wg.y0 > wg.y1) continue;            // region outside the image
         const int cb = ckpt_base ? ckpt_base[tile] : -1;
-        fwd_region<PPT, GL>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, img, alpha_out,
+        fwd_region<PPT, GL>(wg, ranges, pair_item, rec, W, H, vb, bg0, bg1, bg2, img, alpha_out,
                             T_final, n_contrib, n_eval, s, nullptr, nullptr,
                             cb >= 0 ? ckpt + (int64_t)cb * tile_px : nullptr, seg_len, tw, tile_px);
     }
@@ -877,8 +870,7 @@ template <int PPT, int GL, bool PERSIST>
 __global__ void __launch_bounds__(kWarps * 32)
     k_raster_bwd(const int *__restrict__ order, int *__restrict__ queue, int n_items_w, int n_regions,
                  const int2 *__restrict__ ranges, const uint32_t *__restrict__ pair_item,
-                 const float4 *__restrict__ geo, const float4 *__restrict__ col, const float *__restrict__ conic_c,
-                 const float4 *__restrict__ cull, int W, int H, int tw, int th, int TX, int TY, int vb, float bg0,
+                 const SplatRec *__restrict__ rec, int W, int H, int tw, int th, int TX, int TY, int vb, float bg0,
                  float bg1, float bg2, const float *__restrict__ dimg, const float *__restrict__ dalpha,
                  const float *__restrict__ T_final, const int32_t *__restrict__ n_contrib, float *__restrict__ gs,
                  const int *__restrict__ seg_count, const int2 *__restrict__ seg_units,
@@ -915,7 +907,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
         const WarpGeom wg = warp_geom<PPT, GL>(tile, q - u * n_regions, tw, th, TX, TY, W, H);
         if (wg.x0 > wg.x1 || wg.y0 > wg.y1) continue;
-        bwd_region<PPT, GL>(wg, ranges, pair_item, geo, col, conic_c, cull, W, H, vb, bg0, bg1, bg2, dimg, dalpha,
+        bwd_region<PPT, GL>(wg, ranges, pair_item, rec, W, H, vb, bg0, bg1, bg2, dimg, dalpha,
                             T_final, n_contrib, gs, s, raw[w], acc_s[w], seg,
                             seg >= 0 ? ckpt + (int64_t)ckpt_base[tile] * tile_px : nullptr, seg_len, tw, tile_px);
     }
@@ -965,14 +957,12 @@ vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
         const int grid = persistent_grid(k_raster_fwd<PPT, GL, true>, n_items_w);
         k_raster_fwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
-            p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col,
-            p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
+            p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
             bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib,
             p->prof_n_eval, p->ckpt, p->seg_len ? p->ckpt_base : nullptr, p->seg_len);
     } else {
         k_raster_fwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
-            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col, p->conic_c,
-            p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
+            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
             bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib, p->prof_n_eval, nullptr,
             nullptr, 0);
     }
@@ -993,14 +983,12 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
         const int grid = persistent_grid(k_raster_bwd<PPT, GL, true>, n_items_w);
         k_raster_bwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
-            p->tile_order, p->tile_queue + 1, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col,
-            p->conic_c, p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
+            p->tile_order, p->tile_queue + 1, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
             bg[0], bg[1], bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat, p->tile_queue,
             p->seg_len ? p->seg_units : nullptr, p->ckpt, p->ckpt_base, p->seg_len);
     } else {
         k_raster_bwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
-            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->geo, p->col, p->conic_c,
-            p->cull, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
+            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
             bg[2], dimg, dalpha, p->T_final, p->n_contrib, p->g_splat, nullptr, nullptr, nullptr, nullptr, 0);
     }
     VBM_LAUNCH("raster_bwd");

@@ -27,6 +27,17 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kCullMargin = 1e-3f;
 // Floats per item of the splat-gradient records: du dv dA dB dC dopacity dr dg db, padding.
 constexpr int kGradStride = 12;
+
+// A projected splat as the binning and compositing kernels read it: one
+// aligned 64-byte line per (view, Gaussian) item, so that a list entry costs
+// one contiguous 64-byte read (two sectors) whatever its position in memory.
+//   g  = u, v, conic A, conic B        c = r, g, b, opacity
+//   cu = half-widths of the alpha >= 1/255 box (x, y), B / C, B / A
+//   x  = conic C, tau = 2 (ln(255 o) + kCullMargin), camera depth, unused
+struct __align__(64) SplatRec {
+    float4 g, c, cu, x;
+};
+static_assert(sizeof(SplatRec) == 64, "one 64-byte line per splat");
 constexpr int kProfileEvents = 7;       // timing events a plan can record (vbm_plan_set_profile)
 
 #ifdef __CUDACC__
@@ -391,12 +402,7 @@ struct vbm_plan {
     int32_t *d_scene_views = nullptr;
 
     // per item
-    float4 *geo = nullptr;
-    float4 *col = nullptr;
-    float *conic_c = nullptr;
-    float4 *cull = nullptr;                  // [items] half-widths of the alpha >= 1/255 box, B / C, B / A
-    float *tau = nullptr;                    // [items] 2 (ln(255 o) + kCullMargin): bound of the tile test
-    float *depth = nullptr;
+    vbm::SplatRec *rec = nullptr;            // [items] the projected splat, one 64-byte line
     int4 *rect = nullptr;
     int32_t *radius = nullptr;
     uint32_t *listed = nullptr;              // [items] listed-tile word of the projection (listed_tiles)

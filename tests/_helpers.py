@@ -45,15 +45,21 @@ def to_device(P, cams, device="cuda"):
     return torch.from_numpy(np.ascontiguousarray(P)).to(device), vbm.cameras_to_device(camera_array(cams), device)
 
 
+def split_records(rec):
+    """The fields of a plan's per-item splat records ([n][16] float32, one 64-byte line
+    each: u v A B | r g b opacity | half-widths, B/C, B/A | C, tau, depth, -)."""
+    return dict(geo=np.ascontiguousarray(rec[:, 0:4]), col=np.ascontiguousarray(rec[:, 4:8]),
+                cull=np.ascontiguousarray(rec[:, 8:12]), conic_c=np.ascontiguousarray(rec[:, 12]),
+                tau=np.ascontiguousarray(rec[:, 13]), depth=np.ascontiguousarray(rec[:, 14]))
+
+
 def plan_state(plan, n_views):
     """Numpy copies of a plan's buffers after a forward (and backward) call."""
     b = plan.buffers()
     n = b.n_items
     st = dict(n_items=n)
-    st["geo"] = read_device(b.geo, (n, 4), np.float32)
-    st["col"] = read_device(b.col, (n, 4), np.float32)
-    st["conic_c"] = read_device(b.conic_c, (n,), np.float32)
-    st["depth"] = read_device(b.depth, (n,), np.float32)
+    rec = read_device(b.rec, (n, 16), np.float32)
+    st.update(split_records(rec))
     st["rect"] = read_device(b.rect, (n, 4), np.int32)
     st["radius"] = read_device(b.radius, (n,), np.int32)
     n_pairs = int(read_device(b.n_pairs, (1,), np.int64)[0])
@@ -67,8 +73,6 @@ def plan_state(plan, n_views):
         st["T_final"] = read_device(b.T_final, (plan.n_views, plan.height, plan.width), np.float32)
         st["n_contrib"] = read_device(b.n_contrib, (plan.n_views, plan.height, plan.width), np.int32)
     st["g_splat"] = np.ascontiguousarray(read_device(b.g_splat, (n, 12), np.float32)[:, :9].T)
-    st["cull"] = read_device(b.cull, (n, 4), np.float32)
-    st["tau"] = read_device(b.tau, (n,), np.float32)
     st["seg_count"] = read_device(b.seg_count, (4,), np.int32) if b.seg_count else None
     st["checkpoint_slots"] = int(b.checkpoint_slots)
     return st

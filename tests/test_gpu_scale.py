@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import oracle_bank, rel_group_error
+from _helpers import oracle_bank, rel_group_error, split_records
 from oracle import raster as oraster
 
 pytestmark = pytest.mark.gpu
@@ -71,13 +71,11 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute, seg):
     # --- binning of view 0, bit-exact given the GPU's rectangles and depths
     n0 = int(so[1]) if w.view_scene is None else int(so[int(w.view_scene[0]) + 1] - so[int(w.view_scene[0])])
     rect0 = vbm.device_tensor(b.rect, (n0, 4), np.int32).cpu().numpy()
-    depth0 = vbm.device_tensor(b.depth, (n0,), np.float32).cpu().numpy().astype(np.float64)
-    geo0 = vbm.device_tensor(b.geo, (n0, 4), np.float32).cpu().numpy()
-    rec0 = np.stack([geo0[:, 0], geo0[:, 1], geo0[:, 2], geo0[:, 3],
-                     vbm.device_tensor(b.conic_c, (n0,), np.float32).cpu().numpy(),
-                     vbm.device_tensor(b.cull, (n0, 4), np.float32).cpu().numpy()[:, 2],
-                     vbm.device_tensor(b.cull, (n0, 4), np.float32).cpu().numpy()[:, 3],
-                     vbm.device_tensor(b.tau, (n0,), np.float32).cpu().numpy()], axis=1)
+    f0 = split_records(vbm.device_tensor(b.rec, (n0, 16), np.float32).cpu().numpy())
+    depth0 = f0["depth"].astype(np.float64)
+    geo0 = f0["geo"]
+    rec0 = np.stack([geo0[:, 0], geo0[:, 1], geo0[:, 2], geo0[:, 3], f0["conic_c"], f0["cull"][:, 2],
+                     f0["cull"][:, 3], f0["tau"]], axis=1)
     tiles0, items0, _ = oraster.bin_sort(np.zeros(n0, dtype=np.int32), rect0, depth0, TX, TY, 1, splat32=rec0,
                                          tile=tile, image=(W, H))
     end0 = int(ranges[:TX * TY, 1].max())
@@ -97,9 +95,10 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute, seg):
         ranges_c[t] = (len(items_c), len(items_c) + lst.size)
         items_c.extend(remap[int(it)] for it in lst)
     n_items = b.n_items
-    g = _take(vbm, b.geo, (n_items, 4), np.float32, used).astype(np.float64)
-    cc = _take(vbm, b.conic_c, (n_items,), np.float32, used).astype(np.float64)
-    col = _take(vbm, b.col, (n_items, 4), np.float32, used).astype(np.float64)
+    fu = split_records(_take(vbm, b.rec, (n_items, 16), np.float32, used))
+    g = fu["geo"].astype(np.float64)
+    cc = fu["conic_c"].astype(np.float64)
+    col = fu["col"].astype(np.float64)
     splat = np.stack([g[:, 0], g[:, 1], g[:, 2], g[:, 3], cc, col[:, 3]], axis=1)
     ref = oraster.render(V, W, H, tile[0], tile[1], ranges_c, np.asarray(items_c, dtype=np.int32), splat,
                          col[:, :3], np.array(bg))

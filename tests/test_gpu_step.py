@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import read_device, rel_group_error, scene, to_device
+from _helpers import read_device, rel_group_error, scene, split_records, to_device
 from oracle import adam as oadam
 from oracle import loss as oloss
 from oracle import raster as oraster
@@ -243,9 +243,7 @@ def test_gradient_central_differences_c1_full_size(cuda_lib):
                   pair_item=vbm.device_tensor(b.pair_item, (n_pairs,), np.int32).clone(),
                   pair_tile=vbm.device_tensor(b.pair_tile, (n_pairs,), np.int32).clone(),
                   rect=read_device(b.rect, (b.n_items, 4), np.int32),
-                  geo=read_device(b.geo, (b.n_items, 4), np.float32),
-                  conic_c=read_device(b.conic_c, (b.n_items,), np.float32),
-                  col=read_device(b.col, (b.n_items, 4), np.float32))
+                  **split_records(read_device(b.rec, (b.n_items, 16), np.float32)))
         return L, st
 
     def own_alpha(st, item):
