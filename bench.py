@@ -76,6 +76,8 @@ def parse():
                     help="list segment length of the persistent backward (0 = library default, -1 = never split)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps of the batched step without timing (for ncu captures)")
+    ap.add_argument("--views", type=int, default=0,
+                    help="use only the first N views of a single-volume workload (smaller ncu cases)")
     return ap.parse_args()
 
 
@@ -545,6 +547,13 @@ def main():
     vbm.load()
 
     w = make_workload(args.config, device)
+    if args.views:
+        if w.scene_offset is not None:
+            raise ValueError("--views applies to single-volume workloads")
+        w.cam_records, w.cams = w.cam_records[:args.views], w.cams[:args.views]
+        w.targets = w.targets[:args.views].contiguous()
+        w.cfg = dict(w.cfg, views=args.views, workload=w.cfg["workload"] + " (first %d views)" % args.views)
+    torch.cuda.empty_cache()    # the build's workspace, kept by torch's caching allocator
     cfg, params, n, recs, cams, targets = w.cfg, w.params, w.n, w.cam_records, w.cams, w.targets
     V, H, W = targets.shape[0], targets.shape[2], targets.shape[3]
     batch = dict(scene_offset=w.scene_offset, view_scene=w.view_scene, extent=workload_extent(cfg),

@@ -292,6 +292,7 @@ vbm_status vbm_raster_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     p->last_view_begin = vb;
     p->last_view_count = vc;
     p->last_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
+    p->g_splat_clear = p->bwd_seen;   // the projection zeroes the items' splat-gradient records
     record_event(p->prof_ev[4], st);
     s = preprocess_fwd(p, params, stride, cams, vb, vc, st);
     record_event(p->prof_ev[5], st);

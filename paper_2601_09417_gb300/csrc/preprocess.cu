@@ -114,87 +114,109 @@ __device__ __forceinline__ void project_state(const float *__restrict__ P, int64
     project_view(cam, st);
 }
 
+// Views [vb + blockIdx.y vpt, + vpt) of the call (clipped to vb + vc), one
+// Gaussian per thread: the view-independent state (rotation, 3D covariance,
+// opacity) is built once and projected for each of those views.  With
+// several scenes vpt is 1 (consecutive views may render different scenes).
+template <bool MULTI>
 __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
                                  const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
-                                 const int64_t *__restrict__ view_item_offset, int vb, int TX, int TY, int tw, int th,
-                                 int W, int H, SplatRec *__restrict__ rec, int4 *__restrict__ rect, int32_t *__restrict__ radius,
+                                 const int64_t *__restrict__ view_item_offset, int vb, int vc, int vpt, int TX,
+                                 int TY, int tw, int th, int W, int H, SplatRec *__restrict__ rec,
+                                 float4 *__restrict__ gs, int4 *__restrict__ rect, int32_t *__restrict__ radius,
                                  uint32_t *__restrict__ listed, uint32_t *__restrict__ tile_count,
                                  uint32_t *__restrict__ touched)
 {
-    const int v = vb + blockIdx.y;
-    const int scene = view_scene ? view_scene[v] : 0;
+    const int v_begin = vb + blockIdx.y * (MULTI ? vpt : 1);
+    const int v_end = MULTI ? min(v_begin + vpt, vb + vc) : v_begin + 1;
+    const int scene = view_scene ? view_scene[v_begin] : 0;
     const int64_t g0 = scene_offset[scene];
     const int64_t ns = scene_offset[scene + 1] - g0;
     const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = gl < ns;        // every lane stays for the warp-wide tile count
-    TileTest tt = {};
-    bool has_tiles = false;
-    int64_t item = 0;
+    const int64_t g = g0 + gl;
+    ProjState st;
+    float4 cg = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
-        const int64_t g = g0 + gl;
-        item = view_item_offset[v] - view_item_offset[vb] + gl;
-        const vbm_camera cam = cams[v];
-        ProjState st;
-        project_state(P, stride, g, cam, st);
-        SplatRec sr;
-        sr.c = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
-        int4 rc = make_int4(0, 0, 0, 0);
-        int r_int = 0;
-        // A splat whose opacity is below the 1/255 compositing cut-off can never be
-        // blended (alpha = o G <= o), so it gets no tiles.
-        if (!st.culled && st.opac >= kAlphaMin) {
-            float inv_det = 1.0f / st.det;
-            float A = st.c * inv_det, B = -st.b * inv_det, C = st.a * inv_det;
-            float mid = 0.5f * (st.a + st.c);
-            float disc = mid * mid - st.det;
-            float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
-            // Extent of the ellipse where o e^power >= 1/255 (capped at 3 sigma):
-            // pixels beyond it skip this splat anyway, so fewer tiles list it.
-            const float k = fminf(kRadiusSigmas, sqrtf(2.f * logf(255.f * st.opac)));
-            // Bounded so the integer rectangle arithmetic cannot overflow; any
-            // radius above 2^24 already spans every image narrower than 6.7M px.
-            float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
-            float u = cam.fx * st.xz + cam.cx;
-            float vv = cam.fy * st.yz + cam.cy;
-            sr.g = make_float4(u, vv, A, B);
-            // For the tile test and the compositing kernels' culling: tau =
-            // 2 (ln(255 o) + margin); the bounding box of {q <= tau} has
-            // half-widths sqrt(tau a) and sqrt(tau c) (the conic's determinant is
-            // 1 / det), slightly widened; the edge minimisers' ratios B / C and
-            // B / A are rounded divisions of the stored conic.
-            const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
-            const float bc = __fdiv_rn(B, C), ba = __fdiv_rn(B, A);
-            sr.cu = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc, ba);
-            sr.x = make_float4(C, tau, st.t[2], 0.f);
-            r_int = (int)r;
-            int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
-            int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
-            // floor division by the tile size, a power of two: arithmetic shifts
-            const int lw = __ffs(tw) - 1, lh = __ffs(th) - 1;
-            rc.x = min(max((fu - r_int) >> lw, 0), TX);
-            rc.z = min(max(((fu + r_int) >> lw) + 1, 0), TX);
-            rc.y = min(max((fv - r_int) >> lh, 0), TY);
-            rc.w = min(max(((fv + r_int) >> lh) + 1, 0), TY);
-            tt = TileTest{u, vv, A, B, C, bc, ba, tau, rc};
-            has_tiles = true;
-        } else {
-            sr.g = make_float4(0.f, 0.f, 0.f, 0.f);
-            sr.cu = make_float4(0.f, 0.f, 0.f, 0.f);
-            sr.x = make_float4(0.f, -1.f, st.t[2], 0.f);
-        }
-        rec[item] = sr;
-        rect[item] = rc;
-        radius[item] = r_int;
+        project_base(P, stride, g, st);
+        cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
     }
-    // tiles of the rectangle that pass the exact tile test (the image size is
-    // the plan's, as in the pair placement, so both take the same decisions),
-    // counted per tile and recorded per item for the placement
-    uint32_t n_listed = 0;
-    const uint32_t word = listed_tiles(has_tiles, tt, tw, th, W, H, tile_count,
-                                       (uint32_t)(v - vb) * (uint32_t)(TX * TY), TX, &n_listed);
-    if (!valid) return;
-    listed[item] = word;
-    if (touched) touched[item] = n_listed;   // pairs of the item (radix-sort ordering)
+    for (int v = v_begin; v < v_end; v++) {
+        TileTest tt = {};
+        bool has_tiles = false;
+        int64_t item = 0;
+        if (valid) {
+            item = view_item_offset[v] - view_item_offset[vb] + gl;
+            const vbm_camera cam = cams[v];
+            project_view(cam, st);
+            SplatRec sr;
+            sr.c = cg;
+            int4 rc = make_int4(0, 0, 0, 0);
+            int r_int = 0;
+            // A splat whose opacity is below the 1/255 compositing cut-off can never be
+            // blended (alpha = o G <= o), so it gets no tiles.
+            if (!st.culled && st.opac >= kAlphaMin) {
+                float inv_det = 1.0f / st.det;
+                float A = st.c * inv_det, B = -st.b * inv_det, C = st.a * inv_det;
+                float mid = 0.5f * (st.a + st.c);
+                float disc = mid * mid - st.det;
+                float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
+                // Extent of the ellipse where o e^power >= 1/255 (capped at 3 sigma):
+                // pixels beyond it skip this splat anyway, so fewer tiles list it.
+                const float k = fminf(kRadiusSigmas, sqrtf(2.f * logf(255.f * st.opac)));
+                // Bounded so the integer rectangle arithmetic cannot overflow; any
+                // radius above 2^24 already spans every image narrower than 6.7M px.
+                float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
+                float u = cam.fx * st.xz + cam.cx;
+                float vv = cam.fy * st.yz + cam.cy;
+                sr.g = make_float4(u, vv, A, B);
+                // For the tile test and the compositing kernels' culling: tau =
+                // 2 (ln(255 o) + margin); the bounding box of {q <= tau} has
+                // half-widths sqrt(tau a) and sqrt(tau c) (the conic's determinant is
+                // 1 / det), slightly widened; the edge minimisers' ratios B / C and
+                // B / A are rounded divisions of the stored conic.
+                const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
+                const float bc = __fdiv_rn(B, C), ba = __fdiv_rn(B, A);
+                sr.cu = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc,
+                                    ba);
+                sr.x = make_float4(C, tau, st.t[2], 0.f);
+                r_int = (int)r;
+                int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
+                int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
+                // floor division by the tile size, a power of two: arithmetic shifts
+                const int lw = __ffs(tw) - 1, lh = __ffs(th) - 1;
+                rc.x = min(max((fu - r_int) >> lw, 0), TX);
+                rc.z = min(max(((fu + r_int) >> lw) + 1, 0), TX);
+                rc.y = min(max((fv - r_int) >> lh, 0), TY);
+                rc.w = min(max(((fv + r_int) >> lh) + 1, 0), TY);
+                tt = TileTest{u, vv, A, B, C, bc, ba, tau, rc};
+                has_tiles = true;
+            } else {
+                sr.g = make_float4(0.f, 0.f, 0.f, 0.f);
+                sr.cu = make_float4(0.f, 0.f, 0.f, 0.f);
+                sr.x = make_float4(0.f, -1.f, st.t[2], 0.f);
+            }
+            rec[item] = sr;
+            if (gs) {   // the item's splat-gradient record, zero for the backward's atomics
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                gs[3 * item] = z;
+                gs[3 * item + 1] = z;
+                gs[3 * item + 2] = z;
+            }
+            rect[item] = rc;
+            radius[item] = r_int;
+        }
+        // tiles of the rectangle that pass the exact tile test (the image size is
+        // the plan's, as in the pair placement, so both take the same decisions),
+        // counted per tile and recorded per item for the placement
+        uint32_t n_listed = 0;
+        const uint32_t word = listed_tiles(has_tiles, tt, tw, th, W, H, tile_count,
+                                           (uint32_t)(v - vb) * (uint32_t)(TX * TY), TX, &n_listed);
+        if (valid) {
+            listed[item] = word;
+            if (touched) touched[item] = n_listed;   // pairs of the item (radix-sort ordering)
+        }
+    }
 }
 
 // Chain rule from the per-item splat gradient (du, dv, dA, dB, dC, dopacity,
@@ -330,15 +352,25 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
 vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, const vbm_camera *cams, int vb, int vc,
                           cudaStream_t st)
 {
-    dim3 block(256);
-    dim3 grid((unsigned)((p->max_scene + 255) / 256), (unsigned)vc);
     if (p->max_scene == 0) return VBM_OK;
-    k_preprocess_fwd<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
-                                              p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
-                                              p->d_view_item_offset, vb, p->TX, p->TY, p->desc.tile_w,
-                                              p->desc.tile_h, p->desc.width, p->desc.height, p->rec, p->rect,
-                                              p->radius,
-                                              p->listed, p->tile_count, p->touched);
+    // views per thread: as many as keep about four waves of threads (the
+    // view-independent state is then built once per Gaussian and view group)
+    int vpt = 1;
+    if (p->desc.n_scenes == 1) {
+        const int64_t wave = (int64_t)num_sms() * 2048;
+        vpt = (int)std::max<int64_t>(1, std::min<int64_t>(vc, p->max_scene * vc / (4 * wave)));
+    }
+    dim3 block(256);
+    dim3 grid((unsigned)((p->max_scene + 255) / 256), (unsigned)((vc + vpt - 1) / vpt));
+    // plans that have run a backward get their splat-gradient records zeroed
+    // here (render-only plans skip the writes; a plan's first backward clears
+    // them itself)
+    float4 *gs = p->bwd_seen ? reinterpret_cast<float4 *>(p->g_splat) : nullptr;
+    auto kernel = vpt > 1 ? k_preprocess_fwd<true> : k_preprocess_fwd<false>;
+    kernel<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
+                                   p->desc.n_scenes > 1 ? p->d_view_scene : nullptr, p->d_view_item_offset, vb, vc,
+                                   vpt, p->TX, p->TY, p->desc.tile_w, p->desc.tile_h, p->desc.width, p->desc.height,
+                                   p->rec, gs, p->rect, p->radius, p->listed, p->tile_count, p->touched);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);
     return VBM_OK;

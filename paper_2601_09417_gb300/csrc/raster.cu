@@ -1022,7 +1022,12 @@ vbm_status raster_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
 vbm_status raster_bwd(vbm_plan *p, const float *, int64_t, int vb, int vc, const float bg[3], const float *dimg,
                       const float *dalpha, float *, cudaStream_t st)
 {
-    VBM_CUDA(cudaMemsetAsync(p->g_splat, 0, sizeof(float) * kGradStride * p->last_items, st));
+    // the forward's projection zeroed the splat-gradient records (once the
+    // plan has run a backward); otherwise, and for a second backward of the
+    // same forward, they are cleared here
+    if (!p->g_splat_clear) VBM_CUDA(cudaMemsetAsync(p->g_splat, 0, sizeof(float) * kGradStride * p->last_items, st));
+    p->g_splat_clear = false;
+    p->bwd_seen = true;
     VBM_RASTER_DISPATCH(launch_bwd, true, p, vb, vc, bg, dimg, dalpha, st)
 }
 

@@ -407,6 +407,8 @@ struct vbm_plan {
     int32_t *radius = nullptr;
     uint32_t *listed = nullptr;              // [items] listed-tile word of the projection (listed_tiles)
     float *g_splat = nullptr;               // [items][kGradStride]
+    bool g_splat_clear = false;             // host: zeroed by the last forward, no backward since
+    bool bwd_seen = false;                  // host: a backward has run on this plan
 
     // pairs
     uint64_t *pair_key = nullptr;            // [pairs] (depth bits << 32 | item), bucketed by tile
