@@ -248,11 +248,12 @@ def profiled_traffic(kernel, workload_key):
 
 # ------------------------------------------------------- algorithmic work
 
-def step_work(N, V, HW, n_dup, p_fwd, p_bwd, recompute):
+def step_work(N, items, V, HW, n_dup, p_fwd, p_bwd, recompute):
     """Algorithmic work per step of each kernel group (FP32 FLOP, ex2/rcp evaluations, HBM bytes),
-    the counts of the method itself (N Gaussians, V views of HW pixels, n_dup (view, tile,
-    Gaussian) pairs, p_fwd / p_bwd evaluated pairs) and not of this implementation."""
-    items = N * V
+    the counts of the method itself (N Gaussians, `items` (view, Gaussian) pairs (N V for one
+    scene; each view its own scene's Gaussians in a batch of scenes), V views of HW pixels,
+    n_dup (view, tile, Gaussian) pairs, p_fwd / p_bwd evaluated pairs) and not of this
+    implementation."""
     px = V * HW
     state = 0 if recompute else 8                      # T_final and the last contributor per pixel
     return {
@@ -745,7 +746,8 @@ def main():
 
     # ------------------------------------------------------------- roofline
     n_pairs = float(np.mean(pairs))
-    work = step_work(n, V, H * W, n_pairs, p_fwd / args.steps, p_bwd / args.steps, batch["recompute"])
+    n_items = vbm.batch_items([0, n] if w.scene_offset is None else w.scene_offset, V, w.view_scene)
+    work = step_work(n, n_items, V, H * W, n_pairs, p_fwd / args.steps, p_bwd / args.steps, batch["recompute"])
     kernels, lb_sum = {}, 0.0
     for g in ("projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam"):
         lb, bound = lower_bound_ms(work[g], peaks)

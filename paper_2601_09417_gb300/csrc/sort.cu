@@ -318,31 +318,34 @@ __device__ __forceinline__ void sort8(uint64_t (&v)[8])
     cswap(v[1], v[2]); cswap(v[3], v[4]); cswap(v[5], v[6]);
 }
 
-// Outputs [8t, 8t + 8) of the merge of the two sorted runs of length L that
-// contain position 8t (ties: the first run first).
-__device__ __forceinline__ void merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int L, int t)
+// Outputs [8t, 8t + 8) of the merge of the two sorted runs that contain
+// position 8t: [base, base + L) and [base + L, base + 2L), both clipped to the
+// first n8 positions (ties: the first run first).
+__device__ __forceinline__ void merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int L, int t,
+                                           int n8)
 {
     const int o = t * kMergeE;
     const int base = o & ~(2 * L - 1);
     const int d = o - base;
     const uint64_t *A = src, *B = src;
     const int a0 = base, b0 = base + L;
-    int lo = max(0, d - L), hi = min(d, L);
+    const int La = min(L, n8 - a0), Lb = max(0, min(L, n8 - b0));
+    int lo = max(0, d - Lb), hi = min(d, La);
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (A[padded(a0 + mid)] <= B[padded(b0 + d - 1 - mid)]) lo = mid + 1;
         else hi = mid;
     }
     int i = lo, j = d - lo;
-    uint64_t a = i < L ? A[padded(a0 + i)] : 0ull, b = j < L ? B[padded(b0 + j)] : 0ull;
+    uint64_t a = i < La ? A[padded(a0 + i)] : 0ull, b = j < Lb ? B[padded(b0 + j)] : 0ull;
 #pragma unroll
     for (int e = 0; e < kMergeE; e++) {
-        const bool ta = j >= L || (i < L && a <= b);
+        const bool ta = j >= Lb || (i < La && a <= b);
         dst[padded(o + e)] = ta ? a : b;
         i += ta;
         j += !ta;
         const int next = ta ? a0 + i : b0 + j;
-        const bool more = ta ? i < L : j < L;
+        const bool more = ta ? i < La : j < Lb;
         const uint64_t v = more ? src[padded(next)] : 0ull;
         a = ta ? v : a;
         b = ta ? b : v;
@@ -358,17 +361,17 @@ __device__ __forceinline__ void group_sync()
 
 // Sorts keys g[0, n) (n <= G * kMergeE) of a group of G threads (thread t of
 // the group) with shared buffers s0, s1 of padded(G * kMergeE) words each;
-// returns the buffer that holds the sorted keys, padded to a power of two
-// with ~0.  Ends with a group barrier.
+// returns the buffer that holds the sorted keys, followed by ~0 up to the
+// next multiple of kMergeE (runs are clipped there, so a list just above a
+// power of two merges no padding).  Ends with a group barrier.
 template <int G, bool BLOCK>
 __device__ __forceinline__ uint64_t *group_merge_sort(const uint64_t *__restrict__ g, int n, uint64_t *s0,
                                                       uint64_t *s1, int t)
 {
-    int N = kMergeE;
-    while (N < n) N <<= 1;
-    for (int i = t; i < N; i += G) s1[padded(i)] = i < n ? g[i] : kPadKey;
+    const int n8 = (n + kMergeE - 1) / kMergeE * kMergeE;
+    for (int i = t; i < n8; i += G) s1[padded(i)] = i < n ? g[i] : kPadKey;
     group_sync<BLOCK>();
-    const int T = N / kMergeE;
+    const int T = n8 / kMergeE;
     if (t < T) {
         uint64_t v[kMergeE];
 #pragma unroll
@@ -379,8 +382,8 @@ __device__ __forceinline__ uint64_t *group_merge_sort(const uint64_t *__restrict
     }
     group_sync<BLOCK>();
     uint64_t *src = s0, *dst = s1;
-    for (int L = kMergeE; L < N; L <<= 1) {
-        if (t < T) merge_pass(src, dst, L, t);
+    for (int L = kMergeE; L < n8; L <<= 1) {
+        if (t < T) merge_pass(src, dst, L, t, n8);
         group_sync<BLOCK>();
         uint64_t *x = src;
         src = dst;
