@@ -610,12 +610,21 @@ def main():
     torch.cuda.synchronize()
     n_eval = torch.zeros((V, H, W), dtype=torch.int32, device=device)
     bufs = ft.plan.buffers()
-    if bufs.n_contrib:
-        ft.plan.set_profile(kev, n_eval)
-        n_contrib = vbm.device_tensor(bufs.n_contrib, (V, H, W), np.int32)
-    else:   # recompute mode keeps no contributor counts: the profiling hook writes them
-        n_contrib = torch.zeros((V, H, W), dtype=torch.int32, device=device)
-        ft.plan.set_profile(kev, n_eval, n_contrib)
+    own_contrib = bool(bufs.n_contrib)
+    n_contrib = (vbm.device_tensor(bufs.n_contrib, (V, H, W), np.int32) if own_contrib else
+                 torch.zeros((V, H, W), dtype=torch.int32, device=device))
+
+    def count_pairs():
+        """(P_fwd, P_bwd) of the current Gaussians: one untimed forward with the per-pixel
+        count hooks set (recompute plans keep no contributor counts: the hook writes them);
+        the timed graph runs without them."""
+        ft.plan.set_profile(None, n_eval, None if own_contrib else n_contrib)
+        ft.plan.forward(ft.params, ft.cams, ft.img, bg=ft.bg)
+        torch.cuda.synchronize()
+        counts = int(n_eval.sum().item()), int(n_contrib.sum().item())
+        ft.plan.set_profile(kev)
+        return counts
+    ft.plan.set_profile(kev)
     n_pairs_dev = vbm.device_tensor(bufs.n_pairs, (1,), np.int64)
     ft.capture()
     for _ in range(args.warmup):
@@ -628,6 +637,7 @@ def main():
     ft.step_batched()
     torch.cuda.synchronize()
     launches_per_step = vbm.kernel_launches() - launches0
+    counts0 = count_pairs()
     extra_steps = 1        # the launch-count step above
 
     clocks = ClockSampler(_gpu_id(torch, device, local))
@@ -637,7 +647,7 @@ def main():
     clocks.start()
     t_wall0 = time.perf_counter()
     groups = ("head", "projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam")
-    step_ms, grp_ms, p_fwd, p_bwd, pairs = [], {g: [] for g in groups}, 0, 0, []
+    step_ms, grp_ms, pairs = [], {g: [] for g in groups}, []
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush()
@@ -649,8 +659,6 @@ def main():
         marks = [s_ev, kev[4], kev[5], kev[0], kev[1], kev[2], kev[3], kev[6], e_ev]
         for g, a, b in zip(groups, marks[:-1], marks[1:]):
             grp_ms[g].append(a.elapsed_time(b))
-        p_fwd += int(n_eval.sum().item())
-        p_bwd += int(n_contrib.sum().item())
         pairs.append(int(n_pairs_dev.item()))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
@@ -661,6 +669,11 @@ def main():
     total_ms, value = job_rate(sum(step_ms), args.steps, device)
     ms_per_step = total_ms / args.steps
     ok, need, bad = ft.check()
+    counts1 = count_pairs()
+    # evaluated and contributing pairs per step: the mean of the counts before and
+    # after the timed window
+    p_fwd_step = 0.5 * (counts0[0] + counts1[0])
+    p_bwd_step = 0.5 * (counts0[1] + counts1[1])
     state_ms = {g: float(np.median(grp_ms[g])) for g in groups}
 
     # forward alone (projection, binning, sort, compositing) and forward + loss +
@@ -747,7 +760,7 @@ def main():
     # ------------------------------------------------------------- roofline
     n_pairs = float(np.mean(pairs))
     n_items = vbm.batch_items([0, n] if w.scene_offset is None else w.scene_offset, V, w.view_scene)
-    work = step_work(n, n_items, V, H * W, n_pairs, p_fwd / args.steps, p_bwd / args.steps, batch["recompute"])
+    work = step_work(n, n_items, V, H * W, n_pairs, p_fwd_step, p_bwd_step, batch["recompute"])
     kernels, lb_sum = {}, 0.0
     for g in ("projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam"):
         lb, bound = lower_bound_ms(work[g], peaks)
@@ -772,7 +785,8 @@ def main():
                                "%.1f TFLOP/s); derived 152 SMs x 128 lanes x 2 x 2070 MHz = %.1f"
                                % (peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"], peaks["derived_fp32_tflops"]),
                 "sfu_frac": work[kname]["sfu"] / (state_ms[kname] * 1e-3) / 1e12 / peaks["ex2_tera_per_s"],
-                "pairs_fwd_per_step": p_fwd / args.steps, "pairs_bwd_per_step": p_bwd / args.steps,
+                "pairs_fwd_per_step": p_fwd_step, "pairs_bwd_per_step": p_bwd_step,
+                "pairs_counted": "per-pixel counts of two untimed forwards, before and after the timed steps",
                 "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR},
                 "step_frac": lb_sum / ms_per_step, "step_lower_bound_ms": lb_sum,
                 "kernels": kernels, "peaks": peaks}

@@ -315,7 +315,7 @@ struct PixState {
 // stored.
 // The entries are prefetched in registers, or, with rs (the backward's replay),
 // through its asynchronous shared-memory stages.
-template <int PPT, int GL, bool COLOR = true>
+template <int PPT, int GL, bool COLOR = true, bool EVAL = false>
 __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__restrict__ ranges,
                                            const uint32_t *__restrict__ pair_item, const SplatRec *__restrict__ rec, int W, int H, int vb, float bg0,
                                            float bg1, float bg2, float *__restrict__ img,
@@ -424,10 +424,8 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
                     const float testT = T[kk] * (1.f - alpha);
                     const bool term = cand && testT < kTMin;
                     const bool blend = cand && !term;
-                    if (term) {
-                        done[kk] = true;
-                        evaluated[kk] = pos1;
-                    }
+                    done[kk] = done[kk] || term;
+                    if (EVAL && term) evaluated[kk] = pos1;
                     if (COLOR) {
                         const float wgt = blend ? alpha * T[kk] : 0.f;
                         C0[kk] = __fmaf_rn(c.x, wgt, C0[kk]);
@@ -476,7 +474,7 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
         if (alpha_out) alpha_out[v * HW + pix] = 1.f - T[k];
         if (T_final) T_final[v * HW + pix] = T[k];
         if (n_contrib) n_contrib[v * HW + pix] = last[k];
-        if (n_eval) n_eval[v * HW + pix] = evaluated[k];
+        if (EVAL) n_eval[v * HW + pix] = evaluated[k];
     }
 }
 
@@ -841,7 +839,7 @@ __device__ __forceinline__ bool next_item(int &q, int w_global, int n_items_w, i
     return q < n_items_w;
 }
 
-template <int PPT, int GL, bool PERSIST>
+template <int PPT, int GL, bool PERSIST, bool EVAL>
 __global__ void __launch_bounds__(kWarps * 32)
     k_raster_fwd(const int *__restrict__ order, int *__restrict__ queue, int n_items_w, int n_regions,
                  const int2 *__restrict__ ranges, const uint32_t *__restrict__ pair_item,
@@ -860,7 +858,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         const WarpGeom wg = warp_geom<PPT, GL>(tile, q % n_regions, tw, th, TX, TY, W, H);
         if (wg.x0 > wg.x1 || wg.y0 > wg.y1) continue;            // region outside the image
         const int cb = ckpt_base ? ckpt_base[tile] : -1;
-        fwd_region<PPT, GL>(wg, ranges, pair_item, rec, W, H, vb, bg0, bg1, bg2, img, alpha_out,
+        fwd_region<PPT, GL, true, EVAL>(wg, ranges, pair_item, rec, W, H, vb, bg0, bg1, bg2, img, alpha_out,
                             T_final, n_contrib, n_eval, s, nullptr, nullptr,
                             cb >= 0 ? ckpt + (int64_t)cb * tile_px : nullptr, seg_len, tw, tile_px);
     }
@@ -954,17 +952,24 @@ vbm_status launch_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
     const int nr = regions_per_tile(p, PPT);
     const int n_items_w = n_tiles * nr;
     record_event(p->prof_ev[0], st);
+    // the evaluated-entry count (a profiling output) is compiled only into the
+    // variants launched while that hook is set
+    const bool eval = p->prof_n_eval != nullptr;
+    int32_t *nc_out = p->n_contrib ? p->n_contrib : p->prof_n_contrib;
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
-        const int grid = persistent_grid(k_raster_fwd<PPT, GL, true>, n_items_w);
-        k_raster_fwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
-            p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,
-            bg[0], bg[1], bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib,
-            p->prof_n_eval, p->ckpt, p->seg_len ? p->ckpt_base : nullptr, p->seg_len);
+        auto kernel = eval ? k_raster_fwd<PPT, GL, true, true> : k_raster_fwd<PPT, GL, true, false>;
+        const int grid = persistent_grid(kernel, n_items_w);
+        kernel<<<grid, kWarps * 32, 0, st>>>(p->tile_order, p->tile_queue, n_items_w, nr, p->ranges, p->pair_item,
+                                             p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h,
+                                             p->TX, p->TY, vb, bg[0], bg[1], bg[2], img, alpha, p->T_final, nc_out,
+                                             p->prof_n_eval, p->ckpt, p->seg_len ? p->ckpt_base : nullptr,
+                                             p->seg_len);
     } else {
-        k_raster_fwd<PPT, GL, false><<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
-            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1],
-            bg[2], img, alpha, p->T_final, p->n_contrib ? p->n_contrib : p->prof_n_contrib, p->prof_n_eval, nullptr,
-            nullptr, 0);
+        auto kernel = eval ? k_raster_fwd<PPT, GL, false, true> : k_raster_fwd<PPT, GL, false, false>;
+        kernel<<<(n_items_w + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(
+            nullptr, nullptr, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height,
+            p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb, bg[0], bg[1], bg[2], img, alpha, p->T_final, nc_out,
+            p->prof_n_eval, nullptr, nullptr, 0);
     }
     VBM_LAUNCH("raster_fwd");
     record_event(p->prof_ev[1], st);

@@ -162,6 +162,43 @@ def test_composite_matches_oracle_on_gpu_splats(cuda_lib, tile, ppt, persistent,
     assert img.max() > 0.05      # the scene is not empty
 
 
+@pytest.mark.parametrize("ppt,persistent,recompute", [(1, False, False), (2, True, False), (2, True, True),
+                                                     (1, True, True)])
+def test_profiling_counts_match_oracle(cuda_lib, ppt, persistent, recompute):
+    """The plan's profiling hooks: per pixel the number of list entries evaluated (up to and
+    including the one that ended compositing) and, for recompute plans, the contributor
+    count equal the oracle's on the GPU's own splats and lists; the image of a forward with
+    the hooks set (a separately compiled kernel variant) is bit-identical to one without."""
+    vbm = cuda_lib
+    W, H, V = 100, 76, 2
+    P, cams, cams32 = scene(seed=8, n=2500, V=V, W=W, H=H)
+    params, cams_dev = to_device(P, cams)
+    flags = (vbm.PLAN_PERSISTENT if persistent else 0) | (vbm.PLAN_RECOMPUTE if recompute else 0)
+    plan = vbm.Plan([0, P.shape[1]], V, W, H, pair_capacity=1 << 22, pixels_per_thread=ppt, flags=flags,
+                    group_lanes=8)
+    img0 = torch.zeros((V, 3, H, W), device="cuda")
+    plan.forward(params, cams_dev, img0)
+    n_eval = torch.full((V, H, W), -1, dtype=torch.int32, device="cuda")
+    n_contrib = torch.full((V, H, W), -1, dtype=torch.int32, device="cuda") if recompute else None
+    plan.set_profile(None, n_eval, n_contrib)
+    img1 = torch.zeros_like(img0)
+    plan.forward(params, cams_dev, img1)
+    plan.set_profile()
+    torch.cuda.synchronize()
+    assert torch.equal(img0, img1)
+    st = plan_state(plan, V)
+    splat, color = gpu_splats_as_oracle(st)
+    ref = oraster.render(V, W, H, 16, 16, st["ranges"], st["pair_item"].astype(np.int32), splat, color,
+                         np.zeros(3))
+    good = ref["margin"] > 1e-5
+    assert good.mean() > 0.99
+    assert np.array_equal(n_eval.cpu().numpy()[good], ref["n_eval"][good])
+    nc = n_contrib.cpu().numpy() if recompute else st["n_contrib"]
+    assert np.array_equal(nc[good], ref["n_contrib"][good])
+    assert (ref["n_eval"] > 1).any()
+    plan.close()
+
+
 def _flag_pixels_of_unsafe_items(ref_fwd, gpu_rect, n_views, W, H, tile, n):
     """Pixels of tiles whose lists differ between the FP32 and FP64 projections: the tiles in
     the symmetric difference of an item's two rectangles (a radius, rectangle or culling
