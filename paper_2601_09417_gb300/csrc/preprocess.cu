@@ -137,9 +137,17 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     const int64_t g = g0 + gl;
     ProjState st;
     float4 cg = make_float4(0.f, 0.f, 0.f, 0.f);
+    // opacity-only quantities, the same for every view: the radius scale
+    // k = min(3, sqrt(2 ln(255 o))) and tau = 2 (ln(255 o) + margin)
+    float k_sig = 0.f, tau = -1.f;
     if (valid) {
         project_base(P, stride, g, st);
         cg = make_float4(P[11 * stride + g], P[12 * stride + g], P[13 * stride + g], st.opac);
+        if (st.opac >= kAlphaMin) {
+            const float ln255o = logf(255.f * st.opac);
+            k_sig = fminf(kRadiusSigmas, sqrtf(2.f * ln255o));
+            tau = 2.f * (ln255o + kCullMargin);
+        }
     }
     for (int v = v_begin; v < v_end; v++) {
         TileTest tt = {};
@@ -163,10 +171,9 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                 float lam1 = mid + sqrtf(fmaxf(disc, kEigFloor));
                 // Extent of the ellipse where o e^power >= 1/255 (capped at 3 sigma):
                 // pixels beyond it skip this splat anyway, so fewer tiles list it.
-                const float k = fminf(kRadiusSigmas, sqrtf(2.f * logf(255.f * st.opac)));
                 // Bounded so the integer rectangle arithmetic cannot overflow; any
                 // radius above 2^24 already spans every image narrower than 6.7M px.
-                float r = fminf(ceilf(k * sqrtf(lam1)), 16777216.0f);
+                float r = fminf(ceilf(k_sig * sqrtf(lam1)), 16777216.0f);
                 float u = cam.fx * st.xz + cam.cx;
                 float vv = cam.fy * st.yz + cam.cy;
                 sr.g = make_float4(u, vv, A, B);
@@ -175,7 +182,6 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                 // half-widths sqrt(tau a) and sqrt(tau c) (the conic's determinant is
                 // 1 / det), slightly widened; the edge minimisers' ratios B / C and
                 // B / A are rounded divisions of the stored conic.
-                const float tau = 2.f * (logf(255.f * st.opac) + kCullMargin);
                 const float bc = __fdiv_rn(B, C), ba = __fdiv_rn(B, A);
                 sr.cu = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc,
                                     ba);

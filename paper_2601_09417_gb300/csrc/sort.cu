@@ -392,6 +392,113 @@ __device__ __forceinline__ uint64_t *group_merge_sort(const uint64_t *__restrict
     return src;
 }
 
+// Bucket-rank sort of a tile's keys g[0, n) (n <= G * kMergeE) by a block of
+// G threads.  The keys' high words are the items' depth bits, which order like
+// the depths (all positive), so n / 2 buckets spread linearly over the list's
+// range of depth bits give keys of nearby depths; every key is placed into its
+// bucket (shared-memory counts, an exclusive scan, a claimed slot) and then
+// written at its bucket's start plus the number of smaller keys in its bucket
+// (the keys are unique, so the ranks are a permutation).  Returns the buffer
+// holding the sorted keys, or nullptr when some bucket holds more than
+// kBucketMax keys (depths too clustered for this to pay): the caller then
+// merge-sorts.  Buffers: a, b of at least n words, cnt and cur of at least
+// max(1, n / 2) words.  Ends with a block barrier.
+constexpr int kBucketMax = 64;
+
+template <int G>
+__device__ uint64_t *bucket_rank_sort(const uint64_t *__restrict__ g, int n, uint64_t *a, uint64_t *b,
+                                      uint32_t *cnt, uint32_t *cur, uint32_t *scratch, int t)
+{
+    constexpr int E = kMergeE;
+    const int nb = max(1, n / 2);
+    uint64_t key[E];
+    uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const int i = t + e * G;
+        key[e] = i < n ? g[i] : kPadKey;
+        if (i < n) {
+            const uint32_t d = (uint32_t)(key[e] >> 32);
+            lo = min(lo, d);
+            hi = max(hi, d);
+        }
+    }
+    for (int i = t; i < nb; i += G) cnt[i] = 0u;
+    if (t == 0) {
+        scratch[0] = 0xffffffffu;   // depth-bit minimum
+        scratch[1] = 0u;            // maximum
+        scratch[2] = 0u;            // largest bucket
+    }
+    __syncthreads();
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((t & 31) == 0) {
+        atomicMin(&scratch[0], lo);
+        atomicMax(&scratch[1], hi);
+    }
+    __syncthreads();
+    const uint32_t dmin = scratch[0];
+    // monotone in the depth bits: float conversion, a positive scale, truncation
+    const float scale = (float)nb / ((float)(scratch[1] - dmin) + 1.0f);
+    int bk[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        bk[e] = -1;
+        if (t + e * G < n) {
+            bk[e] = min(nb - 1, (int)((float)((uint32_t)(key[e] >> 32) - dmin) * scale));
+            atomicAdd(&cnt[bk[e]], 1u);
+        }
+    }
+    __syncthreads();
+    // exclusive scan of the bucket counts: each thread a contiguous chunk,
+    // then the chunk totals across the block; the largest bucket on the way
+    const int per = (nb + G - 1) / G;
+    const int c0 = min(nb, t * per), c1 = min(nb, c0 + per);
+    uint32_t run = 0u, big = 0u;
+    for (int i = c0; i < c1; i++) {
+        run += cnt[i];
+        big = max(big, cnt[i]);
+    }
+    big = __reduce_max_sync(0xffffffffu, big);
+    if ((t & 31) == 0) atomicMax(&scratch[2], big);
+    // block-wide exclusive scan of the per-thread totals (warp scans, then the warp totals)
+    const int lane = t & 31, w = t >> 5;
+    uint32_t incl = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    uint32_t *wsum = scratch + 4;   // [G / 32]
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (scratch[2] > (uint32_t)kBucketMax) return nullptr;   // block-uniform: merge sort instead
+    uint32_t base = 0u;
+    for (int i = 0; i < w; i++) base += wsum[i];
+    uint32_t pos = base + incl - run;
+    for (int i = c0; i < c1; i++) {
+        const uint32_t c = cnt[i];
+        cur[i] = pos;
+        cnt[i] = pos;          // bucket start (the count is cur - start after the claims)
+        pos += c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; e++)
+        if (bk[e] >= 0) a[atomicAdd(&cur[bk[e]], 1u)] = key[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        if (bk[e] < 0) continue;
+        const uint32_t s0 = cnt[bk[e]], s1 = cur[bk[e]];
+        uint32_t r = s0;
+        for (uint32_t j = s0; j < s1; j++) r += a[j] < key[e];
+        b[r] = key[e];
+    }
+    __syncthreads();
+    return b;
+}
+
 constexpr int kSortWarps = 8;                                    // warps per block of k_tile_sort_warp
 constexpr int kWarpSortMax = 32 * kMergeE;                       // longest list one warp sorts
 constexpr int kWarpBufWords = padded(kWarpSortMax);
@@ -401,7 +508,8 @@ constexpr int kMidBufWords = padded(kMidSortMax);
 constexpr int kBlockSortThreads = 512;
 constexpr int kBlockSortKeys = kBlockSortThreads * kMergeE;      // longest list sorted in shared memory
 constexpr int kBlockBufWords = padded(kBlockSortKeys);
-constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t);
+constexpr size_t kBlockSortSmem = 2 * kBlockBufWords * sizeof(uint64_t) +
+                                  (kBlockSortKeys + 4 + kBlockSortThreads / 32) * sizeof(uint32_t);
 
 // One warp per tile (grid-stride over the tiles): lists of up to 32 keys are
 // sorted in registers; longer ones are queued for k_tile_sort_medium (up to
@@ -512,13 +620,21 @@ __global__ void __launch_bounds__(kMidSortThreads) k_tile_sort_mid(const int2 *_
                                                                    const uint32_t *__restrict__ long_count)
 {
     __shared__ uint64_t buf[2][kMidBufWords];
+    __shared__ uint32_t cnt[kMidSortMax / 2], cur[kMidSortMax / 2], scratch[4 + kMidSortThreads / 32];
     const uint32_t n_mid = long_count[0];
     const int t = threadIdx.x;
     for (uint32_t q = blockIdx.x; q < n_mid; q += gridDim.x) {
         const uint32_t tile = long_tiles[q];
         const int2 r = ranges[tile];
         const int n = r.y - r.x;
-        const uint64_t *src = group_merge_sort<kMidSortThreads, true>(pair_key + r.x, n, buf[0], buf[1], t);
+        const uint64_t *src;
+        uint64_t *bs = bucket_rank_sort<kMidSortThreads>(pair_key + r.x, n, buf[0], buf[1], cnt, cur, scratch, t);
+        if (bs) {
+            for (int i = t; i < n; i += kMidSortThreads) write_sorted(bs[i], r.x + i, tile, pair_tile, pair_item);
+            __syncthreads();
+            continue;
+        }
+        src = group_merge_sort<kMidSortThreads, true>(pair_key + r.x, n, buf[0], buf[1], t);
         for (int i = t; i < n; i += kMidSortThreads) write_sorted(src[padded(i)], r.x + i, tile, pair_tile, pair_item);
         __syncthreads();
     }
@@ -578,6 +694,8 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
 {
     extern __shared__ uint64_t smem_keys[];
     uint64_t *s0 = smem_keys, *s1 = smem_keys + kBlockBufWords;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(s1 + kBlockBufWords), *cur = cnt + kBlockSortKeys / 2;
+    uint32_t *scratch = cur + kBlockSortKeys / 2;
     const uint32_t n_long = long_count[1];
     const int t = threadIdx.x;
     for (uint32_t q = blockIdx.x; q < n_long; q += gridDim.x) {
@@ -586,6 +704,12 @@ __global__ void __launch_bounds__(kBlockSortThreads) k_tile_sort_block(const int
         const int64_t n = r.y - r.x;
         uint64_t *g = pair_key + r.x;
         if (n <= kBlockSortKeys) {
+            uint64_t *bs = bucket_rank_sort<kBlockSortThreads>(g, (int)n, s0, s1, cnt, cur, scratch, t);
+            if (bs) {
+                for (int i = t; i < n; i += kBlockSortThreads) write_sorted(bs[i], r.x + i, tile, pair_tile, pair_item);
+                __syncthreads();
+                continue;
+            }
             const uint64_t *src = group_merge_sort<kBlockSortThreads, true>(g, (int)n, s0, s1, t);
             for (int i = t; i < n; i += kBlockSortThreads) write_sorted(src[padded(i)], r.x + i, tile, pair_tile, pair_item);
             __syncthreads();
@@ -1156,7 +1280,7 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
         k_tile_sort_mid<<<num_sms() * 8, kMidSortThreads, 0, st>>>(p->ranges, p->pair_key, p->pair_tile,
                                                                     p->pair_item, b.long_tiles, b.long_count);
         VBM_LAUNCH("tile_sort_mid");
-        k_tile_sort_block<<<num_sms() * 3, kBlockSortThreads, kBlockSortSmem, st>>>(
+        k_tile_sort_block<<<num_sms() * 2, kBlockSortThreads, kBlockSortSmem, st>>>(
             p->ranges, p->pair_key, p->pair_tile, p->pair_item, b.long_tiles, b.long_count, n_tiles);
         VBM_LAUNCH("tile_sort_block");
         note_launches(2);
