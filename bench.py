@@ -789,6 +789,7 @@ def main():
                 "pairs_counted": "per-pixel counts of two untimed forwards, before and after the timed steps",
                 "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR},
                 "step_frac": lb_sum / ms_per_step, "step_lower_bound_ms": lb_sum,
+                "graph_head_ms": state_ms["head"],
                 "kernels": kernels, "peaks": peaks}
 
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,

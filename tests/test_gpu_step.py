@@ -335,3 +335,30 @@ def test_graph_and_host_steps_match_batched_steps(cuda_lib):
         for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
             nrm, elt = rel_group_error(g[lo:hi], g0[lo:hi])
             assert nrm < 1e-5, (mode, lo, nrm)
+
+
+def test_peak_probe(cuda_lib):
+    """vbm_peak_probe reports its work exactly, and the rates it measures on one wave are
+    positive and below the unit-count limits (FP32: 2 FLOP per lane per clock; ex2 a
+    fraction of that)."""
+    vbm = cuda_lib
+    props = torch.cuda.get_device_properties(0)
+    blocks = props.multi_processor_count * 8
+    out = torch.zeros(blocks * 256, device="cuda")
+    for kind, per_link in ((0, 2.0), (1, 4.0), (2, 1.0)):
+        iters = 4096
+        vbm.peak_probe(kind, blocks, iters, out)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        ops = vbm.peak_probe(kind, blocks, iters, out)
+        e.record()
+        e.synchronize()
+        assert ops == blocks * 256 * iters * 8 * per_link
+        rate = ops / (s.elapsed_time(e) * 1e-3)
+        assert 0 < rate < props.multi_processor_count * 128 * 2 * 2.2e9 * 1.05
+    assert torch.count_nonzero(out) == 0     # the chains never hit the guarded store
+    with pytest.raises(vbm.VbmError) as err:
+        vbm.peak_probe(3, blocks, 16, out)
+    assert err.value.status == vbm.VBM_ERR_ARG
+    with pytest.raises(vbm.VbmError):
+        vbm.peak_probe(0, blocks, 10, out)         # not a multiple of 16
