@@ -617,7 +617,8 @@ def main():
     def count_pairs():
         """(P_fwd, P_bwd) of the current Gaussians: one untimed forward with the per-pixel
         count hooks set (recompute plans keep no contributor counts: the hook writes them);
-        the timed graph runs without them."""
+        the timed graph runs without them, and the timed steps are synchronised one by one,
+        so a count between two of them is outside the timed intervals."""
         ft.plan.set_profile(None, n_eval, None if own_contrib else n_contrib)
         ft.plan.forward(ft.params, ft.cams, ft.img, bg=ft.bg)
         torch.cuda.synchronize()
@@ -637,7 +638,6 @@ def main():
     ft.step_batched()
     torch.cuda.synchronize()
     launches_per_step = vbm.kernel_launches() - launches0
-    counts0 = count_pairs()
     extra_steps = 1        # the launch-count step above
 
     clocks = ClockSampler(_gpu_id(torch, device, local))
@@ -647,9 +647,12 @@ def main():
     clocks.start()
     t_wall0 = time.perf_counter()
     groups = ("head", "projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam")
-    step_ms, grp_ms, pairs = [], {g: [] for g in groups}, []
+    step_ms, grp_ms, pairs, counts = [], {g: [] for g in groups}, [], []
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
+    count_every = max(1, args.steps // 8)
+    for i in range(args.steps):
+        if i % count_every == 0:    # untimed: the pair counts of the state the next step sees
+            counts.append(count_pairs())
         flush()
         s_ev.record()
         ft.step_graph()
@@ -669,11 +672,11 @@ def main():
     total_ms, value = job_rate(sum(step_ms), args.steps, device)
     ms_per_step = total_ms / args.steps
     ok, need, bad = ft.check()
-    counts1 = count_pairs()
-    # evaluated and contributing pairs per step: the mean of the counts before and
-    # after the timed window
-    p_fwd_step = 0.5 * (counts0[0] + counts1[0])
-    p_bwd_step = 0.5 * (counts0[1] + counts1[1])
+    counts.append(count_pairs())
+    # evaluated and contributing pairs per step: the mean of the counts sampled
+    # through the timed window
+    p_fwd_step = float(np.mean([c[0] for c in counts]))
+    p_bwd_step = float(np.mean([c[1] for c in counts]))
     state_ms = {g: float(np.median(grp_ms[g])) for g in groups}
 
     # forward alone (projection, binning, sort, compositing) and forward + loss +
@@ -786,7 +789,8 @@ def main():
                                % (peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"], peaks["derived_fp32_tflops"]),
                 "sfu_frac": work[kname]["sfu"] / (state_ms[kname] * 1e-3) / 1e12 / peaks["ex2_tera_per_s"],
                 "pairs_fwd_per_step": p_fwd_step, "pairs_bwd_per_step": p_bwd_step,
-                "pairs_counted": "per-pixel counts of two untimed forwards, before and after the timed steps",
+                "pairs_counted": "per-pixel counts of %d untimed forwards spread through the timed steps"
+                                 % len(counts),
                 "flop_per_pair": {"fwd": FWD_FLOP_PER_PAIR, "bwd": BWD_FLOP_PER_PAIR},
                 "step_frac": lb_sum / ms_per_step, "step_lower_bound_ms": lb_sum,
                 "graph_head_ms": state_ms["head"],
