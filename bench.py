@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--tile", default=None, help="WxH, skips the autotuner (with --ppt)")
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread with --tile")
     ap.add_argument("--persistent", action="store_true", help="persistent compositing kernels with --tile")
-    ap.add_argument("--gl", type=int, default=32, help="lanes per compositing group with --tile (8, 16, 32)")
+    ap.add_argument("--gl", type=int, default=32, help="lanes per compositing group with --tile (4, 8, 16, 32)")
     ap.add_argument("--bwd-ppt", type=int, default=0, help="backward pixels per thread (0 = the forward's)")
     ap.add_argument("--bwd-gl", type=int, default=0, help="backward lanes per group (0 = the forward's)")
     ap.add_argument("--radix", action="store_true",

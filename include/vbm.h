@@ -235,7 +235,7 @@ typedef struct {
     int64_t pair_capacity;
     int32_t flags;
     int32_t pixels_per_thread;     /* 0 = default (2); 1, 2 or 4 */
-    int32_t group_lanes;           /* 0 = default (32); 8, 16 or 32 lanes per compositing group */
+    int32_t group_lanes;           /* 0 = default (32); 4, 8, 16 or 32 lanes per compositing group */
     int32_t segment_len;           /* persistent plans: the backward walks a tile list longer than
                                       this many entries as segments that different warps take at
                                       once (the forward stores each pixel's transmittance and

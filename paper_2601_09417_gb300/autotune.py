@@ -34,7 +34,7 @@ from . import vbm
 CANDIDATES = [(tile, ppt, gl, pers)
               for tile in ((16, 16), (16, 8), (8, 16), (8, 8), (16, 4), (8, 4))
               for ppt in (1, 2, 4)
-              for gl in (8, 16, 32)
+              for gl in (4, 8, 16, 32)
               for pers in (False, True)
               if tile[1] % (4 * ppt) == 0]   # a warp region is 4 thread rows of ppt pixels
 SEGMENT_LENGTHS = (64, 128, 256, 512, -1)

@@ -106,15 +106,16 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     VBM_ARG((d->tile_w == 8 || d->tile_w == 16) && d->tile_h > 0 && d->tile_h % 4 == 0 &&
                 (tp == 32 || tp == 64 || tp == 128 || tp == 256),
             "tile_w must be 8 or 16, tile_h a multiple of 4 and tile_w * tile_h 32, 64, 128 or 256");
-    VBM_ARG(d->group_lanes == 0 || d->group_lanes == 8 || d->group_lanes == 16 || d->group_lanes == 32,
-            "group_lanes must be 0, 8, 16 or 32");
+    VBM_ARG(d->group_lanes == 0 || d->group_lanes == 4 || d->group_lanes == 8 || d->group_lanes == 16 ||
+                d->group_lanes == 32,
+            "group_lanes must be 0, 4, 8, 16 or 32");
     VBM_ARG(d->pair_capacity > 0 && d->pair_capacity < ((int64_t)1 << 31), "pair_capacity out of range");
     VBM_ARG(d->pixels_per_thread == 0 || d->pixels_per_thread == 1 || d->pixels_per_thread == 2 ||
                 d->pixels_per_thread == 4,
             "pixels_per_thread must be 0, 1, 2 or 4");
-    VBM_ARG(d->bwd_group_lanes == 0 || d->bwd_group_lanes == 8 || d->bwd_group_lanes == 16 ||
-                d->bwd_group_lanes == 32,
-            "bwd_group_lanes must be 0, 8, 16 or 32");
+    VBM_ARG(d->bwd_group_lanes == 0 || d->bwd_group_lanes == 4 || d->bwd_group_lanes == 8 ||
+                d->bwd_group_lanes == 16 || d->bwd_group_lanes == 32,
+            "bwd_group_lanes must be 0, 4, 8, 16 or 32");
     VBM_ARG(d->bwd_pixels_per_thread == 0 || d->bwd_pixels_per_thread == 1 || d->bwd_pixels_per_thread == 2 ||
                 d->bwd_pixels_per_thread == 4,
             "bwd_pixels_per_thread must be 0, 1, 2 or 4");

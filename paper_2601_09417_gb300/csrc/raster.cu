@@ -99,8 +99,8 @@ __device__ __forceinline__ float rect_min_quadratic(float u, float v, float A, f
 // Lane groups inside a warp region: GL lanes cover GW columns x GR thread rows.
 template <int GL>
 struct Groups {
-    static_assert(GL == 8 || GL == 16 || GL == 32, "lane groups of 8, 16 or 32");
-    static constexpr int GR = GL == 8 ? 2 : 4;     // thread rows
+    static_assert(GL == 4 || GL == 8 || GL == 16 || GL == 32, "lane groups of 4, 8, 16 or 32");
+    static constexpr int GR = GL <= 8 ? 2 : 4;     // thread rows
     static constexpr int GW = GL / GR;              // columns: 4, 4, 8
     static constexpr int PER_ROW = kRegionCols / GW;
     static constexpr int NG = 32 / GL;              // groups per warp
@@ -112,7 +112,7 @@ struct WarpGeom {
     int pit0;                   // index of the lane's first pixel inside the tile (row-major, tile_w wide)
     float pxc;
     float x0, x1, y0, y1;       // pixel-centre rectangle of the region (clipped to the image)
-    float gx0[4], gy0[4];       // first pixel centre of each group's block
+    float gx0[8], gy0[8];       // first pixel centre of each group's block
     int g;                      // this lane's group
 };
 
@@ -134,7 +134,7 @@ __device__ __forceinline__ WarpGeom warp_geom(int tile, int region, int tw, int 
     t.g = lane / GL;
     const int k = lane % GL;
 #pragma unroll
-    for (int g = 0; g < 4; g++) {
+    for (int g = 0; g < Gp::NG; g++) {
         t.gx0[g] = ox + (g % Gp::PER_ROW) * Gp::GW + 0.5f;
         t.gy0[g] = oy + (g / Gp::PER_ROW) * Gp::GR * PPT + 0.5f;
     }
@@ -497,13 +497,14 @@ __device__ __forceinline__ void rs_half(const float (&in)[N], float (&out)[(N + 
 
 // Sum of nine values over a lane group, scattered over its lanes with
 // halving steps (GL = 32: 12 shuffles, the last step a pair sum; GL = 16:
-// 11 shuffles; GL = 8: 10 shuffles).  On return out[o] holds the group sum of
-// value base + o for o < cnt, where (base, cnt) come from group_sum_layout.
+// 11 shuffles; GL = 8: 10 shuffles; GL = 4: 8 shuffles).  On return out[o]
+// holds the group sum of value base + o for o < cnt, where (base, cnt) come
+// from group_sum_layout.
 template <int GL>
 struct GroupSum {
-    static constexpr int NOUT = GL == 8 ? 2 : 1;
-    static constexpr int TOP = GL == 32 ? 4 : (GL == 16 ? 3 : 2);    // first lane bit halved
-    static constexpr int STEPS = GL == 8 ? 3 : 4;
+    static constexpr int NOUT = GL == 4 ? 3 : (GL == 8 ? 2 : 1);
+    static constexpr int TOP = GL == 32 ? 4 : (GL == 16 ? 3 : (GL == 8 ? 2 : 1));   // first lane bit halved
+    static constexpr int STEPS = GL == 4 ? 2 : (GL == 8 ? 3 : 4);
 };
 
 // Which values a lane holds after group_sum9: a lane whose bit is set keeps
@@ -534,6 +535,12 @@ __device__ __forceinline__ void group_sum9(const float (&v)[kNV], float (&out)[G
     float a5[5], a3[3], a2[2];
     rs_half<9>(v, a5, T);
     rs_half<5>(a5, a3, T - 1);
+    if constexpr (GL == 4) {
+        out[0] = a3[0];
+        out[1] = a3[1];
+        out[2] = a3[2];
+        return;
+    }
     rs_half<3>(a3, a2, T - 2);
     if constexpr (GL == 8) {
         out[0] = a2[0];
@@ -1005,12 +1012,15 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
 // Dispatch on (pixels per thread, lanes per group).
 #define VBM_RASTER_DISPATCH(FN, BWD, ...)                                                             \
     switch (pixels_per_thread(p, BWD) * 64 + group_lanes(p, BWD)) {                                   \
+        case 1 * 64 + 4: return FN<1, 4>(__VA_ARGS__);                                                \
         case 1 * 64 + 8: return FN<1, 8>(__VA_ARGS__);                                                \
         case 1 * 64 + 16: return FN<1, 16>(__VA_ARGS__);                                              \
         case 1 * 64 + 32: return FN<1, 32>(__VA_ARGS__);                                              \
+        case 2 * 64 + 4: return FN<2, 4>(__VA_ARGS__);                                                \
         case 2 * 64 + 8: return FN<2, 8>(__VA_ARGS__);                                                \
         case 2 * 64 + 16: return FN<2, 16>(__VA_ARGS__);                                              \
         case 2 * 64 + 32: return FN<2, 32>(__VA_ARGS__);                                              \
+        case 4 * 64 + 4: return FN<4, 4>(__VA_ARGS__);                                                \
         case 4 * 64 + 8: return FN<4, 8>(__VA_ARGS__);                                                \
         case 4 * 64 + 16: return FN<4, 16>(__VA_ARGS__);                                              \
         case 4 * 64 + 32: return FN<4, 32>(__VA_ARGS__);                                              \

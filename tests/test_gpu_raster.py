@@ -138,6 +138,7 @@ def test_binning_long_lists_bit_exact(cuda_lib, radix):
                                                     ((16, 16), 1, True, 32), ((8, 8), 1, True, 32),
                                                     ((8, 8), 1, True, 8), ((8, 8), 1, False, 16),
                                                     ((16, 16), 1, False, 8), ((16, 16), 2, True, 16),
+                                                    ((8, 8), 2, True, 4), ((16, 16), 1, False, 4), ((16, 8), 4, True, 4),
                                                     ((16, 8), 4, False, 8), ((8, 8), 2, False, 8),
                                                     ((8, 4), 1, True, 16), ((8, 4), 1, False, 32),
                                                     ((16, 4), 1, True, 8), ((8, 8), 1, "radix", 16)])
@@ -236,7 +237,8 @@ def test_end_to_end_image_matches_fp64_oracle(cuda_lib):
 @pytest.mark.parametrize("ppt,persistent,gl,seg", [(1, False, 32, 0), (2, False, 32, 0), (4, False, 32, 0),
                                                    (1, True, 32, 0), (1, False, 8, 0), (1, True, 16, 0),
                                                    (2, False, 8, 0), (4, True, 16, 0), (1, True, 16, 32),
-                                                   (2, True, 8, 64), (4, True, 32, 32), (1, True, 32, -1)])
+                                                   (2, True, 8, 64), (4, True, 32, 32), (1, True, 32, -1),
+                                                   (2, True, 4, 64), (1, False, 4, 0), (4, True, 4, 32)])
 def test_backward_matches_oracle(cuda_lib, ppt, persistent, gl, seg):
     """seg > 0: tile lists longer than seg entries are walked by the backward as
     segments starting from the forward's checkpoints; -1: never split."""

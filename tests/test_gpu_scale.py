@@ -43,7 +43,8 @@ def _sample_tiles(ranges, n, rng, longest=4):
 @pytest.mark.parametrize("key,tile,ppt,gl,recompute,seg", [("c1", (8, 8), 2, 8, False, 128),
                                                             ("c2", (16, 8), 1, 16, False, 0),
                                                             ("c3", (16, 16), 2, 8, False, 0),
-                                                            ("c4", (8, 8), 1, 16, True, 0)])
+                                                            ("c4", (8, 8), 1, 16, True, 0),
+                                                            ("c4", (8, 8), 2, 4, True, 256)])
 def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute, seg):
     """c1 runs in the launch configuration the benchmark's autotuner picks for it (8x8
     tiles, 2 pixels per thread, 8-lane groups, persistent, 128-entry backward segments)."""
