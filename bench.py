@@ -29,6 +29,7 @@ has no cross-GPU exchange in this build); rank 0 prints the line.
 """
 
 import argparse
+import atexit
 import hashlib
 import json
 import math
@@ -105,34 +106,77 @@ REF_WINDOW = {"c2": 100, "c4": 64}
 # --------------------------------------------------------------------- clocks
 
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 50 ms, each stamped with the host
+    clock when it arrives; started ahead of the timed region (nvidia-smi takes a moment to
+    produce its first line), and summarised over the lines that arrived between mark_begin()
+    and mark_end()."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, interval_ms=50):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
+        self.lines = []             # (host time, line)
+        self.reader = None
+        self.t0 = self.t1 = None
 
     def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+
+        def read(stream):
+            for line in stream:
+                self.lines.append((time.perf_counter(), line))
+        self.reader = threading.Thread(target=read, args=(self.proc.stdout,), daemon=True)
+        self.reader.start()
+        atexit.register(self._end_process)
+
+    def _end_process(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.kill()
+
+    def wait_first(self, timeout_s=5.0):
+        """Blocks until the first sample has arrived (or the timeout passes)."""
+        t_end = time.perf_counter() + timeout_s
+        while self.proc is not None and not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.01)
+
+    def mark_begin(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        if self.reader is not None:
+            self.reader.join(timeout=5)
+        return self.summarise(self.lines, self.t0, self.t1)
+
+    @classmethod
+    def summarise(cls, lines, t0=None, t1=None):
+        """Median SM clock, the largest maximum clock and the active throttle reasons of the
+        samples stamped within [t0, t1] (all samples where a bound is None)."""
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
+        for t, line in lines:
+            if (t0 is not None and t < t0) or (t1 is not None and t > t1):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 7:
                 continue
@@ -141,7 +185,7 @@ class ClockSampler:
                 mx.append(float(parts[1]))
             except ValueError:
                 continue
-            for name, val in zip(names, parts[3:7]):
+            for name, val in zip(cls.NAMES, parts[3:7]):
                 if val.lower() == "active":
                     reasons.add(name)
         if not sm:
@@ -628,6 +672,8 @@ def main():
     ft.plan.set_profile(kev)
     n_pairs_dev = vbm.device_tensor(bufs.n_pairs, (1,), np.int64)
     ft.capture()
+    clocks = ClockSampler(_gpu_id(torch, device, local))
+    clocks.start()
     for _ in range(args.warmup):
         ft.step_graph()
     torch.cuda.synchronize()
@@ -640,11 +686,11 @@ def main():
     launches_per_step = vbm.kernel_launches() - launches0
     extra_steps = 1        # the launch-count step above
 
-    clocks = ClockSampler(_gpu_id(torch, device, local))
+    clocks.wait_first()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_begin()
     t_wall0 = time.perf_counter()
     groups = ("head", "projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam")
     step_ms, grp_ms, pairs, counts = [], {g: [] for g in groups}, [], []
@@ -665,6 +711,7 @@ def main():
         pairs.append(int(n_pairs_dev.item()))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
+    clocks.mark_end()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()

@@ -12,7 +12,8 @@ from paper_2601_09417_gb300 import autotune as at
 def test_candidates_respect_region_rows():
     assert len(at.CANDIDATES) == len(set(at.CANDIDATES))
     for tile, ppt, gl, pers in at.CANDIDATES:
-        assert tile[1] % (4 * ppt) == 0 and gl in (8, 16, 32)
+        assert tile[1] % (4 * ppt) == 0 and gl in (4, 8, 16, 32)
+    assert {gl for _, _, gl, _ in at.CANDIDATES} == {4, 8, 16, 32}
     assert -1 in at.SEGMENT_LENGTHS and all(s == -1 or s % 32 == 0 for s in at.SEGMENT_LENGTHS)
 
 

@@ -56,3 +56,19 @@ def test_oracle_window_extrapolation():
     assert c["cx"] == 64.0 and c["width"] == 128
     c, win = bench._window_camera(cam, None)
     assert win == (0, 0, 1024, 1024) and c["cx"] == 512.0
+
+
+def test_clock_summary_keeps_the_timed_window():
+    # nvidia-smi lines (sm, max, power, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap)
+    # stamped 0.0 .. 0.9 s; the window [0.25, 0.65] holds the samples at 0.3 .. 0.6
+    lines = []
+    for i in range(10):
+        sm = 1200.0 if i < 3 else 2070.0
+        thermal = "Active" if i == 9 else "Not Active"
+        lines.append((0.1 * i, "%.0f, 2070, 900.0, Not Active, %s, Not Active, Not Active\n" % (sm, thermal)))
+    lines.append((0.45, "[N/A], [N/A]\n"))
+    c = bench.ClockSampler.summarise(lines, 0.25, 0.65)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 4}
+    everything = bench.ClockSampler.summarise(lines)
+    assert everything["samples"] == 10 and everything["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.ClockSampler.summarise(lines, 5.0, 6.0) is None
