@@ -224,7 +224,8 @@ typedef struct vbm_plan vbm_plan;
  * thread handles pixels_per_thread pixels of one tile column (at least 32
  * threads per tile), and the threads of a warp form groups of group_lanes
  * lanes that each walk the list entries reaching their own pixel block.
- * pair_capacity bounds the number of (tile, Gaussian) pairs of one call. */
+ * pair_capacity bounds the number of (tile, Gaussian) pairs of one call.
+ * At most 65535 tiles along each image axis. */
 typedef struct {
     int32_t n_scenes;
     int32_t n_views;
@@ -298,9 +299,13 @@ typedef struct {
     const float *rec;         /* [n_items][16], one 64-byte record per item: u, v, conic A, conic B |
                                  r, g, b, opacity | half-widths (x, y) of the alpha >= 1/255 box,
                                  B / C, B / A | conic C, tau = 2 (ln(255 o) + 1e-3) (the binning
-                                 tile test's bound; -1 for an item without tiles), camera z, unused */
-    const int32_t *rect;      /* [n_items][4]: tile x0, y0, x1, y1 (end exclusive)  */
-    const int32_t *radius;    /* [n_items]                                         */
+                                 tile test's bound; -1 for an item without tiles), camera z, the
+                                 radius in pixels (int32 bits) */
+    const uint32_t *place;    /* [n_items][4] placement record: x0 | x1 << 16, y0 | y1 << 16 (the
+                                 tile rectangle [x0, x1) x [y0, y1)), the listed-tile word (bit k:
+                                 the k-th tile of a rectangle of at most 8 tiles, row-major, passed
+                                 the tile test; bit 31 alone: a larger rectangle; 0: no tiles),
+                                 camera z (float bits) */
     const uint32_t *pair_tile;/* [n_pairs] sorted tile ids (relative to view_begin) */
     const uint32_t *pair_item;/* [n_pairs] item of each pair                       */
     const int32_t *ranges;    /* [tiles][2] start, end                             */

@@ -121,6 +121,9 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
             "bwd_pixels_per_thread must be 0, 1, 2 or 4");
     VBM_ARG(d->segment_len == -1 || (d->segment_len >= 0 && d->segment_len <= 65536 && d->segment_len % 32 == 0),
             "segment_len must be -1, 0 or a positive multiple of 32 up to 65536");
+    VBM_ARG((d->width + d->tile_w - 1) / d->tile_w <= kMaxTilesPerAxis &&
+                (d->height + d->tile_h - 1) / d->tile_h <= kMaxTilesPerAxis,
+            "at most 65535 tiles along each image axis");
     VBM_ARG(d->scene_offset[0] == 0, "scene_offset[0] must be 0");
     for (int s = 0; s < d->n_scenes; s++)
         VBM_ARG(d->scene_offset[s + 1] >= d->scene_offset[s], "scene_offset must be non-decreasing");
@@ -170,9 +173,7 @@ vbm_status vbm_plan_create(const vbm_plan_desc *d, vbm_plan **out)
     ALLOC(p->d_scene_view_ptr, d->n_scenes + 1);
     ALLOC(p->d_scene_views, d->n_views);
     ALLOC(p->rec, items);
-    ALLOC(p->rect, items);
-    ALLOC(p->radius, items);
-    ALLOC(p->listed, items);
+    ALLOC(p->place, items);
     ALLOC(p->g_splat, kGradStride * items);
     ALLOC(p->pair_key, pairs);
     ALLOC(p->pair_tile, pairs);
@@ -324,8 +325,7 @@ vbm_status vbm_plan_get_buffers(vbm_plan *p, vbm_plan_buffers *o)
     std::memset(o, 0, sizeof(*o));
     o->n_items = p->last_items;
     o->rec = (const float *)p->rec;
-    o->rect = (const int32_t *)p->rect;
-    o->radius = p->radius;
+    o->place = (const uint32_t *)p->place;
     o->pair_tile = p->pair_tile;
     o->pair_item = p->pair_item;
     o->ranges = (const int32_t *)p->ranges;

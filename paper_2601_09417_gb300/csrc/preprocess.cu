@@ -4,8 +4,9 @@
 // layout P[14][stride], so the 14 loads of a warp are each one coalesced
 // 128-byte transaction.  The forward writes each item's splat record (one
 // 64-byte line: u, v, conic, colour, opacity, the culling box, the tile test's
-// bound and the depth; SplatRec), the tile rectangle and the listed tiles,
-// and adds the item to the pair count of each listed tile.  The
+// bound, the depth and the radius; SplatRec) and its placement record (the
+// tile rectangle, the listed tiles and the depth in 16 bytes), and adds the
+// item to the pair count of each listed tile.  The
 // backward recomputes the forward state from the parameters (cheaper than
 // storing it) and sums the per-view contributions of a Gaussian in
 // registers, so the parameter gradient is written once, without atomics: the
@@ -107,13 +108,6 @@ __device__ __forceinline__ void project_view(const vbm_camera &cam, ProjState &s
     if (!(st.det > 0.f)) st.culled = true;
 }
 
-__device__ __forceinline__ void project_state(const float *__restrict__ P, int64_t stride, int64_t g,
-                                              const vbm_camera &cam, ProjState &st)
-{
-    project_base(P, stride, g, st);
-    project_view(cam, st);
-}
-
 // Views [vb + blockIdx.y vpt, + vpt) of the call (clipped to vb + vc), one
 // Gaussian per thread: the view-independent state (rotation, 3D covariance,
 // opacity) is built once and projected for each of those views.  With
@@ -123,9 +117,8 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                                  const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
                                  const int64_t *__restrict__ view_item_offset, int vb, int vc, int vpt, int TX,
                                  int TY, int tw, int th, int W, int H, SplatRec *__restrict__ rec,
-                                 float4 *__restrict__ gs, int4 *__restrict__ rect, int32_t *__restrict__ radius,
-                                 uint32_t *__restrict__ listed, uint32_t *__restrict__ tile_count,
-                                 uint32_t *__restrict__ touched)
+                                 float4 *__restrict__ gs, uint4 *__restrict__ place,
+                                 uint32_t *__restrict__ tile_count, uint32_t *__restrict__ touched)
 {
     const int v_begin = vb + blockIdx.y * (MULTI ? vpt : 1);
     const int v_end = MULTI ? min(v_begin + vpt, vb + vc) : v_begin + 1;
@@ -153,14 +146,13 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
         TileTest tt = {};
         bool has_tiles = false;
         int64_t item = 0;
+        int4 rc = make_int4(0, 0, 0, 0);
         if (valid) {
             item = view_item_offset[v] - view_item_offset[vb] + gl;
             const vbm_camera cam = cams[v];
             project_view(cam, st);
             SplatRec sr;
             sr.c = cg;
-            int4 rc = make_int4(0, 0, 0, 0);
-            int r_int = 0;
             // A splat whose opacity is below the 1/255 compositing cut-off can never be
             // blended (alpha = o G <= o), so it gets no tiles.
             if (!st.culled && st.opac >= kAlphaMin) {
@@ -185,8 +177,8 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                 const float bc = __fdiv_rn(B, C), ba = __fdiv_rn(B, A);
                 sr.cu = make_float4(sqrtf(tau * st.a) * 1.0001f + 1e-3f, sqrtf(tau * st.c) * 1.0001f + 1e-3f, bc,
                                     ba);
-                sr.x = make_float4(C, tau, st.t[2], 0.f);
-                r_int = (int)r;
+                const int r_int = (int)r;
+                sr.x = make_float4(C, tau, st.t[2], __int_as_float(r_int));
                 int fu = (int)floorf(clampf(u, -kCoordClamp, kCoordClamp));
                 int fv = (int)floorf(clampf(vv, -kCoordClamp, kCoordClamp));
                 // floor division by the tile size, a power of two: arithmetic shifts
@@ -200,7 +192,7 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
             } else {
                 sr.g = make_float4(0.f, 0.f, 0.f, 0.f);
                 sr.cu = make_float4(0.f, 0.f, 0.f, 0.f);
-                sr.x = make_float4(0.f, -1.f, st.t[2], 0.f);
+                sr.x = make_float4(0.f, -1.f, st.t[2], __int_as_float(0));
             }
             rec[item] = sr;
             if (gs) {   // the item's splat-gradient record, zero for the backward's atomics
@@ -209,8 +201,6 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
                 gs[3 * item + 1] = z;
                 gs[3 * item + 2] = z;
             }
-            rect[item] = rc;
-            radius[item] = r_int;
         }
         // tiles of the rectangle that pass the exact tile test (the image size is
         // the plan's, as in the pair placement, so both take the same decisions),
@@ -219,7 +209,7 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
         const uint32_t word = listed_tiles(has_tiles, tt, tw, th, W, H, tile_count,
                                            (uint32_t)(v - vb) * (uint32_t)(TX * TY), TX, &n_listed);
         if (valid) {
-            listed[item] = word;
+            place[item] = pack_place(rc, word, st.t[2]);
             if (touched) touched[item] = n_listed;   // pairs of the item (radix-sort ordering)
         }
     }
@@ -295,7 +285,7 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
         float dJ02 = dT0[0] * Wm[6] + dT0[1] * Wm[7] + dT0[2] * Wm[8];
         float dJ11 = dT1[0] * Wm[3] + dT1[1] * Wm[4] + dT1[2] * Wm[5];
         float dJ12 = dT1[0] * Wm[6] + dT1[1] * Wm[7] + dT1[2] * Wm[8];
-        float tx = st.t[0], ty = st.t[1], tz = st.t[2];
+        float tx = st.t[0], ty = st.t[1];
         float itz = st.itz, itz2 = itz * itz;
         float dxc_dtx = st.clampx ? 0.f : itz, dxc_dtz = st.clampx ? 0.f : -tx * itz2;
         float dyc_dty = st.clampy ? 0.f : itz, dyc_dtz = st.clampy ? 0.f : -ty * itz2;
@@ -376,7 +366,7 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     kernel<<<grid, block, 0, st>>>(params, stride, cams, p->d_scene_offset,
                                    p->desc.n_scenes > 1 ? p->d_view_scene : nullptr, p->d_view_item_offset, vb, vc,
                                    vpt, p->TX, p->TY, p->desc.tile_w, p->desc.tile_h, p->desc.width, p->desc.height,
-                                   p->rec, gs, p->rect, p->radius, p->listed, p->tile_count, p->touched);
+                                   p->rec, gs, p->place, p->tile_count, p->touched);
     VBM_LAUNCH("preprocess_fwd");
     note_launches(1);
     return VBM_OK;

@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_group_count(const int2 *_
 // listed-tile word; wide rectangles are tested again with the same code).
 // Nothing is placed when the pairs overflowed.
 __global__ void k_place_pairs(const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
-                              const int64_t *__restrict__ view_item_offset, int vb, const uint32_t *__restrict__ listed,
-                              const int4 *__restrict__ rect, const SplatRec *__restrict__ rec, int TX, int TY,
+                              const int64_t *__restrict__ view_item_offset, int vb, const uint4 *__restrict__ place,
+                              const SplatRec *__restrict__ rec, int TX, int TY,
                               int tw, int th, int W, int H, uint32_t *__restrict__ tile_count,
                               const int64_t *__restrict__ n_pairs, uint64_t *__restrict__ pair_key)
 {
@@ -250,13 +250,13 @@ __global__ void k_place_pairs(const int64_t *__restrict__ scene_offset, const in
     uint64_t key = 0;
     if (gl < ns) {                     // every lane stays for the warp-wide placement
         const int64_t item = view_item_offset[v] - view_item_offset[vb] + gl;
-        word = listed[item];
+        const uint4 pl = place[item];
+        word = pl.z;
         if (word) {
-            t.rc = rect[item];
-            const float4 x = rec[item].x;
-            key = ((uint64_t)__float_as_uint(x.z) << 32) | (uint64_t)(uint32_t)item;
+            t.rc = place_rect(pl);
+            key = ((uint64_t)pl.w << 32) | (uint64_t)(uint32_t)item;
             if (word & kWideRect) {
-                const float4 g = rec[item].g, cu = rec[item].cu;
+                const float4 g = rec[item].g, cu = rec[item].cu, x = rec[item].x;
                 t = TileTest{g.x, g.y, g.z, g.w, x.x, cu.z, cu.w, x.y, t.rc};
             }
         }
@@ -956,13 +956,13 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(const uint32_
 // Item count of the call into a device scalar, and each item's depth key
 // (float bits: depth > 0 for every item with tiles, so the bits order like the
 // depths; items without tiles sort last) with the item index as value.
-__global__ void k_item_keys(int64_t n, const SplatRec *__restrict__ rec, const uint32_t *__restrict__ touched,
+__global__ void k_item_keys(int64_t n, const uint4 *__restrict__ place, const uint32_t *__restrict__ touched,
                             uint32_t *__restrict__ key, uint32_t *__restrict__ val, int64_t *__restrict__ d_n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *d_n = n;
     if (i >= n) return;
-    key[i] = touched[i] ? __float_as_uint(rec[i].x.z) : 0xffffffffu;
+    key[i] = touched[i] ? place[i].w : 0xffffffffu;
     val[i] = (uint32_t)i;
 }
 
@@ -1079,8 +1079,7 @@ __global__ void __launch_bounds__(kScanThreads) k_gather_down(const uint32_t *__
 // offsets[s + 1]).  Nothing is emitted when the total exceeds the capacity
 // (the tile scan has already reported it).
 __global__ void k_emit_pairs(const uint32_t *__restrict__ idx, const int64_t *__restrict__ offsets, int64_t n,
-                             const uint32_t *__restrict__ listed, const int4 *__restrict__ rect,
-                             const SplatRec *__restrict__ rec, const int64_t *__restrict__ view_item_offset, int vb, int vc, int TX, int TY, int tw,
+                             const uint4 *__restrict__ place, const SplatRec *__restrict__ rec, const int64_t *__restrict__ view_item_offset, int vb, int vc, int TX, int TY, int tw,
                              int th, int W, int H, int64_t capacity, uint32_t *__restrict__ pair_tile,
                              uint32_t *__restrict__ pair_item)
 {
@@ -1096,14 +1095,18 @@ __global__ void k_emit_pairs(const uint32_t *__restrict__ idx, const int64_t *__
         if (s < n && offsets[s + 1] != offsets[s]) {
             beg = offsets[s];
             item = idx[s];
-            word = listed[item];
+            const uint4 pl = place[item];
+            word = pl.z;
             int lo = 0, hi = vc - 1;   // view of the item: last v with offset <= item
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (view_item_offset[vb + mid] - base_item <= (int64_t)item) lo = mid; else hi = mid - 1;
             }
-            const SplatRec r = rec[item];
-            t = TileTest{r.g.x, r.g.y, r.g.z, r.g.w, r.x.x, r.cu.z, r.cu.w, r.x.y, rect[item]};
+            t.rc = place_rect(pl);
+            if (word & kWideRect) {
+                const SplatRec r = rec[item];
+                t = TileTest{r.g.x, r.g.y, r.g.z, r.g.w, r.x.x, r.cu.z, r.cu.w, r.x.y, t.rc};
+            }
             tile0 = (uint32_t)lo * (uint32_t)(TX * TY);
         }
         emit_listed(word, t, tile0, item, beg, TX, tw, th, W, H, pair_tile, pair_item);
@@ -1161,7 +1164,7 @@ vbm_status radix_order(vbm_plan *p, int vb, int vc, int64_t n_tiles, cudaStream_
 {
     const int64_t n_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
     if (n_items == 0) return VBM_OK;
-    k_item_keys<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(n_items, p->rec, p->touched, p->item_key[0],
+    k_item_keys<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(n_items, p->place, p->touched, p->item_key[0],
                                                                     p->item_val[0], p->d_n_items);
     VBM_LAUNCH("item_keys");
     note_launches(1);
@@ -1183,7 +1186,7 @@ vbm_status radix_order(vbm_plan *p, int vb, int vc, int64_t n_tiles, cudaStream_
     const int tile_bits = ceil_log2(n_tiles);
     const int passes = (tile_bits + kRadixBits - 1) / kRadixBits;
     const int first = passes & 1;
-    k_emit_pairs<<<num_sms() * 4, 256, 0, st>>>(p->item_val[a], p->item_offset, n_items, p->listed, p->rect, p->rec,
+    k_emit_pairs<<<num_sms() * 4, 256, 0, st>>>(p->item_val[a], p->item_offset, n_items, p->place, p->rec,
                                                  p->d_view_item_offset, vb, vc, p->TX,
                                                  p->TY, p->desc.tile_w, p->desc.tile_h, p->desc.width, p->desc.height,
                                                  cap, tiles[first], items[first]);
@@ -1247,7 +1250,7 @@ vbm_status binning(vbm_plan *p, int vb, int vc, cudaStream_t st)
     if (!radix && p->max_scene > 0) {
         dim3 grid((unsigned)((p->max_scene + 255) / 256), (unsigned)vc);
         k_place_pairs<<<grid, 256, 0, st>>>(p->d_scene_offset, p->desc.n_scenes > 1 ? p->d_view_scene : nullptr,
-                                            p->d_view_item_offset, vb, p->listed, p->rect, p->rec, p->TX, p->TY,
+                                            p->d_view_item_offset, vb, p->place, p->rec, p->TX, p->TY,
                                             p->desc.tile_w, p->desc.tile_h,
                                             p->desc.width, p->desc.height, p->tile_count, p->d_n_pairs, p->pair_key);
         VBM_LAUNCH("place_pairs");

@@ -38,6 +38,14 @@ struct __align__(64) SplatRec {
     float4 g, c, cu, x;
 };
 static_assert(sizeof(SplatRec) == 64, "one 64-byte line per splat");
+// The last word of a SplatRec (x.w) holds the splat radius in pixels (int32 bits).
+
+// Per-item placement record (uint4) written by the projection: the tile
+// rectangle [x0, x1) x [y0, y1) as x0 | x1 << 16 and y0 | y1 << 16, the
+// listed-tile word (listed_tiles) and the camera depth's float bits, so that
+// the pair placement reads one 16-byte load per item.  Plans have at most
+// kMaxTilesPerAxis tiles along each axis, so every coordinate fits 16 bits.
+constexpr int kMaxTilesPerAxis = 65535;
 constexpr int kProfileEvents = 7;       // timing events a plan can record (vbm_plan_set_profile)
 
 #ifdef __CUDACC__
@@ -86,6 +94,17 @@ struct TileTest {
     float u, v, A, B, C, bc, ba, tau;
     int4 rc;
 };
+
+__device__ __forceinline__ uint4 pack_place(int4 rc, uint32_t word, float depth)
+{
+    return make_uint4((uint32_t)rc.x | (uint32_t)rc.z << 16, (uint32_t)rc.y | (uint32_t)rc.w << 16, word,
+                      __float_as_uint(depth));
+}
+
+__device__ __forceinline__ int4 place_rect(uint4 pl)
+{
+    return make_int4((int)(pl.x & 0xffffu), (int)(pl.y & 0xffffu), (int)(pl.x >> 16), (int)(pl.y >> 16));
+}
 
 // Rectangles of up to this many tiles are tested by their own lane; larger
 // ones by the whole warp, 32 tiles at a time (a few large splats would
@@ -403,9 +422,7 @@ struct vbm_plan {
 
     // per item
     vbm::SplatRec *rec = nullptr;            // [items] the projected splat, one 64-byte line
-    int4 *rect = nullptr;
-    int32_t *radius = nullptr;
-    uint32_t *listed = nullptr;              // [items] listed-tile word of the projection (listed_tiles)
+    uint4 *place = nullptr;                  // [items] tile rectangle, listed-tile word, depth (placement record)
     float *g_splat = nullptr;               // [items][kGradStride]
     bool g_splat_clear = false;             // host: zeroed by the last forward, no backward since
     bool bwd_seen = false;                  // host: a backward has run on this plan

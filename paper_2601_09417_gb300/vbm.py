@@ -72,7 +72,7 @@ class PlanDesc(ctypes.Structure):
 
 class PlanBuffers(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int64)] + [(name, ctypes.c_void_p) for name in
-                                                ("rec", "rect", "radius", "pair_tile", "pair_item", "ranges",
+                                                ("rec", "place", "pair_tile", "pair_item", "ranges",
                                                  "n_pairs", "T_final", "n_contrib", "g_splat", "seg_count")] + \
         [("checkpoint_slots", ctypes.c_int64)]
 

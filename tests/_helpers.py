@@ -47,10 +47,22 @@ def to_device(P, cams, device="cuda"):
 
 def split_records(rec):
     """The fields of a plan's per-item splat records ([n][16] float32, one 64-byte line
-    each: u v A B | r g b opacity | half-widths, B/C, B/A | C, tau, depth, -)."""
+    each: u v A B | r g b opacity | half-widths, B/C, B/A | C, tau, depth, radius (int32 bits))."""
     return dict(geo=np.ascontiguousarray(rec[:, 0:4]), col=np.ascontiguousarray(rec[:, 4:8]),
                 cull=np.ascontiguousarray(rec[:, 8:12]), conic_c=np.ascontiguousarray(rec[:, 12]),
-                tau=np.ascontiguousarray(rec[:, 13]), depth=np.ascontiguousarray(rec[:, 14]))
+                tau=np.ascontiguousarray(rec[:, 13]), depth=np.ascontiguousarray(rec[:, 14]),
+                radius=np.ascontiguousarray(rec[:, 15]).view(np.int32))
+
+
+def split_place(place):
+    """A plan's per-item placement records ([n][4] uint32: x0 | x1 << 16, y0 | y1 << 16,
+    listed-tile word, depth bits) as the tile rectangle [n][4] = x0 y0 x1 y1 (int32), the
+    listed-tile words and the depths."""
+    place = np.asarray(place, dtype=np.uint32)
+    rect = np.stack([place[:, 0] & 0xFFFF, place[:, 1] & 0xFFFF, place[:, 0] >> 16, place[:, 1] >> 16],
+                    axis=1).astype(np.int32)
+    return dict(rect=rect, listed=np.ascontiguousarray(place[:, 2]),
+                place_depth=np.ascontiguousarray(place[:, 3]).view(np.float32))
 
 
 def plan_state(plan, n_views):
@@ -60,8 +72,7 @@ def plan_state(plan, n_views):
     st = dict(n_items=n)
     rec = read_device(b.rec, (n, 16), np.float32)
     st.update(split_records(rec))
-    st["rect"] = read_device(b.rect, (n, 4), np.int32)
-    st["radius"] = read_device(b.radius, (n,), np.int32)
+    st.update(split_place(read_device(b.place, (n, 4), np.uint32)))
     n_pairs = int(read_device(b.n_pairs, (1,), np.int64)[0])
     st["n_pairs"] = n_pairs
     st["pair_tile"] = read_device(b.pair_tile, (n_pairs,), np.uint32)

@@ -97,6 +97,27 @@ def test_binning_bit_exact_given_gpu_depths(cuda_lib, tile, radix):
     assert np.array_equal(st["pair_tile"].astype(np.int64), tiles)
     assert np.array_equal(st["pair_item"].astype(np.int64), items.astype(np.int64))
     assert np.array_equal(st["ranges"], ranges)
+    # the placement records: listed-tile words as the oracle's lists give them, the depth
+    # the splat record's bit for bit
+    assert np.array_equal(st["listed"], _listed_words(tiles, items, st["rect"], st["n_items"], TX, TY))
+    assert np.array_equal(st["place_depth"].view(np.uint32), st["depth"].view(np.uint32))
+
+
+def _listed_words(tiles, items, rect, n_items, TX, TY):
+    """Each item's listed-tile word from a pair list: for a rectangle of at most 8 tiles,
+    bit k for its k-th tile (row-major) in the list; a larger rectangle with any listed
+    tile: bit 31 alone; no listed tile: 0."""
+    items = np.asarray(items, dtype=np.int64)
+    local = np.asarray(tiles, dtype=np.int64) % (TX * TY)
+    tx, ty = local % TX, local // TX
+    x0, y0, x1, y1 = (rect[items, c].astype(np.int64) for c in range(4))
+    cols = x1 - x0
+    small = cols * (y1 - y0) <= 8
+    words = np.zeros(n_items, dtype=np.uint32)
+    k = (ty - y0) * cols + (tx - x0)
+    np.bitwise_or.at(words, items[small], (np.uint32(1) << k[small].astype(np.uint32)))
+    words[items[~small]] = np.uint32(1 << 31)
+    return words
 
 
 @pytest.mark.parametrize("radix", [False, True])

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import oracle_bank, rel_group_error, split_records
+from _helpers import oracle_bank, rel_group_error, split_place, split_records
 from oracle import raster as oraster
 
 pytestmark = pytest.mark.gpu
@@ -71,7 +71,7 @@ def test_full_size_sampled_tiles(cuda_lib, key, tile, ppt, gl, recompute, seg):
     pair_item = vbm.device_tensor(b.pair_item, (n_pairs,), np.int32)
     # --- binning of view 0, bit-exact given the GPU's rectangles and depths
     n0 = int(so[1]) if w.view_scene is None else int(so[int(w.view_scene[0]) + 1] - so[int(w.view_scene[0])])
-    rect0 = vbm.device_tensor(b.rect, (n0, 4), np.int32).cpu().numpy()
+    rect0 = split_place(vbm.device_tensor(b.place, (n0, 4), np.int32).cpu().numpy().view(np.uint32))["rect"]
     f0 = split_records(vbm.device_tensor(b.rec, (n0, 16), np.float32).cpu().numpy())
     depth0 = f0["depth"].astype(np.float64)
     geo0 = f0["geo"]

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import read_device, rel_group_error, scene, split_records, to_device
+from _helpers import read_device, rel_group_error, scene, split_place, split_records, to_device
 from oracle import adam as oadam
 from oracle import loss as oloss
 from oracle import raster as oraster
@@ -242,7 +242,7 @@ def test_gradient_central_differences_c1_full_size(cuda_lib):
         st = dict(img=img, n_contrib=vbm.device_tensor(b.n_contrib, (V, H, W), np.int32).clone(),
                   pair_item=vbm.device_tensor(b.pair_item, (n_pairs,), np.int32).clone(),
                   pair_tile=vbm.device_tensor(b.pair_tile, (n_pairs,), np.int32).clone(),
-                  rect=read_device(b.rect, (b.n_items, 4), np.int32),
+                  rect=split_place(read_device(b.place, (b.n_items, 4), np.uint32))["rect"],
                   **split_records(read_device(b.rec, (b.n_items, 16), np.float32)))
         return L, st
 
