@@ -292,15 +292,17 @@ def profiled_traffic(kernel, workload_key):
 
 # ------------------------------------------------------- algorithmic work
 
-def step_work(N, items, V, HW, n_dup, p_fwd, p_bwd, recompute):
+def step_work(N, items, V, HW, n_dup, p_fwd, p_bwd, recompute, fused_adam=False):
     """Algorithmic work per step of each kernel group (FP32 FLOP, ex2/rcp evaluations, HBM bytes),
     the counts of the method itself (N Gaussians, `items` (view, Gaussian) pairs (N V for one
     scene; each view its own scene's Gaussians in a batch of scenes), V views of HW pixels,
     n_dup (view, tile, Gaussian) pairs, p_fwd / p_bwd evaluated pairs) and not of this
-    implementation."""
+    implementation.  fused_adam: the projection backward and Adam as one group, which reads
+    the splat gradients, the parameters once and the two moments, and writes the parameters
+    and moments (no gradient array)."""
     px = V * HW
     state = 0 if recompute else 8                      # T_final and the last contributor per pixel
-    return {
+    work = {
         "projection": dict(flop=250 * items, sfu=0, bytes=N * 56 + items * 40),
         "binning_sort": dict(flop=0, sfu=0, bytes=items * 8 + n_dup * 12 + n_dup * 12 * 2 + n_dup * 8),
         "raster_fwd": dict(flop=FWD_FLOP_PER_PAIR * p_fwd, sfu=p_fwd, bytes=n_dup * 40 + px * (12 + state)),
@@ -312,6 +314,10 @@ def step_work(N, items, V, HW, n_dup, p_fwd, p_bwd, recompute):
         "projection_bwd": dict(flop=400 * items, sfu=0, bytes=items * 36 + N * 56),
         "adam": dict(flop=0, sfu=0, bytes=14 * N * 28),
     }
+    if fused_adam:
+        del work["projection_bwd"], work["adam"]
+        work["projection_bwd_adam"] = dict(flop=400 * items, sfu=0, bytes=items * 36 + N * 56 * 6)
+    return work
 
 
 def lower_bound_ms(w, peaks):
@@ -692,7 +698,10 @@ def main():
     torch.cuda.synchronize()
     clocks.mark_begin()
     t_wall0 = time.perf_counter()
-    groups = ("head", "projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam")
+    # the backward's end event follows Adam when the two are fused
+    fused_adam = ft.fused_adam
+    groups = ("head", "projection", "binning_sort", "raster_fwd", "loss", "raster_bwd") + \
+        (("projection_bwd_adam",) if fused_adam else ("projection_bwd", "adam"))
     step_ms, grp_ms, pairs, counts = [], {g: [] for g in groups}, [], []
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     count_every = max(1, args.steps // 8)
@@ -705,7 +714,7 @@ def main():
         e_ev.record()
         e_ev.synchronize()
         step_ms.append(s_ev.elapsed_time(e_ev))
-        marks = [s_ev, kev[4], kev[5], kev[0], kev[1], kev[2], kev[3], kev[6], e_ev]
+        marks = [s_ev, kev[4], kev[5], kev[0], kev[1], kev[2], kev[3]] + ([] if fused_adam else [kev[6]]) + [e_ev]
         for g, a, b in zip(groups, marks[:-1], marks[1:]):
             grp_ms[g].append(a.elapsed_time(b))
         pairs.append(int(n_pairs_dev.item()))
@@ -810,9 +819,10 @@ def main():
     # ------------------------------------------------------------- roofline
     n_pairs = float(np.mean(pairs))
     n_items = vbm.batch_items([0, n] if w.scene_offset is None else w.scene_offset, V, w.view_scene)
-    work = step_work(n, n_items, V, H * W, n_pairs, p_fwd_step, p_bwd_step, batch["recompute"])
+    work = step_work(n, n_items, V, H * W, n_pairs, p_fwd_step, p_bwd_step, batch["recompute"],
+                     fused_adam=fused_adam)
     kernels, lb_sum = {}, 0.0
-    for g in ("projection", "binning_sort", "raster_fwd", "loss", "raster_bwd", "projection_bwd", "adam"):
+    for g in groups[1:]:
         lb, bound = lower_bound_ms(work[g], peaks)
         t = state_ms[g]
         rec = {"ms": t, "lower_bound_ms": lb, "bound": bound, "frac": lb / t if t > 0 else None,
@@ -853,6 +863,7 @@ def main():
                        "bwd_pixels_per_thread": bppt or ppt, "bwd_group_lanes": bgl or gl,
                        "pair_order": "device radix sorts" if args.radix else "bucketed per-tile sort",
                        "compositing_state": "recomputed in the backward" if batch["recompute"] else "stored",
+                       "adam": "fused into the projection backward" if fused_adam else "separate kernel",
                        "pairs_mean": int(n_pairs),
                        "timed_iterations": "fine-tuning iterations %d-%d from the built Gaussians (the launch "
                                            "configuration was tuned on a copy %d iterations in)"

@@ -291,6 +291,23 @@ VBM_API vbm_status vbm_raster_bwd(vbm_plan *plan, const float *d_params, int64_t
                           const float *d_dL_dimg, const float *d_dL_dalpha, float *d_grad,
                           int32_t accumulate, void *stream);
 
+/* The backward of the last forward call fused with the Adam step that
+ * follows it in fine-tuning (Sec. 4.4, Sec. 5.2): the result equals, bit for
+ * bit, vbm_raster_bwd with accumulate = 0 into a gradient array that is zero
+ * outside the rows the call's views see, followed by vbm_adam on d_params,
+ * d_m, d_v over the first n columns (every one of them takes its Adam step;
+ * columns of scenes no view of the call renders with a zero gradient).  The
+ * gradient itself is not written: each Gaussian's gradient, summed over the
+ * views in registers, is applied where it is formed, saving the gradient
+ * array's write and read and a second read of the parameters.  d_params is
+ * updated in place (it is read by the backward first, per Gaussian).
+ * Arguments as for vbm_raster_bwd and vbm_adam; stride >= n. */
+VBM_API vbm_status vbm_raster_bwd_adam(vbm_plan *plan, float *d_params, int64_t stride, const vbm_camera *d_cams,
+                                       int32_t view_begin, int32_t view_count, const float bg[3],
+                                       const float *d_dL_dimg, const float *d_dL_dalpha, float *d_m, float *d_v,
+                                       int64_t n, int32_t *d_step, const float lrs[5], float beta1, float beta2,
+                                       float eps, uint32_t *d_nonfinite, void *stream);
+
 /* Internal buffers of a plan after a forward call (device pointers, read
  * only, valid until the next call on the plan).  Items are numbered view by
  * view over the call's views. */

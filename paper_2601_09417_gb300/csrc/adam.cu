@@ -17,33 +17,15 @@ __global__ void k_step_inc(int32_t *step)
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
 }
 
-// One scalar's update (p, m, v in place); false when g is not finite (nothing
-// is changed).
-__device__ __forceinline__ bool adam_elem(float &p, float &m, float &v, float g, float lr, float beta1,
-                                          float beta2, float eps, float bc1, float bc2)
-{
-    if (!isfinite(g)) return false;
-    m = beta1 * m + (1.f - beta1) * g;
-    v = beta2 * v + (1.f - beta2) * g * g;
-    const float mhat = m / bc1;
-    const float vhat = v / bc2;
-    p -= lr * mhat / (sqrtf(vhat) + eps);
-    return true;
-}
-
-__device__ __forceinline__ float row_lr(int row, float lr0, float lr1, float lr2, float lr3, float lr4)
-{
-    return row < 3 ? lr0 : row < 6 ? lr1 : row < 10 ? lr2 : row < 11 ? lr3 : lr4;
-}
-
 // the bias corrections are the same for every scalar: one thread of the block
 // evaluates them
 __device__ __forceinline__ void bias_corrections(float *s_bc, const int32_t *step, float beta1, float beta2)
 {
     if (threadIdx.x == 0) {
         const int t = *step;
-        s_bc[0] = 1.f - powf(beta1, (float)t);
-        s_bc[1] = 1.f - powf(beta2, (float)t);
+        const float2 bc = adam_bias_corrections(t, beta1, beta2);
+        s_bc[0] = bc.x;
+        s_bc[1] = bc.y;
     }
     __syncthreads();
 }
@@ -78,7 +60,7 @@ __global__ void k_adam_flat(float *__restrict__ P, const float *__restrict__ G, 
                 ++row;
                 row_end += n;
             }
-            bad += !adam_elem(p[k], m[k], v[k], g[k], row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, bc1,
+            bad += !adam_elem(p[k], m[k], v[k], g[k], adam_row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, bc1,
                               bc2);
         }
         *reinterpret_cast<float4 *>(P + e0) = p4;
@@ -91,7 +73,7 @@ __global__ void k_adam_flat(float *__restrict__ P, const float *__restrict__ G, 
                 row_end += n;
             }
             float p = P[e], m = M[e], v = V[e];
-            if (!adam_elem(p, m, v, G[e], row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, bc1, bc2)) {
+            if (!adam_elem(p, m, v, G[e], adam_row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, bc1, bc2)) {
                 ++bad;
                 continue;
             }
@@ -117,7 +99,7 @@ __global__ void k_adam_rows(float *__restrict__ P, const float *__restrict__ G, 
     if (i >= n) return;
     const int64_t e = row * stride + i;
     float p = P[e], m = M[e], v = V[e];
-    if (!adam_elem(p, m, v, G[e], row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, s_bc[0], s_bc[1])) {
+    if (!adam_elem(p, m, v, G[e], adam_row_lr(row, lr0, lr1, lr2, lr3, lr4), beta1, beta2, eps, s_bc[0], s_bc[1])) {
         if (nonfinite) atomicAdd(nonfinite, 1u);
         return;
     }
@@ -128,12 +110,19 @@ __global__ void k_adam_rows(float *__restrict__ P, const float *__restrict__ G, 
 
 }  // namespace
 
-vbm_status adam_step(float *P, const float *G, float *M, float *V, int64_t n, int64_t stride, int32_t *step,
-                     const float lrs[5], float beta1, float beta2, float eps, uint32_t *nonfinite, cudaStream_t st)
+vbm_status adam_step_inc(int32_t *step, cudaStream_t st)
 {
     k_step_inc<<<1, 32, 0, st>>>(step);
     VBM_LAUNCH("adam_step_inc");
     note_launches(1);
+    return VBM_OK;
+}
+
+vbm_status adam_step(float *P, const float *G, float *M, float *V, int64_t n, int64_t stride, int32_t *step,
+                     const float lrs[5], float beta1, float beta2, float eps, uint32_t *nonfinite, cudaStream_t st)
+{
+    vbm_status s = adam_step_inc(step, st);
+    if (s != VBM_OK) return s;
     if (n == 0) return VBM_OK;
     const bool flat = stride == n && ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) |
                                        reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(V)) & 15) == 0;

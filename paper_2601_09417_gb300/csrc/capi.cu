@@ -295,6 +295,7 @@ vbm_status vbm_raster_fwd(vbm_plan *p, const float *params, int64_t stride, cons
     p->last_view_count = vc;
     p->last_items = p->view_item_offset[vb + vc] - p->view_item_offset[vb];
     p->g_splat_clear = p->bwd_seen;   // the projection zeroes the items' splat-gradient records
+    p->bwd_queue_used = false;        // the binning zeroes the work-queue counters
     record_event(p->prof_ev[4], st);
     s = preprocess_fwd(p, params, stride, cams, vb, vc, st);
     record_event(p->prof_ev[5], st);
@@ -315,6 +316,36 @@ vbm_status vbm_raster_bwd(vbm_plan *p, const float *params, int64_t stride, cons
     cudaStream_t st = (cudaStream_t)stream;
     s = raster_bwd(p, params, stride, vb, vc, bg, dimg, dalpha, grad, st);
     if (s == VBM_OK) s = preprocess_bwd(p, params, stride, cams, vb, vc, grad, accumulate, st);
+    record_event(p->prof_ev[6], st);
+    return s;
+}
+
+vbm_status vbm_raster_bwd_adam(vbm_plan *p, float *params, int64_t stride, const vbm_camera *cams, int32_t vb,
+                               int32_t vc, const float bg[3], const float *dimg, const float *dalpha, float *m, float *v,
+                               int64_t n, int32_t *step, const float lrs[5], float beta1, float beta2, float eps,
+                               uint32_t *nonfinite, void *stream)
+{
+    vbm_status s = check_call(p, params, stride, cams, vb, vc);
+    if (s != VBM_OK) return s;
+    VBM_ARG(bg && dimg && m && v && step && lrs, "null argument");
+    VBM_ARG(n >= 0 && stride >= n, "invalid size");
+    VBM_ARG(vb == p->last_view_begin && vc == p->last_view_count,
+            "backward views differ from the last forward call on this plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    AdamArgs a;
+    a.P = params;
+    a.M = m;
+    a.V = v;
+    a.step = step;
+    a.n = n;
+    for (int k = 0; k < 5; k++) a.lr[k] = lrs[k];
+    a.beta1 = beta1;
+    a.beta2 = beta2;
+    a.eps = eps;
+    a.nonfinite = nonfinite;
+    s = raster_bwd(p, params, stride, vb, vc, bg, dimg, dalpha, nullptr, st);
+    if (s == VBM_OK) s = adam_step_inc(step, st);
+    if (s == VBM_OK) s = preprocess_bwd(p, params, stride, cams, vb, vc, nullptr, 0, st, &a);
     record_event(p->prof_ev[6], st);
     return s;
 }

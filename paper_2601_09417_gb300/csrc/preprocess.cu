@@ -215,18 +215,66 @@ __global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, co
     }
 }
 
+// Adam step of one Gaussian's 14 parameters with gradient g14 (zero when
+// !seen), in place in P, M, V ([14][stride]); non-finite gradient elements
+// leave their scalars unchanged and are counted.  Rows go in two batches of
+// seven, each batch's loads issued before its stores (the three arrays may
+// alias as far as the compiler knows, so it would not move a later row's
+// loads above an earlier row's stores).
+__device__ __forceinline__ void adam_gaussian(const AdamArgs &a, int64_t stride, int64_t g, const float (&g14)[14],
+                                              bool seen)
+{
+    const float2 bc = adam_bias_corrections(*a.step, a.beta1, a.beta2);
+    uint32_t bad = 0;
+#pragma unroll
+    for (int k0 = 0; k0 < 14; k0 += 7) {
+        float p[7], m[7], v[7];
+#pragma unroll
+        for (int k = 0; k < 7; k++) {
+            const int64_t e = (k0 + k) * stride + g;
+            p[k] = a.P[e];
+            m[k] = a.M[e];
+            v[k] = a.V[e];
+        }
+#pragma unroll
+        for (int k = 0; k < 7; k++) {
+            const bool ok = adam_elem(p[k], m[k], v[k], seen ? g14[k0 + k] : 0.f,
+                                      adam_row_lr(k0 + k, a.lr[0], a.lr[1], a.lr[2], a.lr[3], a.lr[4]), a.beta1,
+                                      a.beta2, a.eps, bc.x, bc.y);
+            bad += !ok;
+            if (!ok) continue;
+            const int64_t e = (k0 + k) * stride + g;
+            a.P[e] = p[k];
+            a.M[e] = m[k];
+            a.V[e] = v[k];
+        }
+    }
+    if (bad && a.nonfinite) atomicAdd(a.nonfinite, bad);
+}
+
 // Chain rule from the per-item splat gradient (du, dv, dA, dB, dC, dopacity,
 // dr, dg, db) to the 14 parameters, summed over the views of the call that
 // see Gaussian g.  Mirrors the forward step by step (see the header comment).
-__global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
+// ADAM: the gradient is not written; the thread applies the Adam step to its
+// Gaussian's parameters instead (Gaussians [0, a.n); those outside
+// [g_begin, g_end) have a zero gradient), with the separate Adam kernel's
+// arithmetic, so the result equals a backward with accumulate = 0 into a
+// zeroed gradient followed by that kernel, bit for bit.
+template <bool ADAM>
+__global__ void k_preprocess_bwd(const float *P, int64_t stride, const vbm_camera *__restrict__ cams,
                                  const int64_t *__restrict__ scene_offset, int n_scenes,
                                  const int32_t *__restrict__ scene_view_ptr, const int32_t *__restrict__ scene_views,
-                                 const int64_t *__restrict__ view_item_offset, int vb, int vc, int64_t n_items,
+                                 const int64_t *__restrict__ view_item_offset, int vb, int vc,
                                  const float *__restrict__ gs, float *__restrict__ grad, int accumulate,
-                                 int64_t g_begin, int64_t g_end)
+                                 int64_t g_begin, int64_t g_end, AdamArgs a)
 {
-    const int64_t g = g_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= g_end) return;
+    const int64_t g = (ADAM ? 0 : g_begin) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ADAM ? g >= a.n : g >= g_end) return;
+    if (ADAM && (g < g_begin || g >= g_end)) {   // no view of the call renders g's scene
+        const float zero[14] = {};
+        adam_gaussian(a, stride, g, zero, false);
+        return;
+    }
     int lo = 0, hi = n_scenes - 1;  // scene of g: last s with scene_offset[s] <= g
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -335,6 +383,10 @@ __global__ void k_preprocess_bwd(const float *__restrict__ P, int64_t stride, co
 #pragma unroll
         for (int k = 0; k < 4; k++) acc[6 + k] += (dq[k] - st.qn[k] * dot) * iq;
     }
+    if constexpr (ADAM) {
+        adam_gaussian(a, stride, g, acc, seen);
+        return;
+    }
     if (!seen) return;
 #pragma unroll
     for (int k = 0; k < 14; k++) {
@@ -373,7 +425,7 @@ vbm_status preprocess_fwd(vbm_plan *p, const float *params, int64_t stride, cons
 }
 
 vbm_status preprocess_bwd(vbm_plan *p, const float *params, int64_t stride, const vbm_camera *cams, int vb, int vc,
-                          float *grad, int accumulate, cudaStream_t st)
+                          float *grad, int accumulate, cudaStream_t st, const AdamArgs *adam)
 {
     // Gaussians of the scenes the call's views render form one column range
     // when the views are consecutive; bound it by the scenes' extent.
@@ -383,15 +435,23 @@ vbm_status preprocess_bwd(vbm_plan *p, const float *params, int64_t stride, cons
         g_begin = std::min(g_begin, p->scene_offset[s]);
         g_end = std::max(g_end, p->scene_offset[s + 1]);
     }
-    if (g_end <= g_begin) return VBM_OK;
+    if (g_end <= g_begin && !adam) return VBM_OK;
     int64_t n = g_end - g_begin;
     // one-warp blocks: a thread's work (its Gaussian's views) is long and the
     // blocks are few, so the finest granularity keeps the SMs evenly loaded
     // (with 128-thread blocks the 8 x 512^2 workload left a second wave of 19
     // blocks running on 19 SMs)
-    k_preprocess_bwd<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(
-        params, stride, cams, p->d_scene_offset, p->desc.n_scenes, p->d_scene_view_ptr, p->d_scene_views,
-        p->d_view_item_offset, vb, vc, p->last_items, p->g_splat, grad, accumulate, g_begin, g_end);
+    if (adam) {   // every Gaussian of [0, n) takes its Adam step
+        const int64_t na = adam->n;
+        if (na == 0) return VBM_OK;
+        k_preprocess_bwd<true><<<(unsigned)((na + 31) / 32), 32, 0, st>>>(
+            params, stride, cams, p->d_scene_offset, p->desc.n_scenes, p->d_scene_view_ptr, p->d_scene_views,
+            p->d_view_item_offset, vb, vc, p->g_splat, nullptr, 0, g_begin, std::min(g_end, na), *adam);
+    } else {
+        k_preprocess_bwd<false><<<(unsigned)((n + 31) / 32), 32, 0, st>>>(
+            params, stride, cams, p->d_scene_offset, p->desc.n_scenes, p->d_scene_view_ptr, p->d_scene_views,
+            p->d_view_item_offset, vb, vc, p->g_splat, grad, accumulate, g_begin, g_end, AdamArgs{});
+    }
     VBM_LAUNCH("preprocess_bwd");
     note_launches(1);
     return VBM_OK;

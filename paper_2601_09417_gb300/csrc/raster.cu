@@ -993,6 +993,10 @@ vbm_status launch_bwd(vbm_plan *p, int vb, int vc, const float bg[3], const floa
     const int n_items_w = n_tiles * nr;
     record_event(p->prof_ev[2], st);
     if (p->desc.flags & VBM_PLAN_PERSISTENT) {
+        // a second backward of the same forward finds the backward's queue
+        // counter spent: clear it (the binning clears it for the first)
+        if (p->bwd_queue_used) VBM_CUDA(cudaMemsetAsync(p->tile_queue + 1, 0, sizeof(int), st));
+        p->bwd_queue_used = true;
         const int grid = persistent_grid(k_raster_bwd<PPT, GL, true>, n_items_w);
         k_raster_bwd<PPT, GL, true><<<grid, kWarps * 32, 0, st>>>(
             p->tile_order, p->tile_queue + 1, n_items_w, nr, p->ranges, p->pair_item, p->rec, p->desc.width, p->desc.height, p->desc.tile_w, p->desc.tile_h, p->TX, p->TY, vb,

@@ -48,6 +48,19 @@ static_assert(sizeof(SplatRec) == 64, "one 64-byte line per splat");
 constexpr int kMaxTilesPerAxis = 65535;
 constexpr int kProfileEvents = 7;       // timing events a plan can record (vbm_plan_set_profile)
 
+// Adam step fused into the projection backward (vbm_raster_bwd_adam): the
+// first n columns of P, M, V ([14][stride], updated in place), the device
+// step counter (already incremented for this step), per-row-group learning
+// rates, and the optional non-finite gradient counter.
+struct AdamArgs {
+    float *P = nullptr, *M = nullptr, *V = nullptr;
+    const int32_t *step = nullptr;
+    int64_t n = 0;
+    float lr[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float beta1 = 0.f, beta2 = 0.f, eps = 0.f;
+    uint32_t *nonfinite = nullptr;
+};
+
 #ifdef __CUDACC__
 // Binning tile test: smallest q = A dx^2 + 2 B dx dy + C dy^2 (dx = x - u,
 // dy = y - v) over the rectangle [x0, x1] x [y0, y1] of a tile's pixel
@@ -87,6 +100,34 @@ __device__ __forceinline__ bool tile_listed(float u, float v, float A, float B, 
     const float x0 = __fadd_rn((float)(tx * tw), 0.5f), x1 = __fsub_rn((float)min(tx * tw + tw, W), 0.5f);
     const float y0 = __fadd_rn((float)(ty * th), 0.5f), y1 = __fsub_rn((float)min(ty * th + th, H), 0.5f);
     return tile_min_q(u, v, A, B, C, bc, ba, x0, x1, y0, y1) <= tau;
+}
+
+// One Adam update of a scalar (p, m, v in place; Sec. 5.2 trains with Adam);
+// false when g is not finite (nothing is changed).  Every rounding is
+// explicit, so the separate Adam kernels and the backward fused with Adam
+// give the same bits.
+__device__ __forceinline__ bool adam_elem(float &p, float &m, float &v, float g, float lr, float beta1,
+                                          float beta2, float eps, float bc1, float bc2)
+{
+    if (!isfinite(g)) return false;
+    m = __fmaf_rn(beta1, m, __fmul_rn(1.f - beta1, g));
+    v = __fmaf_rn(beta2, v, __fmul_rn(__fmul_rn(1.f - beta2, g), g));
+    const float mhat = __fdiv_rn(m, bc1);
+    const float vhat = __fdiv_rn(v, bc2);
+    p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), eps)));
+    return true;
+}
+
+// Learning rate of parameter row `row`: mean, log-scale, quaternion, opacity, colour.
+__device__ __forceinline__ float adam_row_lr(int row, float lr0, float lr1, float lr2, float lr3, float lr4)
+{
+    return row < 3 ? lr0 : row < 6 ? lr1 : row < 10 ? lr2 : row < 11 ? lr3 : lr4;
+}
+
+// Adam's bias corrections 1 - beta^t for step t.
+__device__ __forceinline__ float2 adam_bias_corrections(int t, float beta1, float beta2)
+{
+    return make_float2(1.f - powf(beta1, (float)t), 1.f - powf(beta2, (float)t));
 }
 
 // A splat's tile-test record and its radius rectangle (tiles [x, z) x [y, w)).
@@ -426,6 +467,8 @@ struct vbm_plan {
     float *g_splat = nullptr;               // [items][kGradStride]
     bool g_splat_clear = false;             // host: zeroed by the last forward, no backward since
     bool bwd_seen = false;                  // host: a backward has run on this plan
+    bool bwd_queue_used = false;            // host: a persistent backward has taken its work queue since
+                                            // the last binning zeroed the counters
 
     // pairs
     uint64_t *pair_key = nullptr;            // [pairs] (depth bits << 32 | item), bucketed by tile
@@ -483,5 +526,6 @@ vbm_status raster_fwd(vbm_plan *p, int vb, int vc, const float bg[3], float *img
 vbm_status raster_bwd(vbm_plan *p, const float *params, int64_t stride, int vb, int vc, const float bg[3],
                       const float *dimg, const float *dalpha, float *grad, cudaStream_t st);
 vbm_status preprocess_bwd(vbm_plan *p, const float *params, int64_t stride, const vbm_camera *cams, int vb, int vc,
-                          float *grad, int accumulate, cudaStream_t st);
+                          float *grad, int accumulate, cudaStream_t st, const AdamArgs *adam = nullptr);
+vbm_status adam_step_inc(int32_t *step, cudaStream_t st);
 }  // namespace vbm

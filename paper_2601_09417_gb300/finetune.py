@@ -41,7 +41,7 @@ class FineTuner:
     def __init__(self, params, cam_records, targets, scene_offset=None, view_scene=None, tile=(16, 16), ppt=0,
                  persistent=False, pair_capacity=None, lrs=None, lam=0.2, bg=(0.0, 0.0, 0.0), extent=None,
                  device="cuda", group_lanes=0, recompute=False, segment_len=0, radix_sort=False, bwd_ppt=0,
-                 bwd_group_lanes=0):
+                 bwd_group_lanes=0, fused_adam=True):
         self.device = torch.device(device)
         self.params = params
         self.n = params.shape[1] if scene_offset is None else int(scene_offset[-1])
@@ -79,6 +79,7 @@ class FineTuner:
         self.scale = 1.0 / (self.V * 3 * self.H * self.W)
         ext = extent if extent is not None else 1.0
         self.lrs = list(lrs) if lrs is not None else default_lrs(ext)
+        self.fused_adam = bool(fused_adam)
         self.graph = None
 
     # -------------------------------------------------------------- steps
@@ -93,14 +94,24 @@ class FineTuner:
         vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
                  nonfinite=self.nonfinite)
 
+    def _backward_and_adam(self):
+        """The backward of the batched forward and the Adam step: fused (no gradient array
+        written), or, with fused_adam = False, the separate calls (self.grad then holds the
+        step's gradient)."""
+        if self.fused_adam:
+            self.plan.backward_adam(self.params, self.cams, self.dimg, self.m, self.v, self.n, self.step_count,
+                                    self.lrs, bg=self.bg, nonfinite=self.nonfinite)
+            return
+        self.plan.backward(self.params, self.cams, self.dimg, self.grad, bg=self.bg)
+        vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
+                 nonfinite=self.nonfinite)
+
     def step_batched(self):
         """All views in one launch per kernel, then Adam."""
         self.plan.forward(self.params, self.cams, self.img, bg=self.bg)
         vbm.loss(self.img, self.targets, self.V, self.H, self.W, self.lam, self.scale, self.loss, self.dimg,
                  self.ws)
-        self.plan.backward(self.params, self.cams, self.dimg, self.grad, bg=self.bg)
-        vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
-                 nonfinite=self.nonfinite)
+        self._backward_and_adam()
 
     def capture(self):
         """Capture step_batched as a CUDA graph (run it once first on a side stream)."""
@@ -135,9 +146,7 @@ class FineTuner:
         main.wait_stream(side)
         vbm.loss(self.img, self.targets, self.V, self.H, self.W, self.lam, self.scale, self.loss, self.dimg,
                  self.ws)
-        self.plan.backward(self.params, self.cams, self.dimg, self.grad, bg=self.bg)
-        vbm.adam(self.params, self.grad, self.m, self.v, self.n, self.step_count, self.lrs,
-                 nonfinite=self.nonfinite)
+        self._backward_and_adam()
         host_loss.copy_(self.loss, non_blocking=True)
 
     def capture_host(self, host_targets, host_loss):

@@ -23,7 +23,7 @@ EXPORTED = ["vbm_last_error", "vbm_version", "vbm_bank_build", "vbm_tf_apply", "
             "vbm_plan_destroy", "vbm_plan_check", "vbm_raster_fwd", "vbm_raster_bwd",
             "vbm_plan_get_buffers", "vbm_loss_workspace_size", "vbm_loss", "vbm_adam",
             "vbm_kernel_launches", "vbm_plan_set_profile", "vbm_loss_static", "vbm_bank_ablate",
-            "vbm_peak_probe"]
+            "vbm_peak_probe", "vbm_raster_bwd_adam"]
 
 
 class VbmError(RuntimeError):
@@ -111,6 +111,8 @@ def load():
         "vbm_loss_workspace_size": (I32, [I32, I32, I32, ctypes.POINTER(S)]),
         "vbm_loss": (I32, [V, V, I32, I32, I32, F32, F64, V, I32, V, V, S, V]),
         "vbm_adam": (I32, [V, V, V, V, I64, I64, V, ctypes.POINTER(F32 * 5), F32, F32, F32, V, V]),
+        "vbm_raster_bwd_adam": (I32, [V, V, I64, V, I32, I32, ctypes.POINTER(F32 * 3), V, V, V, V, I64, V,
+                                      ctypes.POINTER(F32 * 5), F32, F32, F32, V, V]),
         "vbm_kernel_launches": (I64, []),
         "vbm_loss_static": (I32, [V, V, I32, I32, I32, F32, F64, V, I32, V, V]),
         "vbm_plan_set_profile": (I32, [V, I32, ctypes.POINTER(V), V, V]),
@@ -342,6 +344,18 @@ class Plan:
         _check(self._lib.vbm_raster_bwd(self.handle, _ptr(params), params.shape[1], _ptr(cams_dev), view_begin,
                                         vc, ctypes.byref(bgc), _ptr(dimg), _ptr(dalpha), _ptr(grad),
                                         int(bool(accumulate)), _stream()))
+
+    def backward_adam(self, params, cams_dev, dimg, m, v, n, step, lrs, dalpha=None, view_begin=0, view_count=None,
+                      bg=(0.0, 0.0, 0.0), beta1=0.9, beta2=0.999, eps=1e-15, nonfinite=None):
+        """The backward of the last forward fused with the Adam step (vbm_raster_bwd_adam):
+        params, m and v are updated in place; no gradient array is written."""
+        vc = self.n_views - view_begin if view_count is None else view_count
+        bgc = (ctypes.c_float * 3)(*bg)
+        lr = (ctypes.c_float * 5)(*[float(x) for x in lrs])
+        _check(self._lib.vbm_raster_bwd_adam(self.handle, _ptr(params), params.shape[1], _ptr(cams_dev), view_begin,
+                                             vc, ctypes.byref(bgc), _ptr(dimg), _ptr(dalpha), _ptr(m), _ptr(v),
+                                             int(n), _ptr(step), ctypes.byref(lr), float(beta1), float(beta2),
+                                             float(eps), _ptr(nonfinite), _stream()))
 
     def set_profile(self, events=None, n_eval=None, n_contrib=None):
         """Record cudaEvents (4 or 7 torch.cuda.Event, see vbm_plan_set_profile) around the

@@ -33,6 +33,13 @@ def test_step_work_counts():
     # a batch of scenes counts each view's own scene
     s = bench.step_work(N, 1234, V, HW, P, pf, pb, recompute=False)
     assert s["projection"]["bytes"] == 56 * N + 40 * 1234
+    # projection backward fused with Adam: one group, the gradient array's write and read
+    # and the second parameter read gone
+    f = bench.step_work(N, items, V, HW, P, pf, pb, recompute=False, fused_adam=True)
+    assert "adam" not in f and "projection_bwd" not in f
+    sep = w["projection_bwd"]["bytes"] + w["adam"]["bytes"] + 14 * N * 4   # + the gradient's write
+    assert sep - f["projection_bwd_adam"]["bytes"] == 3 * 14 * N * 4         # gradient write, read; P re-read
+    assert f["projection_bwd_adam"]["flop"] == w["projection_bwd"]["flop"]
 
 
 def test_lower_bound_takes_the_binding_resource():

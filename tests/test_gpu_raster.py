@@ -329,6 +329,31 @@ def test_backward_end_to_end_fp64(cuda_lib):
         assert nrm < 1e-3 and elt < 1e-3, (lo, nrm, elt)
 
 
+@pytest.mark.parametrize("persistent,seg", [(False, 0), (True, 64), (True, -1)])
+def test_second_backward_of_one_forward(cuda_lib, persistent, seg):
+    """Two backward calls after one forward give the same gradient (up to the atomic order
+    of the splat-gradient sums): the second finds its splat-gradient records and, in
+    persistent plans, its work-queue counter cleared again."""
+    W, H, V = 96, 72, 2
+    P, cams, _ = scene(seed=14, n=4000, V=V, W=W, H=H)
+    plan, params, cams_dev, _, _ = _forward(cuda_lib, P, cams, W, H, tile=(8, 8), persistent=persistent,
+                                            seg=seg, gl=8)
+    if seg > 0:
+        assert plan_state(plan, V)["seg_count"][0] > 0          # some lists are walked as segments
+    w = torch.from_numpy(np.random.default_rng(15).standard_normal((V, 3, H, W)).astype(np.float32)).cuda()
+    grads = []
+    for _ in range(2):
+        g = torch.zeros_like(params)
+        plan.backward(params, cams_dev, w, g)
+        torch.cuda.synchronize()
+        grads.append(g.cpu().numpy())
+    for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+        nrm, _ = rel_group_error(grads[1][lo:hi], grads[0][lo:hi])
+        assert nrm < 1e-5, (lo, nrm)
+    assert np.abs(grads[0]).max() > 0
+    plan.close()
+
+
 def test_per_view_calls_equal_batched_call(cuda_lib):
     W, H, V = 64, 48, 4
     P, cams, cams32 = scene(seed=7, n=1500, V=V, W=W, H=H)

@@ -312,7 +312,7 @@ def test_graph_and_host_steps_match_batched_steps(cuda_lib):
     launch = dict(tile=(8, 8), ppt=1, group_lanes=16, persistent=True, extent=w.cfg["G"])
     runs = {}
     for mode in ("batched", "graph", "host"):
-        ft = FineTuner(P0.clone(), w.cam_records, w.targets, **launch)
+        ft = FineTuner(P0.clone(), w.cam_records, w.targets, fused_adam=False, **launch)
         host_t = torch.empty(w.targets.shape, dtype=torch.float32, pin_memory=True)
         host_t.copy_(w.targets)
         host_l = torch.zeros(1, dtype=torch.float64, pin_memory=True)
@@ -335,6 +335,65 @@ def test_graph_and_host_steps_match_batched_steps(cuda_lib):
         for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
             nrm, elt = rel_group_error(g[lo:hi], g0[lo:hi])
             assert nrm < 1e-5, (mode, lo, nrm)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_fused_backward_adam_equals_separate_calls(cuda_lib, persistent):
+    """vbm_raster_bwd_adam against vbm_raster_bwd (accumulate = 0, zeroed gradient) +
+    vbm_adam on copies of the same state, at Adam step 6 with nonzero moments (the update
+    is then smooth in the gradient): the columns of a second scene that no view renders
+    take the zero-gradient step bit for bit, the rendered columns agree up to the atomic
+    order of the splat-gradient sums, the step counters advance together, and a
+    non-finite pixel gradient is counted alike."""
+    vbm = cuda_lib
+    W, H, V = 64, 48, 3
+    P, cams, _ = scene(seed=11, n=1200, V=V, W=W, H=H)
+    n1 = P.shape[1]
+    extra, _, _ = scene(seed=12, n=300, V=1, W=W, H=H)
+    P2 = np.concatenate([P, extra], axis=1)
+    n = P2.shape[1]
+    params, cams_dev = to_device(P2, cams)
+    plan = vbm.Plan([0, n1, n], V, W, H, view_scene=[0] * V, tile_w=8, tile_h=8, pair_capacity=1 << 20,
+                    flags=vbm.PLAN_PERSISTENT if persistent else 0, group_lanes=8)
+    img = torch.zeros((V, 3, H, W), device="cuda")
+    plan.forward(params, cams_dev, img)
+    rng = np.random.default_rng(13)
+    lrs = oadam.default_lrs(32.0)
+    m0 = torch.from_numpy((0.01 * rng.standard_normal((14, n))).astype(np.float32)).cuda()
+    v0 = torch.from_numpy((1e-3 * rng.random((14, n)) + 1e-6).astype(np.float32)).cuda()
+    for bad_pixel in (False, True):
+        dimg_h = rng.standard_normal((V, 3, H, W)).astype(np.float32)
+        if bad_pixel:
+            dimg_h[1, 0, H // 2, W // 2] = np.nan
+        dimg = torch.from_numpy(dimg_h).cuda()
+        out = {}
+        for fused in (False, True):
+            Pw, m, v = params.clone(), m0.clone(), v0.clone()
+            step = torch.full((1,), 5, dtype=torch.int32, device="cuda")
+            bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+            if fused:
+                plan.backward_adam(Pw, cams_dev, dimg, m, v, n, step, lrs, nonfinite=bad)
+            else:
+                grad = torch.zeros_like(params)
+                plan.backward(params, cams_dev, dimg, grad)
+                vbm.adam(Pw, grad, m, v, n, step, lrs, nonfinite=bad)
+            torch.cuda.synchronize()
+            out[fused] = [t.cpu().numpy() for t in (Pw, m, v)] + [int(step.item()), int(bad.item())]
+        (Pa, ma, va, sa, ba), (Pb, mb, vb, sb, bb) = out[False], out[True]
+        assert sa == sb == 6
+        assert ba == bb and (ba > 0) == bad_pixel
+        for a, b in ((Pa, Pb), (ma, mb), (va, vb)):
+            assert np.array_equal(a[:, n1:], b[:, n1:])          # unrendered scene: bit for bit
+        if bad_pixel:
+            continue
+        P0 = P2.astype(np.float32)
+        for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+            da, db = Pa[lo:hi, :n1] - P0[lo:hi, :n1], Pb[lo:hi, :n1] - P0[lo:hi, :n1]
+            nrm, elt = rel_group_error(db, da)
+            assert nrm < 1e-4, (lo, nrm, elt)
+            nrm, _ = rel_group_error(mb[lo:hi, :n1], ma[lo:hi, :n1])
+            assert nrm < 1e-5, (lo, nrm)
+    plan.close()
 
 
 def test_peak_probe(cuda_lib):
