@@ -561,7 +561,9 @@ __device__ __forceinline__ void group_sum9(const float (&v)[kNV], float (&out)[G
 // operation (dy = g.y + (-pyc) equals g.y - pyc exactly), so the decisions
 // are the forward's.  Writes the nine partials of this lane's pixels to acc
 // (du, dv, dA, dB, dC, dopacity, dr, dg, db; conic terms in the natural-log
-// parameterisation) and returns whether any pixel blended.
+// parameterisation), du and dv without their factor ln 2 and dA and dC
+// without their factor -1/2 (the round's flush applies them once per splat),
+// and returns whether any pixel blended.
 template <int PPT>
 __device__ __forceinline__ bool pair_step(const WarpSlots &s, int j, float pxc, const float2 (&npyc)[PPT / 2],
                                           const int (&nc)[PPT], float (&T)[PPT], float (&Q)[PPT],
@@ -614,18 +616,17 @@ __device__ __forceinline__ bool pair_step(const WarpSlots &s, int j, float pxc, 
         const float2 dLdaG = __fmul2_rn(dLda, G), dpw = __fmul2_rn(dLda, raw);
         const float2 dG = make_float2(g0 ? dLdaG.x : 0.f, g1 ? dLdaG.y : 0.f);
         const float2 dpow = make_float2(g0 ? dpw.x : 0.f, g1 ? dpw.y : 0.f);
-        const float2 dpl = __fmul2_rn(dpow, make_float2(kLn2, kLn2));
         if (h == 0) {      // the first pair starts the sums
             s_G = dG;
-            s_u = __fmul2_rn(dpl, __ffma2_rn(a_dy, dy, a_c));
-            s_v = __fmul2_rn(dpl, __ffma2_rn(b_dy, dy, b_c));
+            s_u = __fmul2_rn(dpow, __ffma2_rn(a_dy, dy, a_c));
+            s_v = __fmul2_rn(dpow, __ffma2_rn(b_dy, dy, b_c));
             s_pw = dpow;
             s_dy = __fmul2_rn(dpow, dy);
             s_dy2 = __fmul2_rn(dpow, __fmul2_rn(dy, dy));
         } else {
             s_G = __fadd2_rn(s_G, dG);
-            s_u = __ffma2_rn(dpl, __ffma2_rn(a_dy, dy, a_c), s_u);
-            s_v = __ffma2_rn(dpl, __ffma2_rn(b_dy, dy, b_c), s_v);
+            s_u = __ffma2_rn(dpow, __ffma2_rn(a_dy, dy, a_c), s_u);
+            s_v = __ffma2_rn(dpow, __ffma2_rn(b_dy, dy, b_c), s_v);
             s_pw = __fadd2_rn(s_pw, dpow);
             s_dy = __ffma2_rn(dpow, dy, s_dy);
             s_dy2 = __ffma2_rn(dpow, __fmul2_rn(dy, dy), s_dy2);
@@ -637,9 +638,9 @@ __device__ __forceinline__ bool pair_step(const WarpSlots &s, int j, float pxc, 
     }
     acc[0] = s_u.x + s_u.y;
     acc[1] = s_v.x + s_v.y;
-    acc[2] = -0.5f * dx * dx * (s_pw.x + s_pw.y);
+    acc[2] = dx * dx * (s_pw.x + s_pw.y);
     acc[3] = -dx * (s_dy.x + s_dy.y);
-    acc[4] = -0.5f * (s_dy2.x + s_dy2.y);
+    acc[4] = s_dy2.x + s_dy2.y;
     acc[5] = s_G.x + s_G.y;
     acc[6] = s_r.x + s_r.y;
     acc[7] = s_g.x + s_g.y;
@@ -791,11 +792,11 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
                             const float dpow = dLda * raw;   // dL/dpower = dL/dalpha o G
                             acc[5] += dLda * G;
                             // natural-log exponent: A' = -log2e A / 2, B' = -log2e B
-                            acc[0] += dpow * kLn2 * (2.f * g.z * dx + g.w * dy);
-                            acc[1] += dpow * kLn2 * (2.f * cp.x * dy + g.w * dx);
-                            acc[2] += dpow * (-0.5f * dx * dx);
+                            acc[0] += dpow * (2.f * g.z * dx + g.w * dy);
+                            acc[1] += dpow * (2.f * cp.x * dy + g.w * dx);
+                            acc[2] += dpow * (dx * dx);
                             acc[3] += dpow * (-dx * dy);
-                            acc[4] += dpow * (-0.5f * dy * dy);
+                            acc[4] += dpow * (dy * dy);
                         }
                     }
                 }
@@ -821,6 +822,12 @@ __device__ __forceinline__ void bwd_region(const WarpGeom &wg, const int2 *__res
             acc_s[lane][q] = 0.f;
         }
         if (nz) {
+            // the constant factors the step leaves out: ln 2 of the base-2
+            // exponent in du and dv, -1/2 in dA and dC
+            a[0] *= kLn2;
+            a[1] *= kLn2;
+            a[2] *= -0.5f;
+            a[4] *= -0.5f;
             float *rec_g = gs + (int64_t)s.item[lane] * kGradStride;
             atomicAdd(reinterpret_cast<float4 *>(rec_g), make_float4(a[0], a[1], a[2], a[3]));
             atomicAdd(reinterpret_cast<float4 *>(rec_g + 4), make_float4(a[4], a[5], a[6], a[7]));
