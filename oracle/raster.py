@@ -49,6 +49,8 @@ def _load():
         lib.orc_bin_sort.argtypes = [I64, P, P, P, I32, I32, I32, I64, P, P, P, P, P, I32, I32, I32, I32]
         lib.orc_tile_min_q.argtypes = [ctypes.c_double] * 9
         lib.orc_tile_min_q.restype = ctypes.c_double
+        lib.orc_tile_min_q_f32.argtypes = [ctypes.c_float] * 11
+        lib.orc_tile_min_q_f32.restype = ctypes.c_float
         lib.orc_bin_sort.restype = I64
         lib.orc_render.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_render_bwd.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, I64]
@@ -111,6 +113,13 @@ def splat_records(splat, dtype=np.float64):
 def tile_min_q(u, v, A, B, C, x0, x1, y0, y1):
     """Smallest A dx^2 + 2 B dx dy + C dy^2 over the rectangle [x0, x1] x [y0, y1] (FP64)."""
     return _load().orc_tile_min_q(u, v, A, B, C, x0, x1, y0, y1)
+
+
+def tile_min_q_f32(u, v, A, B, C, bc, ba, x0, x1, y0, y1):
+    """The float32 copy of tile_min_q (the edges facing the centre only), every argument
+    rounded to float32 first; bc = B / C and ba = B / A as the caller rounded them."""
+    return float(np.float32(_load().orc_tile_min_q_f32(*[float(np.float32(a)) for a in
+                                                          (u, v, A, B, C, bc, ba, x0, x1, y0, y1)])))
 
 
 def bin_sort(view_of, rect, depth, TX, TY, n_views, capacity=None, splat64=None, splat32=None, tile=(16, 16),

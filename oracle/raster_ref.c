@@ -148,10 +148,18 @@ static void project_state(const double *P, int64_t n, int64_t i, const double *c
  * the edge (dy = -(B / C) dx on a vertical edge, dx = -(B / A) dy on a
  * horizontal one) is clamped to the edge.  The tile is listed when that
  * minimum is <= tau = 2 (ln(255 o) + CULL_MARGIN).  Two copies: double for the
- * FP64 pipeline, and float, operation by operation, for checking a float32
- * implementation's lists bit for bit from its own float32 splat records
- * (bc = B / C and ba = B / A rounded to float; compiled with
- * -ffp-contract=off, so nothing is fused).
+ * FP64 pipeline (all four edges: the plain definition), and float, operation
+ * by operation, for checking a float32 implementation's lists bit for bit
+ * from its own float32 splat records (bc = B / C and ba = B / A rounded to
+ * float; compiled with -ffp-contract=off, so nothing is fused).  The float
+ * copy follows that implementation in evaluating only the edges whose
+ * half-planes exclude the centre (x0 if u < x0, x1 if u > x1, likewise in y):
+ * the minimum of a convex quadratic over a box lies on such an edge (at a
+ * point inside an edge the level set through it touches the edge from the far
+ * side, where the centre lies; at a corner a line through the corner
+ * separates the box from that level set, so the centre violates one of the
+ * corner's two edges), and each kept edge is evaluated with the same
+ * operations as in the four-edge form.
  */
 static double tile_min_q(double u, double v, double A, double B, double C, double bc, double ba, double x0,
                          double x1, double y0, double y1)
@@ -174,25 +182,28 @@ static double tile_min_q(double u, double v, double A, double B, double C, doubl
 static float tile_min_q_f32(float u, float v, float A, float B, float C, float bc, float ba, float x0, float x1,
                             float y0, float y1)
 {
-    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.0f;
-    float best = INFINITY;
-    for (int e = 0; e < 2; e++) {
-        float dx = (e ? x1 : x0) - u;
-        float dy = fminf(fmaxf(v - bc * dx, y0), y1) - v;
-        float q = (A * dx) * dx + ((2.0f * B) * dx) * dy + (C * dy) * dy;
-        best = fminf(best, q);
-        float ey = (e ? y1 : y0) - v;
-        float ex = fminf(fmaxf(u - ba * ey, x0), x1) - u;
-        q = (A * ex) * ex + ((2.0f * B) * ex) * ey + (C * ey) * ey;
-        best = fminf(best, q);
-    }
-    return best;
+    int left = u < x0, right = u > x1, below = v < y0, above = v > y1;
+    if (!(left || right || below || above)) return 0.0f;
+    float dx = (left ? x0 : x1) - u;
+    float dy = fminf(fmaxf(v - bc * dx, y0), y1) - v;
+    float qv = (A * dx) * dx + ((2.0f * B) * dx) * dy + (C * dy) * dy;
+    float ey = (below ? y0 : y1) - v;
+    float ex = fminf(fmaxf(u - ba * ey, x0), x1) - u;
+    float qh = (A * ex) * ex + ((2.0f * B) * ex) * ey + (C * ey) * ey;
+    return fminf(left || right ? qv : INFINITY, below || above ? qh : INFINITY);
 }
 
 /* The tile test, exported for the oracle's own tests. */
 double orc_tile_min_q(double u, double v, double A, double B, double C, double x0, double x1, double y0, double y1)
 {
     return tile_min_q(u, v, A, B, C, B / C, B / A, x0, x1, y0, y1);
+}
+
+/* Its float copy, exported likewise (bc, ba as the caller rounded them). */
+float orc_tile_min_q_f32(float u, float v, float A, float B, float C, float bc, float ba, float x0, float x1,
+                         float y0, float y1)
+{
+    return tile_min_q_f32(u, v, A, B, C, bc, ba, x0, x1, y0, y1);
 }
 
 /* Is tile (tx, ty) listed for a splat record sp = u v A B C bc ba tau? */

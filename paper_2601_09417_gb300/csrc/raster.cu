@@ -77,23 +77,22 @@ __device__ __forceinline__ float rcp_approx(float x)
 }
 
 // Smallest q = A dx^2 + 2 B dx dy + C dy^2 (dx = x - u, dy = y - v) over the
-// rectangle [x0, x1] x [y0, y1]: 0 inside, else the minimum over the four
-// edges, each the clamped 1D minimiser (bc = B / C, ba = B / A precomputed).
+// rectangle [x0, x1] x [y0, y1]: 0 inside, else the minimum over the (at most
+// two) edges whose half-planes exclude the centre, each the clamped 1D
+// minimiser (bc = B / C, ba = B / A precomputed); the binning's tile test
+// (tile_min_q) gives the reason.
 __device__ __forceinline__ float rect_min_quadratic(float u, float v, float A, float B, float C, float bc, float ba,
                                                     float x0, float x1, float y0, float y1)
 {
-    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.f;
-    float best = 3.4e38f;
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-        const float dx = (e ? x1 : x0) - u;
-        const float dy = fminf(fmaxf(v - bc * dx, y0), y1) - v;
-        best = fminf(best, A * dx * dx + 2.f * B * dx * dy + C * dy * dy);
-        const float ey = (e ? y1 : y0) - v;
-        const float ex = fminf(fmaxf(u - ba * ey, x0), x1) - u;
-        best = fminf(best, A * ex * ex + 2.f * B * ex * ey + C * ey * ey);
-    }
-    return best;
+    const bool left = u < x0, right = u > x1, below = v < y0, above = v > y1;
+    if (!(left || right || below || above)) return 0.f;
+    const float dx = (left ? x0 : x1) - u;
+    const float dy = fminf(fmaxf(v - bc * dx, y0), y1) - v;
+    const float qv = A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
+    const float ey = (below ? y0 : y1) - v;
+    const float ex = fminf(fmaxf(u - ba * ey, x0), x1) - u;
+    const float qh = A * ex * ex + 2.f * B * ex * ey + C * ey * ey;
+    return fminf(left || right ? qv : 3.4e38f, below || above ? qh : 3.4e38f);
 }
 
 // Lane groups inside a warp region: GL lanes cover GW columns x GR thread rows.

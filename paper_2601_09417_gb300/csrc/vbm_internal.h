@@ -64,8 +64,13 @@ struct AdamArgs {
 #ifdef __CUDACC__
 // Binning tile test: smallest q = A dx^2 + 2 B dx dy + C dy^2 (dx = x - u,
 // dy = y - v) over the rectangle [x0, x1] x [y0, y1] of a tile's pixel
-// centres: 0 if (u, v) lies inside, else the least of the four edge minima,
-// each edge's 1D minimiser (dy = -bc dx, dx = -ba dy with bc = B / C,
+// centres: 0 if (u, v) lies inside; else the minimum of a convex quadratic
+// over a box lies on an edge whose half-plane excludes the centre (at an
+// interior point of an edge the level set through it is tangent to the edge,
+// with the centre inside, on the far side; at a corner a line through the
+// corner separates the box from that level set), so at most one vertical
+// edge (x0 if u < x0, x1 if u > x1) and one horizontal edge are evaluated,
+// each by its 1D minimiser (dy = -bc dx, dx = -ba dy with bc = B / C,
 // ba = B / A) clamped to the edge.  A tile is listed for a splat when this is
 // <= tau = 2 (ln(255 o) + kCullMargin): alpha = o e^(-q/2) >= 1/255 needs
 // q <= 2 ln(255 o), so a pixel of an unlisted tile would skip the splat.
@@ -74,23 +79,19 @@ struct AdamArgs {
 __device__ __forceinline__ float tile_min_q(float u, float v, float A, float B, float C, float bc, float ba,
                                             float x0, float x1, float y0, float y1)
 {
-    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.f;
-    float best = __int_as_float(0x7f800000);
+    const bool left = u < x0, right = u > x1, below = v < y0, above = v > y1;
+    if (!(left || right || below || above)) return 0.f;
+    const float inf = __int_as_float(0x7f800000);
     const float B2 = __fmul_rn(2.f, B);
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-        const float dx = __fsub_rn(e ? x1 : x0, u);
-        const float dy = __fsub_rn(fminf(fmaxf(__fsub_rn(v, __fmul_rn(bc, dx)), y0), y1), v);
-        float q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(B2, dx), dy)),
-                            __fmul_rn(__fmul_rn(C, dy), dy));
-        best = fminf(best, q);
-        const float ey = __fsub_rn(e ? y1 : y0, v);
-        const float ex = __fsub_rn(fminf(fmaxf(__fsub_rn(u, __fmul_rn(ba, ey)), x0), x1), u);
-        q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, ex), ex), __fmul_rn(__fmul_rn(B2, ex), ey)),
-                      __fmul_rn(__fmul_rn(C, ey), ey));
-        best = fminf(best, q);
-    }
-    return best;
+    const float dx = __fsub_rn(left ? x0 : x1, u);
+    const float dy = __fsub_rn(fminf(fmaxf(__fsub_rn(v, __fmul_rn(bc, dx)), y0), y1), v);
+    const float qv = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(B2, dx), dy)),
+                               __fmul_rn(__fmul_rn(C, dy), dy));
+    const float ey = __fsub_rn(below ? y0 : y1, v);
+    const float ex = __fsub_rn(fminf(fmaxf(__fsub_rn(u, __fmul_rn(ba, ey)), x0), x1), u);
+    const float qh = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, ex), ex), __fmul_rn(__fmul_rn(B2, ex), ey)),
+                               __fmul_rn(__fmul_rn(C, ey), ey));
+    return fminf(left || right ? qv : inf, below || above ? qh : inf);
 }
 
 // Is tile (tx, ty) of a tw x th grid over a W x H image listed for the splat?

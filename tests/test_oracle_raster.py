@@ -124,6 +124,83 @@ def test_tile_min_q_is_the_minimum_over_the_rectangle():
         assert brute - got <= slope * h + 1e-9
 
 
+def _four_edge_f32(u, v, A, B, C, bc, ba, x0, x1, y0, y1):
+    """All four edges in float32 (numpy scalars round every operation), the order of the
+    binning test's four-edge form."""
+    f = np.float32
+    u, v, A, B, C, bc, ba, x0, x1, y0, y1 = (f(a) for a in (u, v, A, B, C, bc, ba, x0, x1, y0, y1))
+    if x0 <= u <= x1 and y0 <= v <= y1:
+        return 0.0
+    best = np.inf
+    for e in (0, 1):
+        dx = (x1 if e else x0) - u
+        dy = min(max(v - bc * dx, y0), y1) - v
+        best = min(best, (A * dx) * dx + ((f(2) * B) * dx) * dy + (C * dy) * dy)
+        ey = (y1 if e else y0) - v
+        ex = min(max(u - ba * ey, x0), x1) - u
+        best = min(best, (A * ex) * ex + ((f(2) * B) * ex) * ey + (C * ey) * ey)
+    return float(best)
+
+
+def test_tile_min_q_two_facing_edges_suffice():
+    """The float32 tile test evaluates only the edges whose half-planes exclude the centre.
+    The minimum of a convex quadratic over a box lies on such an edge, so its value equals
+    the four-edge FP64 definition to float32 rounding and, where the kept edges hold the
+    minimum, the float32 four-edge form bit for bit; cases put the centre inside, beside,
+    diagonal to and on the lines through the rectangle's edges, with strongly tilted
+    ellipses."""
+    rng = np.random.default_rng(41)
+    same = 0
+    for it in range(3000):
+        L = rng.normal(size=(2, 2)) * rng.uniform(0.05, 2.0)
+        M = L @ L.T + np.eye(2) * rng.uniform(0.001, 0.5)
+        A, B, C = (float(np.float32(a)) for a in (M[0, 0], M[0, 1], M[1, 1]))
+        x0, y0 = (float(np.float32(a)) for a in rng.uniform(-10, 10, 2))
+        x1, y1 = float(np.float32(x0 + rng.uniform(0.5, 12))), float(np.float32(y0 + rng.uniform(0.5, 12)))
+        u, v = (float(np.float32(a)) for a in rng.uniform(-25, 25, 2))
+        if it % 5 == 1:
+            u = x0 if it % 2 else x1          # on a vertical edge's line
+        if it % 7 == 2:
+            v = y0 if it % 3 else y1          # on a horizontal edge's line
+        bc, ba = float(np.float32(B) / np.float32(C)), float(np.float32(B) / np.float32(A))
+        got = raster.tile_min_q_f32(u, v, A, B, C, bc, ba, x0, x1, y0, y1)
+        ref64 = raster.tile_min_q(u, v, A, B, C, x0, x1, y0, y1)
+        four = _four_edge_f32(u, v, A, B, C, bc, ba, x0, x1, y0, y1)
+        scale = (abs(A) + abs(B) + abs(C)) * (abs(u) + abs(v) + abs(x0) + abs(x1) + abs(y0) + abs(y1) + 1) ** 2
+        assert abs(got - ref64) <= 2e-6 * scale, (it, got, ref64)
+        assert got >= four                  # dropping edges can only raise the float minimum
+        assert got - four <= 2e-6 * scale    # and then only by rounding
+        same += got == four
+    assert same > 0.99 * 3000
+
+
+def test_two_facing_edges_hold_the_minimum_fp64():
+    """In exact arithmetic the two-edge rule is the definition: in FP64 the edges facing
+    the centre give the four-edge minimum of the oracle to 1e-12 relative (both edges of a
+    corner evaluate the same point)."""
+    rng = np.random.default_rng(42)
+    for it in range(3000):
+        L = rng.normal(size=(2, 2)) * rng.uniform(0.05, 2.0)
+        M = L @ L.T + np.eye(2) * rng.uniform(0.001, 0.5)
+        A, B, C = M[0, 0], M[0, 1], M[1, 1]
+        x0, y0 = rng.uniform(-10, 10, 2)
+        x1, y1 = x0 + rng.uniform(0.5, 12), y0 + rng.uniform(0.5, 12)
+        u, v = rng.uniform(-25, 25, 2)
+        if x0 <= u <= x1 and y0 <= v <= y1:
+            continue
+        cand = []
+        if u < x0 or u > x1:
+            dx = (x0 if u < x0 else x1) - u
+            dy = min(max(v - B / C * dx, y0), y1) - v
+            cand.append(A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+        if v < y0 or v > y1:
+            ey = (y0 if v < y0 else y1) - v
+            ex = min(max(u - B / A * ey, x0), x1) - u
+            cand.append(A * ex * ex + 2 * B * ex * ey + C * ey * ey)
+        ref = raster.tile_min_q(u, v, A, B, C, x0, x1, y0, y1)
+        assert abs(min(cand) - ref) <= 1e-12 * max(1.0, ref), (it, min(cand), ref)
+
+
 def test_projection_covariance_is_symmetric_pd_and_culls():
     cams = orbit_cameras((32, 32, 32), 3, 80, 60)
     P = gaussians_in_view(200, 32, seed=3)
