@@ -112,8 +112,11 @@ __device__ __forceinline__ void project_view(const vbm_camera &cam, ProjState &s
 // Gaussian per thread: the view-independent state (rotation, 3D covariance,
 // opacity) is built once and projected for each of those views.  With
 // several scenes vpt is 1 (consecutive views may render different scenes).
+// Four resident blocks (64 registers): the kernel waits on its parameter and
+// camera loads, and 32 warps per SM hide more of that than 24.
 template <bool MULTI>
-__global__ void k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
+__global__ void __launch_bounds__(256, 4)
+    k_preprocess_fwd(const float *__restrict__ P, int64_t stride, const vbm_camera *__restrict__ cams,
                                  const int64_t *__restrict__ scene_offset, const int32_t *__restrict__ view_scene,
                                  const int64_t *__restrict__ view_item_offset, int vb, int vc, int vpt, int TX,
                                  int TY, int tw, int th, int W, int H, SplatRec *__restrict__ rec,
