@@ -263,8 +263,11 @@ __device__ __forceinline__ void adam_gaussian(const AdamArgs &a, int64_t stride,
 // [g_begin, g_end) have a zero gradient), with the separate Adam kernel's
 // arithmetic, so the result equals a backward with accumulate = 0 into a
 // zeroed gradient followed by that kernel, bit for bit.
+// Twenty resident one-warp blocks (at most 102 registers; the Adam epilogue
+// would otherwise take 115 and leave 17): the kernel waits on its gradient
+// loads.
 template <bool ADAM>
-__global__ void k_preprocess_bwd(const float *P, int64_t stride, const vbm_camera *__restrict__ cams,
+__global__ void __launch_bounds__(32, 20) k_preprocess_bwd(const float *P, int64_t stride, const vbm_camera *__restrict__ cams,
                                  const int64_t *__restrict__ scene_offset, int n_scenes,
                                  const int32_t *__restrict__ scene_view_ptr, const int32_t *__restrict__ scene_views,
                                  const int64_t *__restrict__ view_item_offset, int vb, int vc,
