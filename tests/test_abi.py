@@ -44,6 +44,34 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(lib.BankEntry) == 128
 
 
+def test_struct_layouts_match_header(lib, tmp_path):
+    """Every struct the binding declares has the header's size and, field by field, the
+    header's offsets (a C program compiled against include/vbm.h prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = [("vbm_camera", lib.Camera), ("vbm_tf", lib.TF), ("vbm_bank_entry", lib.BankEntry),
+               ("vbm_bank", lib.Bank), ("vbm_select", lib.Select), ("vbm_plan_desc", lib.PlanDesc),
+               ("vbm_plan_buffers", lib.PlanBuffers)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vbm.h"', "int main(void) {"]
+    for cname, cls in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines))
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", include, "-o", str(exe), str(src)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, cls in structs:
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert int(got[cname + "." + f[0]]) == getattr(cls, f[0]).offset, (cname, f[0])
+
+
 def test_host_argument_validation(lib):
     with pytest.raises(lib.VbmError) as e:
         lib.Plan([0, 10], 2, 64, 64, tile_w=16, tile_h=12)      # 192-pixel tiles are not supported
@@ -51,6 +79,10 @@ def test_host_argument_validation(lib):
     with pytest.raises(lib.VbmError) as e:
         lib.Plan([0, 10, 5], 2, 64, 64, view_scene=[0, 1])       # decreasing offsets
     assert e.value.status == lib.VBM_ERR_ARG
+    with pytest.raises(lib.VbmError) as e:
+        lib.Plan([0, 10], 1, 8 * 65536, 64, tile_w=8, tile_h=8)  # 65536 tiles across: the placement
+    assert e.value.status == lib.VBM_ERR_ARG                    # record packs tile columns in 16 bits
+    assert "65535 tiles" in lib.load().vbm_last_error().decode()
     with pytest.raises(lib.VbmError) as e:
         lib.bank_build(0, 0)
     assert e.value.status == lib.VBM_ERR_ARG
