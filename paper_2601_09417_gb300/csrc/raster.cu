@@ -420,13 +420,13 @@ __device__ __forceinline__ void fwd_region(const WarpGeom &wg, const int2 *__res
                     const int kk = k + h;
                     const float alpha = fminf(kAlphaMax, raw[h]);
                     const bool cand = !done[kk] && p2[h] <= 0.f && alpha >= kAlphaMin;
-                    const float testT = T[kk] * (1.f - alpha);
+                    const float testT = __fmaf_rn(-alpha, T[kk], T[kk]);   // T (1 - alpha), one rounding
                     const bool term = cand && testT < kTMin;
                     const bool blend = cand && !term;
                     done[kk] = done[kk] || term;
                     if (EVAL && term) evaluated[kk] = pos1;
-                    if (COLOR) {
-                        const float wgt = blend ? alpha * T[kk] : 0.f;
+                    if (COLOR && blend) {
+                        const float wgt = __fmul_rn(alpha, T[kk]);
                         C0[kk] = __fmaf_rn(c.x, wgt, C0[kk]);
                         C1[kk] = __fmaf_rn(c.y, wgt, C1[kk]);
                         C2[kk] = __fmaf_rn(c.z, wgt, C2[kk]);
