@@ -9,8 +9,8 @@
 // pixel centres gives the largest alpha any of its pixels can see; entries
 // below the 1/255 cut-off, with a 1e-3 margin in the exponent far above
 // rounding, are dropped) and stores it in the warp's shared-memory slot.  The
-// lanes of the warp form groups of GL lanes (GL = 32, 16 or 8) that own
-// 8 x 4, 4 x 4 or 4 x 2 thread positions; a group keeps a 32-bit mask of the
+// lanes of the warp form groups of GL lanes (GL = 32, 16, 8 or 4) that own
+// 8 x 4, 4 x 4, 4 x 2 or 2 x 2 thread positions; a group keeps a 32-bit mask of the
 // slots whose alpha >= 1/255 bounding box reaches its pixels and walks only
 // those, so the groups of a warp composite different splats at the same
 // time.  An entry a warp drops or a group skips would have been skipped by
@@ -29,11 +29,12 @@
 // contributor count (a group also drops entries beyond the largest count of
 // its own pixels), recovers the transmittance with a hardware reciprocal of
 // (1 - alpha) and accumulates per-(view, splat) gradients: per splat, a group
-// sums its nine partials over its lanes by a reduce-scatter (10 to 12
+// sums its nine partials over its lanes by a reduce-scatter (8 to 12
 // shuffles, skipped when no lane of the warp contributes), the lanes holding
 // the sums add them to the warp's shared-memory accumulator for the round,
 // and the round is flushed to the per-item gradient records with vector
-// atomics (two float4 and one float per staged entry with a nonzero value).
+// atomics (two float4 and one float per staged entry with a nonzero value),
+// the partials' constant factors applied at the flush.
 //
 // Launch: blocks of kWarps warps; each warp takes work items (tile, region)
 // either by its global warp index or, persistent, from an atomic queue whose
